@@ -1,0 +1,386 @@
+"""Seeded synthetic scenes for the photon Monte Carlo path.
+
+This module describes WHAT is simulated: optical prescriptions, phase screens, spectra, sensor tables and
+source catalogues, all generated from recorded seeds.  Both the CUDA path and the CPU oracle consume the
+same scene objects; neither side's per-photon arithmetic lives here.  What the paper computes before the
+photon loop starts (screen synthesis, Sec. 2.3.1; the blackbody SED, Sec. 2.2; the Rajkanan absorption
+coefficient, Sec. 2.4.2; the Sersic radial distribution, Sec. 2.2.1) is produced here as tables, because
+the photon path itself only looks those tables up.
+
+Units: lengths in mm, angles in rad, wavelengths in nm, times in s, phases in rad at LAMBDA_REF_NM.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import math
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+LAMBDA_REF_NM = 500.0
+H_TOP_MM = 100.0e6           # top of the atmosphere, 100 km (Sec. 2.2)
+
+# surface kinds
+MIRROR, REFRACT, DETECTOR = 0, 1, 2
+# material kinds
+VACUUM, SELLMEIER, SILICON = 0, 1, 2
+# source kinds
+POINT, SERSIC, GAUSS = 0, 1, 2
+
+# fused silica Sellmeier coefficients of Malitson (1965), lambda in um, C in um^2
+FUSED_SILICA_B = (0.6961663, 0.4079426, 0.8974794)
+FUSED_SILICA_C = (0.0684043 ** 2, 0.1162414 ** 2, 9.896161 ** 2)
+
+ARCSEC = math.pi / (180.0 * 3600.0)
+DEG = math.pi / 180.0
+
+
+@dataclass
+class Material:
+    kind: int = VACUUM
+    B: Sequence[float] = (0.0, 0.0, 0.0)
+    C: Sequence[float] = (0.0, 0.0, 0.0)
+
+
+@dataclass
+class Coating:
+    """Transmission probability T(lambda, theta), piecewise constant on a uniform grid
+    (the paper's angle/wavelength coating interface, Sec. 2.4.2)."""
+    lam0: float
+    dlam: float
+    theta0: float
+    dtheta: float
+    table: np.ndarray            # shape (n_lambda, n_theta), float64 in [0, 1]
+
+
+@dataclass
+class Surface:
+    kind: int
+    R: float = 0.0               # radius of curvature (mm); 0 = flat
+    kappa: float = 0.0
+    alpha: Sequence[float] = (0.0,) * 8      # alpha_3 .. alpha_10, units mm^(1-i)
+    z: float = 0.0               # vertex position on the optical axis (mm)
+    r_in: float = 0.0            # clear aperture (mm), photons outside are removed
+    r_out: float = 1.0e30
+    material: int = 0            # medium after a refracting surface (index into Scene.materials)
+    coating: int = -1            # index into Scene.coatings, -1 = none
+    pert: Sequence[float] = (0.0,) * 6       # dx, dy, dz (mm), tx, ty, tz (rad)
+    zern_rnorm: float = 0.0      # normalisation radius of the Zernike figure (mm)
+    zern: Sequence[float] = ()   # Noll coefficients c_1..c_J (mm of sag)
+
+
+@dataclass
+class Detector:
+    nx: int
+    ny: int
+    pixel: float                 # mm
+    x0: float = 0.0              # chip centre in the detector surface frame (mm)
+    y0: float = 0.0
+    t_si: float = 0.1            # silicon thickness (mm)
+    ell_lam0: float = 300.0      # absorption length table: lambda grid (nm) and values (mm)
+    ell_dlam: float = 1.0
+    ell: np.ndarray = None
+    sigma: np.ndarray = None     # diffusion sigma (mm) at depths uniformly spaced over [0, t_si]
+
+
+@dataclass
+class ScreenScale:
+    pixel: float                 # mm
+    phase: np.ndarray            # (N, N) float64, rad at LAMBDA_REF_NM, row = y index, column = x index
+
+
+@dataclass
+class Layer:
+    z: float                     # altitude of the layer in the telescope frame (mm)
+    vx: float = 0.0              # wind (mm/s)
+    vy: float = 0.0
+    scales: List[ScreenScale] = field(default_factory=list)
+
+
+@dataclass
+class Sources:
+    kind: np.ndarray             # int32
+    sed: np.ndarray              # int32, index into the SED tables
+    xi: np.ndarray               # tangent-plane direction components (rad), Sec. 2.2
+    eta: np.ndarray
+    redshift: np.ndarray
+    t0: np.ndarray
+    t_exp: np.ndarray
+    a: np.ndarray                # Sersic semi-major axis at r = r_e (rad); Gaussian sigma (rad)
+    b: np.ndarray                # Sersic semi-minor axis (rad)
+    pa: np.ndarray               # position angle (rad)
+    table: np.ndarray            # int32, Sersic radial table index
+    n_photons: np.ndarray        # uint64
+
+    def __len__(self):
+        return len(self.kind)
+
+    def subset(self, idx):
+        return Sources(**{f.name: np.asarray(getattr(self, f.name))[idx] for f in dataclasses.fields(self)})
+
+
+@dataclass
+class Scene:
+    seed: int
+    pupil_r_in: float
+    pupil_r_out: float
+    surfaces: List[Surface]
+    materials: List[Material]
+    coatings: List[Coating]
+    detector: Detector
+    layers: List[Layer]
+    sed_lam0: float
+    sed_dlam: float
+    sed_flux: np.ndarray         # (n_sed, n_bins) flux density per unit wavelength
+    sersic: np.ndarray           # (n_tables, K) radius in units of r_e at u = (k + 0.5) / K
+    sources: Sources
+    h_top: float = H_TOP_MM
+    lambda_ref: float = LAMBDA_REF_NM
+    atmosphere: bool = True
+    sensor: bool = True          # False: record the hit on the detector surface, no silicon
+    z_entrance: float = None     # plane (mm) where the raytrace starts, below every layer, above every optic
+
+    def __post_init__(self):
+        if self.z_entrance is None:
+            self.z_entrance = max(s.z for s in self.surfaces) + 1000.0
+
+
+# ----------------------------------------------------------------------------------------------------------
+# tables the paper computes before the photon loop
+# ----------------------------------------------------------------------------------------------------------
+
+def blackbody_flux(T_K, lam_nm):
+    """Planck spectral radiance per unit wavelength (arbitrary overall scale) at lam_nm."""
+    h, c, k = 6.62607015e-34, 2.99792458e8, 1.380649e-23
+    lam = np.asarray(lam_nm, dtype=np.float64) * 1e-9
+    x = h * c / (lam * k * np.asarray(T_K, dtype=np.float64)[..., None])
+    return (1.0 / lam ** 5) / np.expm1(x) * 1e-30
+
+
+def sed_tables(temps_K, lam0=300.0, dlam=1.0, nbins=900):
+    centres = lam0 + (np.arange(nbins) + 0.5) * dlam
+    return blackbody_flux(np.atleast_1d(temps_K), centres)
+
+
+def rajkanan_alpha_per_cm(lam_nm, T_K=173.0):
+    """Absorption coefficient of silicon (1/cm) from the Rajkanan model with the constants of Sec. 2.4.2.
+    Each squared term contributes only where its base is positive; the direct-gap term only above E_gd."""
+    E = 1239.841984 / np.asarray(lam_nm, dtype=np.float64)
+    kT = 8.617333262e-5 * T_K
+    beta, gamma = 7.021e-4, 1108.0
+    shift = beta * T_K * T_K / (T_K + gamma)
+    Eg = (1.1557 - shift, 2.5 - shift)
+    Egd = 3.2 - shift
+    Ep = (1.827e-2, 5.773e-2)
+    C = (5.5, 4.0)
+    A = (3.231e2, 7.237e3)
+    Ad = 1.052e6
+    alpha = np.zeros_like(E)
+    for i in range(2):
+        for j in range(2):
+            b1 = E - Eg[j] + Ep[i]
+            b2 = E - Eg[j] - Ep[i]
+            t1 = np.where(b1 > 0, b1 * b1, 0.0) / np.expm1(Ep[i] / kT)
+            t2 = np.where(b2 > 0, b2 * b2, 0.0) / (-np.expm1(-Ep[i] / kT))
+            alpha += C[i] * A[j] * (t1 + t2)
+    alpha += Ad * np.sqrt(np.clip(E - Egd, 0.0, None))
+    return alpha
+
+
+def absorption_length_table(lam0=300.0, dlam=1.0, n=901, T_K=173.0):
+    lam = lam0 + np.arange(n) * dlam
+    return 10.0 / rajkanan_alpha_per_cm(lam, T_K)      # mm
+
+
+def sersic_bn(n):
+    from scipy.special import gammaincinv
+    return float(gammaincinv(2.0 * n, 0.5))
+
+
+def sersic_radius_table(n, K=1024):
+    """Inverse cumulative distribution of the radius (units of the half-light radius) of a circular
+    Sersic profile I(r) ~ exp(-b_n r^(1/n)) (Sec. 2.2.1), sampled at u = (k + 0.5) / K."""
+    from scipy.special import gammaincinv
+    bn = sersic_bn(n)
+    u = (np.arange(K) + 0.5) / K
+    return (gammaincinv(2.0 * n, u) / bn) ** n
+
+
+# ----------------------------------------------------------------------------------------------------------
+# phase screens (Sec. 2.3.1): FFT synthesis with subharmonics
+# ----------------------------------------------------------------------------------------------------------
+
+PSD_CONST = 0.023   # phase PSD 0.023 r0^(-5/3) f^(-11/3), f in cycles per metre
+
+
+def phase_psd(f2, r0_m, L0_m):
+    inv_L0_2 = 0.0 if not np.isfinite(L0_m) else 1.0 / (L0_m * L0_m)
+    with np.errstate(divide="ignore"):
+        return PSD_CONST * r0_m ** (-5.0 / 3.0) * (f2 + inv_L0_2) ** (-11.0 / 6.0)
+
+
+def _cell_power(fx, fy, dfc, r0_m, L0_m, nq=8):
+    """Power of the PSD integrated over the square cell of side dfc centred on (fx, fy) (Gauss-Legendre),
+    given to the single mode that stands for the cell.  Near the origin the PSD changes by orders of
+    magnitude across a cell, so its midpoint value under-represents the cell's variance."""
+    x, w = np.polynomial.legendre.leggauss(nq)
+    x = 0.5 * x * dfc
+    w = 0.5 * w
+    FX = np.asarray(fx)[..., None, None] + x[:, None]
+    FY = np.asarray(fy)[..., None, None] + x[None, :]
+    return (phase_psd(FX * FX + FY * FY, r0_m, L0_m) * (w[:, None] * w[None, :])).sum((-1, -2)) * dfc * dfc
+
+
+def fft_mode_power(N, pix_m, r0_m, L0_m, keep="all", fcut=None):
+    """Variance given to each FFT mode of an N x N screen (layout of numpy.fft.fftfreq)."""
+    df = 1.0 / (N * pix_m)
+    f = np.fft.fftfreq(N, pix_m)
+    fx, fy = np.meshgrid(f, f)
+    power = phase_psd(fx * fx + fy * fy, r0_m, L0_m) * df * df
+    power[0, 0] = 0.0
+    if keep == "low":
+        return np.where((np.abs(fx) < fcut) & (np.abs(fy) < fcut), power, 0.0)
+    m = np.fft.fftfreq(N, 1.0 / N).astype(int)
+    near = np.where(np.abs(m) <= 3)[0]
+    for iy in near:
+        for ix in near:
+            if iy or ix:
+                power[iy, ix] = _cell_power(fx[iy, ix], fy[iy, ix], df, r0_m, L0_m)
+    return power
+
+
+def phase_screen(N, pix_m, r0_m, L0_m, rng, subharmonics=0, keep="all", fcut=None):
+    """Periodic N x N screen of phase (rad at 500 nm) with pixel pix_m metres (FFT synthesis).
+
+    keep="all": every FFT mode except f = 0 (cells next to the origin carry their cell-integrated power),
+    plus `subharmonics` levels of 3 x 3 sub-harmonic cells that represent the origin's cell (they make the
+    screen non-periodic).  keep="low": only modes with |fx| < fcut and |fy| < fcut (the coarse scale of a
+    two-scale pair), each with its midpoint power.
+    """
+    df = 1.0 / (N * pix_m)
+    power = fft_mode_power(N, pix_m, r0_m, L0_m, keep, fcut)
+    cn = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))) * np.sqrt(power)
+    phs = np.fft.ifft2(cn).real * (N * N)
+    if keep == "all" and subharmonics:
+        x = np.arange(N) * pix_m
+        X, Y = np.meshgrid(x, x)
+        lo = np.zeros((N, N))
+        for p in range(1, subharmonics + 1):
+            dfp = df / 3.0 ** p
+            for m in (-1, 0, 1):
+                for n in (-1, 0, 1):
+                    if m == 0 and n == 0:
+                        continue
+                    fxp, fyp = m * dfp, n * dfp
+                    amp = np.sqrt(_cell_power(fxp, fyp, dfp, r0_m, L0_m))
+                    c = (rng.standard_normal() + 1j * rng.standard_normal()) * amp
+                    lo += (c * np.exp(2j * np.pi * (fxp * X + fyp * Y))).real
+        phs = phs + lo - lo.mean()
+    return phs
+
+
+# ----------------------------------------------------------------------------------------------------------
+# sources
+# ----------------------------------------------------------------------------------------------------------
+
+def point_sources(xi, eta, n_photons, sed=None, t0=0.0, t_exp=15.0):
+    n = len(xi)
+    z = np.zeros(n)
+    return Sources(kind=np.full(n, POINT, np.int32),
+                   sed=np.zeros(n, np.int32) if sed is None else np.asarray(sed, np.int32),
+                   xi=np.asarray(xi, np.float64), eta=np.asarray(eta, np.float64), redshift=z.copy(),
+                   t0=np.full(n, t0), t_exp=np.full(n, t_exp), a=z.copy(), b=z.copy(), pa=z.copy(),
+                   table=np.zeros(n, np.int32), n_photons=np.asarray(n_photons, np.uint64))
+
+
+def concat_sources(parts: Sequence[Sources]) -> Sources:
+    return Sources(**{f.name: np.concatenate([np.asarray(getattr(p, f.name)) for p in parts])
+                      for f in dataclasses.fields(Sources)})
+
+
+# ----------------------------------------------------------------------------------------------------------
+# scene recipes
+# ----------------------------------------------------------------------------------------------------------
+
+def _sensor(nx, pixel, lam0, nlam, t_si=0.1, sigma=0.003):
+    return Detector(nx=nx, ny=nx, pixel=pixel, t_si=t_si, ell_lam0=lam0, ell_dlam=1.0,
+                    ell=absorption_length_table(lam0, 1.0, nlam + 1), sigma=np.array([sigma, sigma]))
+
+
+def paraboloid_scene(n_photons=100_000, seed=1, screen_n=512, screen_pix_mm=20.0, r0_m=0.15,
+                     layer_z_mm=5.0e6, atmosphere=True, sensor=True, screen_seed=11, xi=0.0, eta=0.0,
+                     sed_T=5800.0, lam_lo=400.0, lam_hi=700.0, chip=256):
+    """One on-axis star through one frozen Kolmogorov screen onto a D = 1 m f/10 paraboloid and a
+    chip of 10 um pixels behind 100 um of silicon (the plain-method tiny case)."""
+    R = 20000.0
+    surfaces = [Surface(kind=MIRROR, R=R, kappa=-1.0, z=0.0, r_in=0.0, r_out=500.0),
+                Surface(kind=DETECTOR, R=0.0, z=R / 2.0, material=1)]
+    materials = [Material(VACUUM), Material(SILICON)]
+    nb = int(round(lam_hi - lam_lo))
+    layers = []
+    if atmosphere:
+        # sub-harmonics restore the low-frequency power the FFT lattice misses; they make the screen
+        # non-periodic, so it is rolled by half a screen to put the seam 5 m away from the pupil (v = 0)
+        rng = np.random.default_rng(screen_seed)
+        ph = phase_screen(screen_n, screen_pix_mm * 1e-3, r0_m, np.inf, rng, subharmonics=3)
+        ph = np.roll(ph, (screen_n // 2, screen_n // 2), (0, 1))
+        layers = [Layer(z=layer_z_mm, scales=[ScreenScale(screen_pix_mm, ph)])]
+    src = point_sources([xi], [eta], [n_photons])
+    return Scene(seed=seed, pupil_r_in=0.0, pupil_r_out=500.0, surfaces=surfaces, materials=materials,
+                 coatings=[], detector=_sensor(chip, 0.01, lam_lo, nb), layers=layers, sed_lam0=lam_lo,
+                 sed_dlam=1.0, sed_flux=sed_tables([sed_T], lam_lo, 1.0, nb), sersic=np.ones((1, 4)),
+                 sources=src, atmosphere=atmosphere, sensor=sensor)
+
+
+def cn2_weights(rng, n_layers=7):
+    """Relative turbulence integral per layer: one log-normal draw for the ground layer and one shared by
+    the free-atmosphere layers (Sec. 2.3.1), applied to a fixed base profile and normalised to 1."""
+    base = np.array([0.45, 0.10, 0.10, 0.10, 0.10, 0.08, 0.07])[:n_layers]
+    g_ground, g_free = rng.standard_normal(2)
+    w = base * np.exp(0.4 * np.r_[g_ground, np.full(n_layers - 1, g_free)])
+    return w / w.sum()
+
+
+LAYER_HEIGHTS_KM = (0.0, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0)
+ATM_Z0_MM = 25_000.0     # telescope-frame height of altitude 0: above every optical surface
+
+
+def von_karman_layers(seed=7, r0_m=0.15, L0_m=20.0, fine_n=4096, fine_pix_mm=10.0, coarse_n=1024,
+                      coarse_pix_mm=640.0, heights_km=LAYER_HEIGHTS_KM, wind_scale_m_s=10.0):
+    """Seven frozen-flow layers, each a fine screen plus a coarse screen holding the modes too long for
+    the fine one (two of the paper's pixel scales, Sec. 2.3.1)."""
+    rng = np.random.default_rng(seed)
+    w = cn2_weights(rng, len(heights_km))
+    fcut = 1.0 / (2.0 * fine_n * fine_pix_mm * 1e-3)
+    layers = []
+    for k, h in enumerate(heights_km):
+        r0k = r0_m * w[k] ** (-3.0 / 5.0)
+        fine = phase_screen(fine_n, fine_pix_mm * 1e-3, r0k, L0_m, rng, subharmonics=0)
+        coarse = phase_screen(coarse_n, coarse_pix_mm * 1e-3, r0k, L0_m, rng, subharmonics=0, keep="low",
+                              fcut=fcut)
+        speed = wind_scale_m_s * math.sqrt(-math.log(1.0 - rng.random()))    # Weibull, k = 2
+        ang = 2.0 * math.pi * rng.random()
+        layers.append(Layer(z=ATM_Z0_MM + h * 1e6, vx=speed * 1e3 * math.cos(ang), vy=speed * 1e3 * math.sin(ang),
+                            scales=[ScreenScale(fine_pix_mm, fine), ScreenScale(coarse_pix_mm, coarse)]))
+    layers.sort(key=lambda L: -L.z)
+    return layers
+
+
+DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+def load_optics_json(path):
+    with open(path) as f:
+        d = json.load(f)
+    surfaces = [Surface(**s) for s in d["surfaces"]]
+    materials = [Material(**m) for m in d["materials"]]
+    return d, surfaces, materials
+
+
+def filter_coating(lo=550.0, hi=700.0, T_in=0.95, lam0=300.0, nlam=900):
+    lam = lam0 + np.arange(nlam) + 0.5
+    T = np.where((lam > lo) & (lam < hi), T_in, 0.0)
+    return Coating(lam0=lam0, dlam=1.0, theta0=0.0, dtheta=math.pi / 2, table=T[:, None].copy())
