@@ -1,0 +1,230 @@
+/*
+ * phosim.h — C ABI of the GB300 photon Monte Carlo library.
+ *
+ * The library traces astrophysical photons one by one through frozen-flow atmospheric phase screens, an
+ * aspheric multi-surface telescope/camera and a silicon sensor into a pixel histogram, as described in
+ * Peterson et al. 2015 (PhoSim), Sec. 2.  Every per-photon step runs in CUDA kernels for sm_103a on the
+ * caller's stream; nothing in this interface uses C++ or PyTorch types.
+ *
+ * Conventions
+ *   - Units: mm for lengths, rad for angles, nm for wavelengths, s for times, rad (at lambda_ref) for phase.
+ *   - The telescope frame has z along the optical axis; photons arrive travelling towards -z (Sec. 2.2).
+ *   - Ownership: the caller owns every input and output buffer.  A scene owns device copies of everything
+ *     loaded into it; load calls copy synchronously and may be called again to replace what they load.
+ *   - Errors: every call returns a phosim_status (0 = success, negative = error) and never throws or aborts.
+ *     A failed call leaves the scene as it was before the call, except where noted.  Per-photon events
+ *     (vignetting, total internal reflection, a non-converged intersection, leaving the chip) are not
+ *     errors: such photons are dropped and counted (phosim_get_counters).
+ *   - Thread safety: calls on different scenes may run concurrently; calls on one scene must not overlap.
+ */
+#ifndef PHOSIM_H
+#define PHOSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int phosim_status;
+#define PHOSIM_OK 0
+#define PHOSIM_ERR_INVALID_ARGUMENT (-1)
+#define PHOSIM_ERR_OUT_OF_MEMORY (-2)
+#define PHOSIM_ERR_CUDA (-3)
+#define PHOSIM_ERR_UNSUPPORTED (-4)
+#define PHOSIM_ERR_NOT_READY (-5)    /* a required load (optics, SEDs) has not been done */
+#define PHOSIM_ERR_LIMIT (-6)        /* a size exceeds a documented maximum */
+
+#define PHOSIM_MAX_SURFACES 16
+#define PHOSIM_MAX_LAYERS 8
+#define PHOSIM_MAX_SCALES 2
+#define PHOSIM_MAX_ZERNIKE 28        /* Noll j <= 28: radial order <= 6 */
+#define PHOSIM_MAX_COATED 6          /* coated surfaces with an accept-reject draw */
+
+/* surface kinds, materials, source kinds (Sec. 2.4.1, 2.2) */
+enum { PHOSIM_MIRROR = 0, PHOSIM_REFRACT = 1, PHOSIM_DETECTOR = 2 };
+enum { PHOSIM_VACUUM = 0, PHOSIM_SELLMEIER = 1, PHOSIM_SILICON = 2 };
+enum { PHOSIM_POINT = 0, PHOSIM_SERSIC = 1, PHOSIM_GAUSS = 2 };
+
+/* precision of the photon path */
+enum {
+    PHOSIM_PLAIN_FP64 = 0,   /* every step in FP64 */
+    PHOSIM_MIXED = 1         /* FP64 for positions, surface transforms and intersections; FP32 for the
+                                wavelength blur, screen-gradient deflections, source shapes, silicon
+                                conversion and diffusion; FP32 moment partials with compensated sums */
+};
+
+/* scene flags */
+#define PHOSIM_ATMOSPHERE 1u     /* apply the phase-screen layers */
+#define PHOSIM_SENSOR 2u         /* silicon conversion and diffusion; otherwise the detector-surface hit */
+
+/* record flags (phosim_photon_record.flags): bit 0 = detected; otherwise bits 8..15 hold the reason the
+   photon was dropped and bits 16..23 the index of the surface where it happened */
+#define PHOSIM_F_DETECTED 1u
+enum {
+    PHOSIM_LOST_VIGNETTED = 1, PHOSIM_LOST_MISSED = 2, PHOSIM_LOST_NEWTON = 3, PHOSIM_LOST_TIR = 4,
+    PHOSIM_LOST_COATING = 5, PHOSIM_LOST_OFF_CHIP = 6, PHOSIM_LOST_NOT_CONVERTED = 7
+};
+
+/* Scene description (Sec. 2.2 pupil and top of the atmosphere; Sec. 2.4.1 detector device; Sec. 2.4.2
+   absorption length; Sec. 2.5 diffusion).  Tables are host pointers, copied at creation. */
+typedef struct phosim_scene_desc {
+    uint64_t seed;              /* Philox4x32-10 key */
+    int32_t precision;          /* PHOSIM_PLAIN_FP64 or PHOSIM_MIXED */
+    uint32_t flags;             /* PHOSIM_ATMOSPHERE | PHOSIM_SENSOR */
+    double pupil_r_in, pupil_r_out;   /* annulus sampled on the first surface (Sec. 2.2), mm */
+    double h_top;               /* top of the atmosphere, telescope-frame z, mm (100 km) */
+    double z_entrance;          /* plane below every layer and above every optic where the raytrace starts */
+    double lambda_ref;          /* wavelength of the screen phases, nm */
+    int32_t nx, ny;             /* pixels of the chip */
+    double pixel;               /* mm */
+    double x0, y0;              /* chip centre in the detector surface frame, mm */
+    double t_si;                /* silicon thickness, mm */
+    double ell_lam0, ell_dlam;  /* absorption length table: lambda_k = ell_lam0 + k ell_dlam (nm) */
+    int32_t n_ell;              /* >= 2 */
+    const double* ell;          /* mm, linear interpolation, clamped at the ends */
+    int32_t n_sigma;            /* >= 2 */
+    const double* sigma;        /* diffusion sigma (mm) at depths k t_si / (n_sigma - 1) below the entrance */
+} phosim_scene_desc;
+
+/* One optical surface (Sec. 2.4.1, Table 1): z(r) = r^2 / (R (1 + sqrt(1 - (1 + kappa) r^2 / R^2)))
+   + sum_{i=3..10} alpha_i r^i + sum_j zern[j-1] Z_j(x / zern_rnorm, y / zern_rnorm) (Noll order and
+   normalisation), about a vertex at (pert[0], pert[1], z + pert[2]) rotated by
+   Rz(pert[5]) Ry(pert[4]) Rx(pert[3]).  R = 0 means flat.  Surfaces are met in array order. */
+typedef struct phosim_surface {
+    int32_t kind;               /* PHOSIM_MIRROR, PHOSIM_REFRACT or PHOSIM_DETECTOR (last surface only) */
+    int32_t material;           /* medium after a refracting surface / the silicon of the detector */
+    int32_t coating;            /* index of the coating table, -1 = none */
+    int32_t n_zern;             /* number of Zernike coefficients used, <= PHOSIM_MAX_ZERNIKE */
+    double R, kappa;
+    double alpha[8];            /* alpha_3 .. alpha_10 */
+    double z;
+    double r_in, r_out;         /* clear aperture radius bounds in the surface frame */
+    double pert[6];             /* dx, dy, dz (mm), tx, ty, tz (rad) */
+    double zern_rnorm;
+    double zern[PHOSIM_MAX_ZERNIKE];
+} phosim_surface;
+
+typedef struct phosim_material {
+    int32_t kind;               /* PHOSIM_VACUUM, PHOSIM_SELLMEIER (lambda in um, C in um^2), PHOSIM_SILICON */
+    double B[3], C[3];
+} phosim_material;
+
+/* transmission probability, piecewise constant in (lambda, incidence angle) (Sec. 2.4.2) */
+typedef struct phosim_coating {
+    double lam0, dlam;          /* nm */
+    double theta0, dtheta;      /* rad */
+    int32_t n_lambda, n_theta;
+    const double* table;        /* host, n_lambda x n_theta, row-major */
+} phosim_coating;
+
+/* One frozen-flow layer (Sec. 2.3.1): up to two screen scales whose gradients add. */
+typedef struct phosim_screen_scale {
+    double pixel;               /* mm */
+    int32_t n;                  /* n x n periodic screen, n >= 3 */
+    const double* phase;        /* host, row-major (row = y), rad at lambda_ref */
+} phosim_screen_scale;
+
+typedef struct phosim_layer {
+    double z;                   /* telescope-frame height, mm; layers must be given top to bottom */
+    double vx, vy;              /* wind, mm/s: the screen sampled at time t is the one at position - v t */
+    int32_t n_scales;
+    phosim_screen_scale scales[PHOSIM_MAX_SCALES];
+} phosim_layer;
+
+/* A source (Sec. 2.2): its direction's tangent-plane components, spectrum, time window and shape. */
+typedef struct phosim_source {
+    int32_t kind;               /* PHOSIM_POINT, PHOSIM_SERSIC, PHOSIM_GAUSS */
+    int32_t sed;                /* index of the SED table */
+    int32_t table;              /* Sersic radial table index */
+    int32_t pad;
+    double xi, eta;             /* n_x, n_y of the undisturbed photon */
+    double redshift;
+    double t0, t_exp;
+    double a, b, pa;            /* Sersic semi-axes at the half-light radius and position angle (rad);
+                                   PHOSIM_GAUSS: a = sigma (rad) */
+} phosim_source;
+
+/* Per-photon record, written only when a record buffer is given (debugging / parity). */
+typedef struct phosim_photon_record {
+    double x, y;                /* final position in the detector surface frame (after diffusion), mm */
+    double xc, yc;              /* lateral position where the photon converted, mm */
+    double lambda;              /* nm */
+    uint32_t flags;
+    int32_t pix;                /* y * nx + x, or -1 */
+} phosim_photon_record;
+
+/* Per-source moment sums, PHOSIM_MOMENT_WORDS doubles per source, additive across calls:
+   [0] detected count, [1] sum dx, [2] sum dy, [3] sum dx^2, [4] sum dx dy, [5] sum dy^2,
+   [6] ref_x, [7] ref_y, with dx = x - ref_x, dy = y - ref_y and (ref_x, ref_y) the detector-plane
+   position of the source's chief ray at lambda_ref (written, not added). */
+#define PHOSIM_MOMENT_WORDS 8
+
+typedef struct phosim_scene phosim_scene;
+
+/* Create a scene from its description (copies the tables).  Errors: INVALID_ARGUMENT (null pointers,
+   sizes < 2, non-positive pixel or thickness, unknown precision), OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_create_scene(const phosim_scene_desc* desc, phosim_scene** out);
+
+/* Load the surfaces in the order photons meet them (Sec. 2.4.1-2.4.2) with their media and coatings.
+   The last surface must be the only PHOSIM_DETECTOR.  At most PHOSIM_MAX_SURFACES surfaces and
+   PHOSIM_MAX_COATED coated surfaces.  Errors: INVALID_ARGUMENT, LIMIT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_load_optics(phosim_scene* scene, const phosim_surface* surfaces, int n_surfaces,
+                                 const phosim_material* materials, int n_materials,
+                                 const phosim_coating* coatings, int n_coatings);
+
+/* Load the atmosphere (Sec. 2.3): layers top to bottom; the central-difference gradient screens are
+   built on the device.  n_layers = 0 removes the atmosphere.  Errors: INVALID_ARGUMENT, LIMIT,
+   OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_load_screens(phosim_scene* scene, const phosim_layer* layers, int n_layers);
+
+/* Load the SEDs (Sec. 2.2): flux per unit wavelength at bin centres lam0 + (k + 1/2) dlam, n_sed x n_bins,
+   host, row-major.  The photon-number cumulative tables are built on the device.
+   Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_load_seds(phosim_scene* scene, const double* flux, int n_sed, int n_bins, double lam0,
+                               double dlam);
+
+/* Load Sersic radial tables (Sec. 2.2.1): radius / half-light radius at u = (k + 1/2) / n_nodes,
+   n_tables x n_nodes, host.  Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_load_sersic(phosim_scene* scene, const double* table, int n_tables, int n_nodes);
+
+/* Trace photons first[s] .. first[s] + n_photons[s] - 1 of every source s (first = NULL: from 0).
+   sources, n_photons and first are host arrays.  Photon i of source s always draws the same random
+   numbers (counter = (i, s, block), key = seed), whatever the batching.
+   image: nx * ny uint32 counts, ADDED to (device or host pointer; a host pointer is staged through a
+          scene-owned device buffer and the call returns after the copy back).
+   records: NULL or a device array of sum(n_photons) records in source order.
+   moments: NULL or a device array of n_src * PHOSIM_MOMENT_WORDS doubles; sums are added.
+   stream: a cudaStream_t (NULL = legacy default stream); all device work is ordered on it.
+   Errors: INVALID_ARGUMENT, NOT_READY, LIMIT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_trace(phosim_scene* scene, const phosim_source* sources, int n_src,
+                           const uint64_t* n_photons, const uint64_t* first, uint32_t* image,
+                           phosim_photon_record* records, double* moments, void* stream);
+
+/* Pathwise gradient (adjoint raytrace) of L = sum_s sum_k dL_dmoments[s][k] M_s[k] with respect to the
+   listed surface parameters, where M_s = (mean x, mean y, Ixx, Ixy, Iyy) of the detected photons of
+   source s (central second moments).  Common random numbers, accept decisions of the forward pass held.
+   param_surface[p], param_field[p]: field 0..5 = pert[0..5], field 100 + j = zern[j].
+   dL_dmoments: host, n_src x 5.  grad: host, n_src x n_params, written (per-source contributions).
+   moments_out: NULL or host n_src x 6 (count, mean x, mean y, Ixx, Ixy, Iyy).
+   Errors: INVALID_ARGUMENT, NOT_READY, LIMIT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_grad(phosim_scene* scene, const phosim_source* sources, int n_src,
+                          const uint64_t* n_photons, const double* dL_dmoments, const int32_t* param_surface,
+                          const int32_t* param_field, int n_params, double* grad, double* moments_out,
+                          void* stream);
+
+/* Launch shape of the trace kernel: threads per block and photons per warp tile (0 = keep current). */
+phosim_status phosim_set_schedule(phosim_scene* scene, int threads_per_block, int tile_photons);
+
+/* Totals of the last phosim_trace: out[0] = photons traced, out[1] = detected, out[1 + r] = dropped for
+   reason r = 1..7 (PHOSIM_LOST_*).  n >= 9.  Synchronises the scene's last stream. */
+phosim_status phosim_get_counters(phosim_scene* scene, uint64_t* out, int n);
+
+void phosim_destroy_scene(phosim_scene* scene);
+const char* phosim_status_string(phosim_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHOSIM_H */

@@ -1,0 +1,593 @@
+// Host side of the phosim C ABI: scene construction, table preparation kernels and the trace launch.
+//
+// Loads copy the caller's host tables to device memory owned by the scene and prepare the forms the
+// photon kernel reads: central-difference gradient screens (Sec. 2.3.2), integer thresholds of the
+// photon-number cumulative SED tables (Sec. 2.2), surface frames and Zernike figures as monomials
+// (Sec. 2.4.1).  phosim_trace uploads the source list and launches one persistent trace kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "phosim_device.cuh"
+#include "phosim_scene.hpp"
+
+using namespace phosim;
+
+namespace phosim {
+void free_all(std::vector<void*>& v) {
+    for (void* p : v) cudaFree(p);
+    v.clear();
+}
+}  // namespace phosim
+
+namespace {
+
+#define CU(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            (void)cudaGetLastError();                       \
+            return e_ == cudaErrorMemoryAllocation ? PHOSIM_ERR_OUT_OF_MEMORY : PHOSIM_ERR_CUDA; \
+        }                                                   \
+    } while (0)
+
+template <class T>
+phosim_status upload(std::vector<void*>& owner, const T* host, size_t n, T** out) {
+    void* p = nullptr;
+    CU(cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(T)));
+    owner.push_back(p);
+    if (n) CU(cudaMemcpy(p, host, n * sizeof(T), cudaMemcpyHostToDevice));
+    *out = (T*)p;
+    return PHOSIM_OK;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+// ----------------------------------------------------------------------------------------- Zernike figure
+// Noll index -> radial order n, |m| and whether the term is the cosine one (even j) or the sine one.
+void noll(int j, int& n, int& am, bool& cosine) {
+    n = (int)std::ceil((std::sqrt(8.0 * j + 1.0) - 3.0) / 2.0);
+    while (n * (n + 1) / 2 >= j) --n;            // guard the floating estimate
+    while ((n + 1) * (n + 2) / 2 < j) ++n;
+    const int k = j - n * (n + 1) / 2 - 1;       // position within order n, 0..n
+    am = (n % 2 == 0) ? 2 * ((k + 1) / 2) : 2 * (k / 2) + 1;
+    cosine = (j % 2 == 0);
+}
+
+double fact(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
+double binom(int n, int k) { return fact(n) / (fact(k) * fact(n - k)); }
+
+// coefficients P[b][a] of x^a y^b of Z_j(x, y) in coordinates normalised to the unit disk
+void zernike_monomials(int j, double P[7][7]) {
+    int n, am;
+    bool cosine;
+    noll(j, n, am, cosine);
+    double A[7][7] = {}, B[7][7] = {};
+    // A = sum_s c_s (x^2 + y^2)^((n - am)/2 - s): the radial polynomial divided by rho^am
+    for (int s = 0; s <= (n - am) / 2; ++s) {
+        const double c = ((s % 2) ? -1.0 : 1.0) * fact(n - s) /
+                         (fact(s) * fact((n + am) / 2 - s) * fact((n - am) / 2 - s));
+        const int q = (n - am) / 2 - s;
+        for (int t = 0; t <= q; ++t) A[2 * (q - t)][2 * t] += c * binom(q, t);
+    }
+    // B = Re (x + i y)^am for the cosine term, Im (x + i y)^am for the sine term
+    for (int t = 0; t <= am; ++t) {
+        const double c = binom(am, t);
+        if (t % 2 == 0 && (am == 0 || cosine)) B[t][am - t] += ((t / 2) % 2 ? -1.0 : 1.0) * c;
+        if (t % 2 == 1 && am > 0 && !cosine) B[t][am - t] += (((t - 1) / 2) % 2 ? -1.0 : 1.0) * c;
+    }
+    const double N = am == 0 ? std::sqrt((double)n + 1.0) : std::sqrt(2.0 * (n + 1.0));
+    for (int b = 0; b < 7; ++b)
+        for (int a = 0; a < 7; ++a) P[b][a] = 0.0;
+    for (int b1 = 0; b1 < 7; ++b1)
+        for (int a1 = 0; a1 + b1 < 7; ++a1) {
+            if (A[b1][a1] == 0.0) continue;
+            for (int b2 = 0; b1 + b2 < 7; ++b2)
+                for (int a2 = 0; a1 + a2 + b1 + b2 < 7; ++a2)
+                    P[b1 + b2][a1 + a2] += N * A[b1][a1] * B[b2][a2];
+        }
+}
+
+// R = Rz(tz) Ry(ty) Rx(tx) takes surface-frame directions to the telescope frame; M = R^T
+void rotation(const double* pert, double M[9]) {
+    const double cx = std::cos(pert[3]), sx = std::sin(pert[3]);
+    const double cy = std::cos(pert[4]), sy = std::sin(pert[4]);
+    const double cz = std::cos(pert[5]), sz = std::sin(pert[5]);
+    const double R[3][3] = {{cz * cy, cz * sy * sx - sz * cx, cz * sy * cx + sz * sx},
+                            {sz * cy, sz * sy * sx + cz * cx, sz * sy * cx - cz * sx},
+                            {-sy, cy * sx, cy * cx}};
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) M[3 * i + k] = R[k][i];
+}
+
+phosim_status build_surface(const phosim_surface& s, DSurface& d) {
+    std::memset(&d, 0, sizeof(d));
+    d.kind = s.kind;
+    d.material = s.material;
+    d.coating = s.coating;
+    d.coat_slot = -1;
+    int flags = 0;
+    if (s.R != 0.0) {
+        flags |= SF_CONIC;
+        d.c = 1.0 / s.R;
+        d.k1c2 = (1.0 + s.kappa) / (s.R * s.R);
+    }
+    for (int i = 0; i < 4; ++i) {
+        d.ao[i] = s.alpha[2 * i];        // alpha_3, 5, 7, 9
+        d.ae[i] = s.alpha[2 * i + 1];    // alpha_4, 6, 8, 10
+        if (d.ao[i] != 0.0) flags |= SF_ODD;
+        if (d.ae[i] != 0.0) flags |= SF_EVEN;
+    }
+    if (s.n_zern > 0 && s.zern_rnorm > 0.0) {
+        double P[7][7] = {}, Pj[7][7];
+        bool any = false;
+        for (int j = 1; j <= s.n_zern; ++j) {
+            if (s.zern[j - 1] == 0.0) continue;
+            any = true;
+            zernike_monomials(j, Pj);
+            for (int b = 0; b < 7; ++b)
+                for (int a = 0; a + b < 7; ++a) P[b][a] += s.zern[j - 1] * Pj[b][a];
+        }
+        if (any) {
+            flags |= SF_ZERN;
+            d.zinv = 1.0 / s.zern_rnorm;
+            int off = 0;
+            for (int b = 0; b < 7; ++b)
+                for (int a = 0; a + b < 7; ++a) d.zp[off++] = P[b][a];
+        }
+    }
+    if (!(flags & (SF_CONIC | SF_EVEN | SF_ODD | SF_ZERN))) flags |= SF_FLAT_ONLY;
+    d.flags = flags;
+    rotation(s.pert, d.M);
+    d.o[0] = s.pert[0];
+    d.o[1] = s.pert[1];
+    d.o[2] = s.z + s.pert[2];
+    d.r_in2 = s.r_in * s.r_in;
+    d.r_out2 = s.r_out * s.r_out;
+    return PHOSIM_OK;
+}
+
+// ----------------------------------------------------------------------------------------- device kernels
+// central-difference gradient of a periodic phase screen, rad per mm (Sec. 2.3.2)
+__global__ void gradient_screen_kernel(const double* __restrict__ ph, int n, double two_pix, double2* g64, float2* g32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= n) return;
+    const int ip = i + 1 == n ? 0 : i + 1, im = i == 0 ? n - 1 : i - 1;
+    const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
+    const size_t r = (size_t)j * n;
+    const double gx = (ph[r + ip] - ph[r + im]) / two_pix;
+    const double gy = (ph[(size_t)jp * n + i] - ph[(size_t)jm * n + i]) / two_pix;
+    g64[r + i] = make_double2(gx, gy);
+    g32[r + i] = make_float2((float)gx, (float)gy);
+}
+
+// Photon-number cumulative table of each SED (flux x wavelength x bin width, summed in bin order with
+// IEEE round-to-nearest operations and no contraction), turned into integer thresholds: bin k is taken by
+// the draw w when ((w + 1/2) 2^-32) < cdf_k, i.e. w < ceil(cdf_k 2^32 - 1/2).
+__global__ void sed_threshold_kernel(const double* __restrict__ flux, int n_sed, int n_bins, double lam0, double dlam,
+                                     double* cum, unsigned long long* thr) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sed) return;
+    const double* f = flux + (size_t)s * n_bins;
+    double* c = cum + (size_t)s * n_bins;
+    double acc = 0.0;
+    for (int k = 0; k < n_bins; ++k) {
+        const double centre = __dadd_rn(lam0, __dmul_rn((double)k + 0.5, dlam));
+        const double pk = __dmul_rn(__dmul_rn(f[k], centre), dlam);
+        acc = __dadd_rn(acc, pk);
+        c[k] = acc;
+    }
+    unsigned long long* t = thr + (size_t)s * (n_bins - 1);
+    for (int k = 0; k < n_bins - 1; ++k) {
+        const double ck = __ddiv_rn(c[k], acc);
+        const double X = __dmul_rn(ck, 4294967296.0);
+        t[k] = (unsigned long long)ceil(__dsub_rn(X, 0.5));
+    }
+}
+
+}  // namespace
+
+// =========================================================================================================
+extern "C" {
+
+const char* phosim_status_string(phosim_status s) {
+    switch (s) {
+        case PHOSIM_OK: return "ok";
+        case PHOSIM_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case PHOSIM_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case PHOSIM_ERR_CUDA: return "CUDA error";
+        case PHOSIM_ERR_UNSUPPORTED: return "unsupported";
+        case PHOSIM_ERR_NOT_READY: return "scene not ready (optics or SEDs not loaded)";
+        case PHOSIM_ERR_LIMIT: return "size exceeds a library maximum";
+        default: return "unknown status";
+    }
+}
+
+phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out) {
+    if (!d || !out) return PHOSIM_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (d->precision != PHOSIM_PLAIN_FP64 && d->precision != PHOSIM_MIXED) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (d->nx <= 0 || d->ny <= 0 || (int64_t)d->nx * d->ny > (int64_t)1 << 31) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!(d->pixel > 0.0) || !(d->t_si > 0.0) || !(d->lambda_ref > 0.0) || !(d->ell_dlam > 0.0))
+        return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (d->n_ell < 2 || d->n_sigma < 2 || !d->ell || !d->sigma) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!(d->pupil_r_out > d->pupil_r_in) || d->pupil_r_in < 0.0) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!(d->h_top > d->z_entrance) || !is_finite(d->h_top) || !is_finite(d->z_entrance)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < d->n_ell; ++i) if (!(d->ell[i] > 0.0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < d->n_sigma; ++i) if (!(d->sigma[i] >= 0.0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    phosim_scene* sc = new (std::nothrow) phosim_scene();
+    if (!sc) return PHOSIM_ERR_OUT_OF_MEMORY;
+    std::memset(&sc->base, 0, sizeof(sc->base));
+    TraceParams& P = sc->base;
+    P.k0 = (uint32_t)d->seed;
+    P.k1 = (uint32_t)(d->seed >> 32);
+    P.flags = d->flags;
+    P.pr_in2 = d->pupil_r_in * d->pupil_r_in;
+    P.pr_dr2 = d->pupil_r_out * d->pupil_r_out - P.pr_in2;
+    P.h_top = d->h_top;
+    P.z_ent = d->z_entrance;
+    P.lam_ref = d->lambda_ref;
+    P.kick0 = d->lambda_ref * 1e-6 / (2.0 * M_PI);
+    P.nx = d->nx; P.ny = d->ny;
+    P.pixel = d->pixel; P.inv_pixel = 1.0 / d->pixel;
+    P.xlo = d->x0 - 0.5 * d->nx * d->pixel;
+    P.ylo = d->y0 - 0.5 * d->ny * d->pixel;
+    P.t_si = d->t_si;
+    P.ell_lam0 = d->ell_lam0; P.inv_ell_dlam = 1.0 / d->ell_dlam;
+    P.n_ell = d->n_ell; P.n_sig = d->n_sigma;
+    P.sig_scale = (d->n_sigma - 1) / d->t_si;
+    sc->precision = d->precision;
+    std::vector<float> f(d->ell, d->ell + d->n_ell), g(d->sigma, d->sigma + d->n_sigma);
+    double* pd;
+    float* pf;
+    phosim_status st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sc->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete sc;
+        return PHOSIM_ERR_CUDA;
+    }
+    if ((st = upload(sc->table_mem, d->ell, (size_t)d->n_ell, &pd)) != PHOSIM_OK) goto fail;
+    P.ell = pd;
+    if ((st = upload(sc->table_mem, f.data(), f.size(), &pf)) != PHOSIM_OK) goto fail;
+    P.ell32 = pf;
+    if ((st = upload(sc->table_mem, d->sigma, (size_t)d->n_sigma, &pd)) != PHOSIM_OK) goto fail;
+    P.sig = pd;
+    if ((st = upload(sc->table_mem, g.data(), g.size(), &pf)) != PHOSIM_OK) goto fail;
+    P.sig32 = pf;
+    if (cudaMalloc(&sc->d_counters, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = PHOSIM_ERR_OUT_OF_MEMORY;
+        goto fail;
+    }
+    cudaMemset(sc->d_counters, 0, 16 * sizeof(unsigned long long));
+    *out = sc;
+    return PHOSIM_OK;
+fail:
+    phosim_destroy_scene(sc);
+    return st;
+}
+
+void phosim_destroy_scene(phosim_scene* sc) {
+    if (!sc) return;
+    if (sc->last_stream) cudaStreamSynchronize(sc->last_stream);
+    free_all(sc->table_mem);
+    free_all(sc->optics_mem);
+    free_all(sc->screen_mem);
+    free_all(sc->sed_mem);
+    free_all(sc->sersic_mem);
+    cudaFree(sc->d_src);
+    cudaFree(sc->d_prefix);
+    cudaFree(sc->d_counters);
+    cudaFree(sc->d_stage);
+    (void)cudaGetLastError();
+    delete sc;
+}
+
+phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, int n_surf, const phosim_material* mats,
+                                 int n_mat, const phosim_coating* coats, int n_coat) {
+    if (!sc || !surf || n_surf < 1 || (n_mat > 0 && !mats) || (n_coat > 0 && !coats) || n_mat < 1 || n_coat < 0)
+        return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (n_surf > PHOSIM_MAX_SURFACES || n_mat > kMaxMaterials || n_coat > kMaxCoatings) return PHOSIM_ERR_LIMIT;
+    for (int i = 0; i < n_surf; ++i) {
+        const phosim_surface& s = surf[i];
+        const bool last = i == n_surf - 1;
+        if (s.kind < PHOSIM_MIRROR || s.kind > PHOSIM_DETECTOR) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if ((s.kind == PHOSIM_DETECTOR) != last) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (s.material < 0 || s.material >= n_mat) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (s.coating < -1 || s.coating >= n_coat) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (s.n_zern < 0 || s.n_zern > PHOSIM_MAX_ZERNIKE) return PHOSIM_ERR_LIMIT;
+        if (!is_finite(s.R) || !is_finite(s.kappa) || !is_finite(s.z) || s.r_in < 0.0 || !(s.r_out >= s.r_in))
+            return PHOSIM_ERR_INVALID_ARGUMENT;
+    }
+    for (int k = 0; k < n_mat; ++k)
+        if (mats[k].kind < PHOSIM_VACUUM || mats[k].kind > PHOSIM_SILICON) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int k = 0; k < n_coat; ++k)
+        if (!coats[k].table || coats[k].n_lambda < 1 || coats[k].n_theta < 1 || !(coats[k].dlam > 0.0) ||
+            !(coats[k].dtheta > 0.0))
+            return PHOSIM_ERR_INVALID_ARGUMENT;
+    TraceParams P = sc->base;
+    int coated = 0;
+    for (int i = 0; i < n_surf; ++i) {
+        build_surface(surf[i], P.surf[i]);
+        if (surf[i].coating >= 0 && surf[i].kind != PHOSIM_DETECTOR) {
+            if (coated >= PHOSIM_MAX_COATED) return PHOSIM_ERR_LIMIT;
+            P.surf[i].coat_slot = coated++;
+        }
+    }
+    P.pupil_surf = P.surf[0];
+    P.pupil_surf.flags &= ~SF_ZERN;
+    if (!(P.pupil_surf.flags & (SF_CONIC | SF_EVEN | SF_ODD))) P.pupil_surf.flags |= SF_FLAT_ONLY;
+    P.pupil_z = surf[0].z;
+    P.n_surf = n_surf;
+    P.n_coated = coated;
+    P.n_mat = n_mat;
+    for (int k = 0; k < n_mat; ++k) {
+        P.mat[k].kind = mats[k].kind;
+        for (int q = 0; q < 3; ++q) { P.mat[k].B[q] = mats[k].B[q]; P.mat[k].C[q] = mats[k].C[q]; }
+    }
+    std::vector<void*> mem;
+    for (int k = 0; k < n_coat; ++k) {
+        double* d;
+        phosim_status st = upload(mem, coats[k].table, (size_t)coats[k].n_lambda * coats[k].n_theta, &d);
+        if (st != PHOSIM_OK) { free_all(mem); return st; }
+        DCoating& C = P.coat[k];
+        C.lam0 = coats[k].lam0; C.inv_dlam = 1.0 / coats[k].dlam;
+        C.th0 = coats[k].theta0; C.inv_dth = 1.0 / coats[k].dtheta;
+        C.nl = coats[k].n_lambda; C.nt = coats[k].n_theta;
+        C.T = d;
+    }
+    P.n_coat = n_coat;
+    free_all(sc->optics_mem);
+    sc->optics_mem = mem;
+    sc->base = P;
+    sc->surfaces.assign(surf, surf + n_surf);
+    sc->optics_loaded = true;
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, int n_layers) {
+    if (!sc || n_layers < 0 || (n_layers > 0 && !layers)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (n_layers > PHOSIM_MAX_LAYERS) return PHOSIM_ERR_LIMIT;
+    for (int k = 0; k < n_layers; ++k) {
+        const phosim_layer& L = layers[k];
+        if (L.n_scales < 1 || L.n_scales > PHOSIM_MAX_SCALES) return PHOSIM_ERR_LIMIT;
+        if (k > 0 && !(L.z < layers[k - 1].z)) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (!is_finite(L.z) || !is_finite(L.vx) || !is_finite(L.vy)) return PHOSIM_ERR_INVALID_ARGUMENT;
+        for (int q = 0; q < L.n_scales; ++q)
+            if (L.scales[q].n < 3 || !(L.scales[q].pixel > 0.0) || !L.scales[q].phase) return PHOSIM_ERR_INVALID_ARGUMENT;
+    }
+    TraceParams P = sc->base;
+    std::vector<void*> mem;
+    for (int k = 0; k < n_layers; ++k) {
+        const phosim_layer& L = layers[k];
+        DLayer& D = P.layer[k];
+        D.z = L.z; D.vx = L.vx; D.vy = L.vy; D.n_scales = L.n_scales;
+        for (int q = 0; q < L.n_scales; ++q) {
+            const phosim_screen_scale& S = L.scales[q];
+            const size_t nn = (size_t)S.n * S.n;
+            double* ph = nullptr;
+            void *g64 = nullptr, *g32 = nullptr;
+            cudaError_t e = cudaMalloc(&ph, nn * sizeof(double));
+            if (e == cudaSuccess) e = cudaMalloc(&g64, nn * sizeof(double2));
+            if (e == cudaSuccess) { mem.push_back(g64); e = cudaMalloc(&g32, nn * sizeof(float2)); }
+            if (e == cudaSuccess) { mem.push_back(g32); e = cudaMemcpy(ph, S.phase, nn * sizeof(double), cudaMemcpyHostToDevice); }
+            if (e == cudaSuccess) {
+                gradient_screen_kernel<<<dim3((S.n + 255) / 256, S.n), 256>>>(ph, S.n, 2.0 * S.pixel, (double2*)g64, (float2*)g32);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            cudaFree(ph);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                free_all(mem);
+                return e == cudaErrorMemoryAllocation ? PHOSIM_ERR_OUT_OF_MEMORY : PHOSIM_ERR_CUDA;
+            }
+            D.s[q].n = S.n;
+            D.s[q].inv_pix = 1.0 / S.pixel;
+            D.s[q].g64 = (const double2*)g64;
+            D.s[q].g32 = (const float2*)g32;
+        }
+    }
+    P.n_layers = n_layers;
+    free_all(sc->screen_mem);
+    sc->screen_mem = mem;
+    sc->base = P;
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_load_seds(phosim_scene* sc, const double* flux, int n_sed, int n_bins, double lam0, double dlam) {
+    if (!sc || !flux || n_sed < 1 || n_bins < 2 || !(dlam > 0.0) || !is_finite(lam0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    const size_t n = (size_t)n_sed * n_bins;
+    double total = 0.0;
+    for (int s = 0; s < n_sed; ++s) {
+        double row = 0.0;
+        for (int k = 0; k < n_bins; ++k) {
+            const double v = flux[(size_t)s * n_bins + k];
+            if (!(v >= 0.0) || !is_finite(v)) return PHOSIM_ERR_INVALID_ARGUMENT;
+            row += v;
+        }
+        if (!(row > 0.0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+        total += row;
+    }
+    std::vector<void*> mem;
+    double *d_flux = nullptr, *d_cum = nullptr;
+    unsigned long long* d_thr = nullptr;
+    cudaError_t e = cudaMalloc(&d_flux, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d_cum, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d_thr, (size_t)n_sed * (n_bins - 1) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(d_flux, flux, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        sed_threshold_kernel<<<(n_sed + 127) / 128, 128>>>(d_flux, n_sed, n_bins, lam0, dlam, d_cum, d_thr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_flux);
+    cudaFree(d_cum);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaFree(d_thr);
+        return e == cudaErrorMemoryAllocation ? PHOSIM_ERR_OUT_OF_MEMORY : PHOSIM_ERR_CUDA;
+    }
+    free_all(sc->sed_mem);
+    sc->sed_mem.push_back(d_thr);
+    sc->base.thr = d_thr;
+    sc->base.n_bins = n_bins;
+    sc->base.sed_lam0 = lam0;
+    sc->base.sed_dlam = dlam;
+    sc->n_sed = n_sed;
+    sc->seds_loaded = true;
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_load_sersic(phosim_scene* sc, const double* table, int n_tables, int n_nodes) {
+    if (!sc || !table || n_tables < 1 || n_nodes < 2) return PHOSIM_ERR_INVALID_ARGUMENT;
+    const size_t n = (size_t)n_tables * n_nodes;
+    for (size_t i = 0; i < n; ++i) if (!(table[i] >= 0.0) || !is_finite(table[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
+    std::vector<float> f(table, table + n);
+    std::vector<void*> mem;
+    double* d;
+    float* df;
+    phosim_status st = upload(mem, table, n, &d);
+    if (st == PHOSIM_OK) st = upload(mem, f.data(), n, &df);
+    if (st != PHOSIM_OK) { free_all(mem); return st; }
+    free_all(sc->sersic_mem);
+    sc->sersic_mem = mem;
+    sc->base.sersic = d;
+    sc->base.sersic32 = df;
+    sc->base.sersic_K = n_nodes;
+    sc->sersic_tables = n_tables;
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_set_schedule(phosim_scene* sc, int threads, int tile) {
+    if (!sc || threads < 0 || tile < 0) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (threads) {
+        if (threads % 32 || threads > 256) return PHOSIM_ERR_INVALID_ARGUMENT;
+        sc->threads = threads;
+    }
+    if (tile) {
+        if (tile > (1 << 20)) return PHOSIM_ERR_LIMIT;
+        sc->tile_photons = tile;
+    }
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_get_counters(phosim_scene* sc, uint64_t* out, int n) {
+    if (!sc || !out || n < kNumCounters) return PHOSIM_ERR_INVALID_ARGUMENT;
+    unsigned long long h[kNumCounters];
+    CU(cudaStreamSynchronize(sc->last_stream));
+    CU(cudaMemcpy(h, sc->d_counters + 1, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < kNumCounters; ++k) out[k] = h[k];
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src, const uint64_t* n_photons,
+                           const uint64_t* first, uint32_t* image, phosim_photon_record* records, double* moments,
+                           void* stream) {
+    if (!sc || n_src < 0 || (n_src > 0 && (!src || !n_photons)) || !image) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool mixed = sc->precision == PHOSIM_MIXED;
+    // launch shape
+    int per_sm = 0;
+    CU(trace_occupancy(mixed, sc->threads, &per_sm));
+    if (per_sm < 1) per_sm = 1;
+    const int blocks = sc->sm_count * per_sm;
+    const uint64_t warps = (uint64_t)blocks * (sc->threads / 32);
+    uint64_t total = 0;
+    for (int s = 0; s < n_src; ++s) total += n_photons[s];
+    uint64_t T = sc->tile_photons;
+    if (!T) {
+        T = total / (warps * 8);
+        T = std::min<uint64_t>(1024, std::max<uint64_t>(32, (T + 31) / 32 * 32));
+    }
+    // sources and per-source tile prefix
+    std::vector<DSource> hs((size_t)n_src);
+    std::vector<unsigned long long> prefix((size_t)n_src + 1, 0);
+    uint64_t rec = 0;
+    for (int s = 0; s < n_src; ++s) {
+        const phosim_source& q = src[s];
+        if (q.kind < PHOSIM_POINT || q.kind > PHOSIM_GAUSS) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (q.sed < 0 || q.sed >= sc->n_sed) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (q.kind == PHOSIM_SERSIC && (q.table < 0 || q.table >= sc->sersic_tables)) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (!is_finite(q.xi) || !is_finite(q.eta) || q.xi * q.xi + q.eta * q.eta >= 1.0 || !(q.redshift > -1.0))
+            return PHOSIM_ERR_INVALID_ARGUMENT;
+        DSource& d = hs[s];
+        std::memset(&d, 0, sizeof(d));
+        d.kind = q.kind; d.sed = q.sed; d.table = q.table;
+        d.xi = q.xi; d.eta = q.eta; d.zfac = 1.0 + q.redshift; d.t0 = q.t0; d.t_exp = q.t_exp;
+        d.a = q.a; d.b = q.b; d.cpa = std::cos(q.pa); d.spa = std::sin(q.pa);
+        d.first = first ? first[s] : 0;
+        d.count = n_photons[s];
+        d.rec_off = rec;
+        rec += n_photons[s];
+        prefix[s + 1] = prefix[s] + (n_photons[s] + T - 1) / T;
+    }
+    if (n_src == 0 || total == 0) return PHOSIM_OK;
+    if (sc->cap_src < (size_t)n_src) {
+        cudaFree(sc->d_src);
+        cudaFree(sc->d_prefix);
+        sc->d_src = nullptr; sc->d_prefix = nullptr; sc->cap_src = 0;
+        CU(cudaMalloc(&sc->d_src, (size_t)n_src * sizeof(DSource)));
+        CU(cudaMalloc(&sc->d_prefix, ((size_t)n_src + 1) * sizeof(unsigned long long)));
+        sc->cap_src = n_src;
+    }
+    // image: a pointer the device cannot use as device memory is staged through a scene buffer
+    cudaPointerAttributes attr;
+    bool host_image = false;
+    if (cudaPointerGetAttributes(&attr, image) != cudaSuccess) {
+        (void)cudaGetLastError();
+        host_image = true;
+    } else {
+        host_image = attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
+    }
+    const size_t img_bytes = (size_t)sc->base.nx * sc->base.ny * sizeof(uint32_t);
+    uint32_t* d_image = image;
+    if (host_image) {
+        if (sc->cap_stage < img_bytes) {
+            cudaFree(sc->d_stage);
+            sc->d_stage = nullptr; sc->cap_stage = 0;
+            CU(cudaMalloc(&sc->d_stage, img_bytes));
+            sc->cap_stage = img_bytes;
+        }
+        d_image = sc->d_stage;
+        CU(cudaMemcpyAsync(d_image, image, img_bytes, cudaMemcpyHostToDevice, st));
+    }
+    CU(cudaMemcpyAsync(sc->d_src, hs.data(), hs.size() * sizeof(DSource), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(sc->d_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(sc->d_counters, 0, (1 + kNumCounters) * sizeof(unsigned long long), st));
+    TraceParams P = sc->base;
+    P.sources = sc->d_src;
+    P.tile_prefix = sc->d_prefix;
+    P.n_src = n_src;
+    P.tile_photons = (uint32_t)T;
+    P.n_tiles = prefix[n_src];
+    P.tile_counter = sc->d_counters;
+    P.counters = sc->d_counters + 1;
+    P.image = d_image;
+    P.moments = moments;
+    P.records = records;
+    CU(launch_chief_rays(P, sc->d_src, n_src, moments, st));
+    CU(launch_trace(P, mixed, blocks, sc->threads, st));
+    sc->last_stream = st;
+    if (host_image) {
+        CU(cudaMemcpyAsync(image, d_image, img_bytes, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src, const uint64_t* n_photons,
+                          const double* dL, const int32_t* ps, const int32_t* pf, int n_params, double* grad,
+                          double* moments_out, void* stream) {
+    (void)sc; (void)src; (void)n_src; (void)n_photons; (void)dL; (void)ps; (void)pf; (void)n_params;
+    (void)grad; (void)moments_out; (void)stream;
+    return PHOSIM_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+// Device-side data layout and per-photon physics of the GB300 photon Monte Carlo library.
+//
+// One thread follows one photon through Sec. 2 of Peterson et al. (2015): sampling (Sec. 2.2), the
+// frozen-flow screen layers (Sec. 2.3), the surfaces (Sec. 2.4.1-2.4.2), the silicon sensor and the
+// pixel (Sec. 2.4.2, 2.5).  Scene constants travel in the kernel parameter block (constant bank), so every
+// per-surface read is a uniform constant-cache hit; screens and tables are read through the L1/L2 path.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "phosim.h"
+
+namespace phosim {
+
+constexpr int kMaxMaterials = 8;
+constexpr int kMaxCoatings = 8;
+constexpr int kZPoly = 28;                 // monomials x^a y^b, a + b <= 6
+
+enum SurfFlags : int { SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FLAT_ONLY = 16 };
+
+struct DSurface {
+    int kind, material, coating, coat_slot;   // coat_slot: index of this surface's accept draw, -1 none
+    int flags, pad0, pad1, pad2;
+    double c, k1c2;                           // 1/R, (1 + kappa) / R^2
+    double ae[4];                             // alpha_4, alpha_6, alpha_8, alpha_10
+    double ao[4];                             // alpha_3, alpha_5, alpha_7, alpha_9
+    double M[9];                              // telescope -> surface frame rotation (row-major)
+    double o[3];                              // displaced vertex in the telescope frame
+    double r_in2, r_out2;
+    double zinv;                              // 1 / zern_rnorm
+    double zp[kZPoly];                        // sum_j c_j Z_j as monomials of (x zinv, y zinv), row b = y power
+};
+
+struct DMaterial {
+    int kind, pad;
+    double B[3], C[3];
+};
+
+struct DCoating {
+    double lam0, inv_dlam, th0, inv_dth;
+    int nl, nt, pad0, pad1;
+    const double* T;                          // nl x nt
+};
+
+struct DScale {
+    int n, pad;
+    double inv_pix;
+    const double2* g64;                       // central-difference gradient (rad / mm), n x n
+    const float2* g32;
+};
+
+struct DLayer {
+    double z, vx, vy;
+    int n_scales, pad;
+    DScale s[PHOSIM_MAX_SCALES];
+};
+
+struct DSource {
+    int kind, sed, table, pad;
+    double xi, eta, zfac, t0, t_exp, a, b, cpa, spa;
+    double ref_x, ref_y;
+    uint64_t first, count, rec_off;           // photons [first, first + count); record index of the first
+};
+
+// counters: [0] traced, [1] detected, [1 + r] dropped for reason r
+constexpr int kNumCounters = 9;
+
+struct TraceParams {
+    // scene
+    uint32_t k0, k1;                          // Philox key
+    uint32_t flags;
+    int n_surf, n_layers, n_coated, n_mat, n_coat;
+    double pr_in2, pr_dr2;                    // pupil annulus
+    double h_top, z_ent;
+    double lam_ref, kick0;                    // kick0 = lambda_ref [mm] / 2 pi
+    double pupil_z;                           // nominal vertex height of the first surface
+    DSurface pupil_surf;                      // its nominal shape (no figure error, no misalignment)
+    DSurface surf[PHOSIM_MAX_SURFACES];
+    DMaterial mat[kMaxMaterials];
+    DCoating coat[kMaxCoatings];
+    DLayer layer[PHOSIM_MAX_LAYERS];
+    // sensor / detector
+    int nx, ny, n_ell, n_sig;
+    double pixel, inv_pixel, xlo, ylo, t_si, ell_lam0, inv_ell_dlam, sig_scale;
+    const double* ell;
+    const float* ell32;
+    const double* sig;
+    const float* sig32;
+    // spectra, shapes
+    int n_bins, sersic_K;
+    double sed_lam0, sed_dlam;
+    const unsigned long long* thr;            // n_sed x (n_bins - 1) integer thresholds on the bin draw
+    const double* sersic;
+    const float* sersic32;
+    // work and outputs: tile t of the launch is tile t - tile_prefix[s] of the source s with
+    // tile_prefix[s] <= t < tile_prefix[s + 1]; a tile holds tile_photons consecutive photons
+    const DSource* sources;
+    const unsigned long long* tile_prefix;
+    int n_src;
+    uint32_t tile_photons;
+    uint64_t n_tiles;
+    unsigned long long* tile_counter;
+    unsigned long long* counters;
+    uint32_t* image;
+    double* moments;
+    phosim_photon_record* records;
+};
+
+// ------------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two 32x32 multiplications per round.
+// ------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// slot map of one photon's random words: counter = (photon lo, photon hi, source, block)
+//   block 0: pupil r, pupil phi, wavelength bin, wavelength blur
+//   block 1: time, shape a, shape b, conversion
+//   block 2: diffusion a, diffusion b, coated surface 0, coated surface 1
+//   block 3: coated surfaces 2..5
+__device__ __forceinline__ double u64of(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
+__device__ __forceinline__ float u32of(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+
+// ------------------------------------------------------------------------------------------------------
+// surface shape (Sec. 2.4.1)
+// ------------------------------------------------------------------------------------------------------
+// Zernike figure as a bivariate polynomial of degree 6 in normalised coordinates (u, v).
+__device__ __forceinline__ void zern_eval(const double* __restrict__ zp, double u, double v, double& z, double& zu,
+                                          double& zv) {
+    // rows b = 0..6 hold the x-polynomial of y^b, degree 6 - b, ascending powers of x
+    double q[7], dq[7];
+    int off = 0;
+#pragma unroll
+    for (int b = 0; b <= 6; ++b) {
+        const int deg = 6 - b;
+        double acc = zp[off + deg], dacc = 0.0;
+#pragma unroll
+        for (int a = deg - 1; a >= 0; --a) {
+            dacc = fma(dacc, u, acc);
+            acc = fma(acc, u, zp[off + a]);
+        }
+        q[b] = acc;
+        dq[b] = dacc;
+        off += deg + 1;
+    }
+    double zz = q[6], zzu = dq[6], zzv = 0.0;
+#pragma unroll
+    for (int b = 5; b >= 0; --b) {
+        zzv = fma(zzv, v, zz);
+        zz = fma(zz, v, q[b]);
+        zzu = fma(zzu, v, dq[b]);
+    }
+    z = zz; zu = zzu; zv = zzv;
+}
+
+// sag and its partial derivatives in the surface frame; false outside the conic's domain
+__device__ __forceinline__ bool sag(const DSurface& S, double x, double y, double& z, double& zx, double& zy) {
+    const double r2 = x * x + y * y;
+    double g = 0.0;   // (1/r) dz/dr
+    z = 0.0;
+    if (S.flags & SF_CONIC) {
+        const double arg = 1.0 - S.k1c2 * r2;
+        if (arg < 0.0) return false;
+        const double sq = sqrt(arg);
+        z = S.c * r2 / (1.0 + sq);
+        g = S.c / sq;
+    }
+    if (S.flags & SF_EVEN) {
+        const double pe = fma(r2, fma(r2, fma(r2, S.ae[3], S.ae[2]), S.ae[1]), S.ae[0]);
+        z = fma(r2 * r2, pe, z);
+        const double pd = fma(r2, fma(r2, fma(r2, 10.0 * S.ae[3], 8.0 * S.ae[2]), 6.0 * S.ae[1]), 4.0 * S.ae[0]);
+        g = fma(r2, pd, g);
+    }
+    if (S.flags & SF_ODD) {
+        const double r = sqrt(r2);
+        const double po = fma(r2, fma(r2, fma(r2, S.ao[3], S.ao[2]), S.ao[1]), S.ao[0]);
+        z = fma(r2 * r, po, z);
+        const double pd = fma(r2, fma(r2, fma(r2, 9.0 * S.ao[3], 7.0 * S.ao[2]), 5.0 * S.ao[1]), 3.0 * S.ao[0]);
+        g = fma(r, pd, g);
+    }
+    zx = x * g;
+    zy = y * g;
+    if (S.flags & SF_ZERN) {
+        double zz, zu, zv;
+        zern_eval(S.zp, x * S.zinv, y * S.zinv, zz, zu, zv);
+        z += zz;
+        zx = fma(zu, S.zinv, zx);
+        zy = fma(zv, S.zinv, zy);
+    }
+    return true;
+}
+
+// Intersection (Sec. 2.4.2): exact root of the paraboloid with the vertex curvature as first guess, then
+// Newton's method on F(l) = p_z + l d_z - S(p_x + l d_x, p_y + l d_y) until the step is below 1e-8 mm.
+// On success l is the distance and (zx, zy) the slopes at the root (within 1e-8 mm of it).
+__device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[3], const double d[3], double& l,
+                                              double& zx, double& zy) {
+    if (S.flags & SF_FLAT_ONLY) {
+        if (d[2] == 0.0) return PHOSIM_LOST_MISSED;
+        l = -p[2] / d[2];
+        zx = 0.0; zy = 0.0;
+        return 0;
+    }
+    const double qa = 0.5 * S.c * (d[0] * d[0] + d[1] * d[1]);
+    const double qb = S.c * (p[0] * d[0] + p[1] * d[1]) - d[2];
+    const double qc = 0.5 * S.c * (p[0] * p[0] + p[1] * p[1]) - p[2];
+    const double disc = qb * qb - 4.0 * qa * qc;
+    if (qa == 0.0 || disc < 0.0) {
+        if (qb == 0.0) return PHOSIM_LOST_MISSED;
+        l = -qc / qb;
+    } else {
+        const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
+        if (q == 0.0) return PHOSIM_LOST_MISSED;
+        l = qc / q;
+    }
+#pragma unroll 1
+    for (int it = 0; it < 20; ++it) {
+        const double x = fma(l, d[0], p[0]), y = fma(l, d[1], p[1]);
+        double zs;
+        if (!sag(S, x, y, zs, zx, zy)) return PHOSIM_LOST_MISSED;
+        const double F = fma(l, d[2], p[2]) - zs;
+        const double dF = d[2] - zx * d[0] - zy * d[1];
+        if (dF == 0.0) return PHOSIM_LOST_NEWTON;
+        const double step = F / dF;
+        l -= step;
+        if (fabs(step) < 1e-8) return 0;
+    }
+    return PHOSIM_LOST_NEWTON;
+}
+
+__device__ __forceinline__ double sellmeier(const DMaterial& m, double lam_nm) {
+    const double l2 = (lam_nm * 1e-3) * (lam_nm * 1e-3);
+    double n2 = 1.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n2 += m.B[i] * l2 / (l2 - m.C[i]);
+    return sqrt(n2);
+}
+
+// silicon index of Sec. 2.4.1, E in eV
+__device__ __forceinline__ double silicon_index(double lam_nm) {
+    const double E = 1239.841984 / lam_nm;
+    return 3.36 + 0.211 * E + 2.79 * exp((E - 3.30) / 0.398);
+}
+__device__ __forceinline__ float silicon_index_f(float lam_nm) {
+    const float E = 1239.841984f / lam_nm;
+    return 3.36f + 0.211f * E + 2.79f * expf((E - 3.30f) * (1.0f / 0.398f));
+}
+
+// Snell's law in vector form (Sec. 2.4.2); false on total internal reflection
+__device__ __forceinline__ bool refract(double d[3], double Nx, double Ny, double Nz, double n1, double n2) {
+    double cosi = -(d[0] * Nx + d[1] * Ny + d[2] * Nz);
+    if (cosi < 0.0) { Nx = -Nx; Ny = -Ny; Nz = -Nz; cosi = -cosi; }
+    const double mu = n1 / n2;
+    const double k = 1.0 - mu * mu * (1.0 - cosi * cosi);
+    if (k < 0.0) return false;
+    const double a = mu * cosi - sqrt(k);
+    d[0] = fma(mu, d[0], a * Nx);
+    d[1] = fma(mu, d[1], a * Ny);
+    d[2] = fma(mu, d[2], a * Nz);
+    return true;
+}
+
+__device__ __forceinline__ void to_surface(const DSurface& S, const double x[3], const double d[3], double p[3],
+                                           double dl[3]) {
+    const double rx = x[0] - S.o[0], ry = x[1] - S.o[1], rz = x[2] - S.o[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p[i] = fma(S.M[3 * i], rx, fma(S.M[3 * i + 1], ry, S.M[3 * i + 2] * rz));
+        dl[i] = fma(S.M[3 * i], d[0], fma(S.M[3 * i + 1], d[1], S.M[3 * i + 2] * d[2]));
+    }
+}
+
+__device__ __forceinline__ void from_surface(const DSurface& S, const double p[3], const double dl[3], double x[3],
+                                             double d[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        x[i] = fma(S.M[i], p[0], fma(S.M[3 + i], p[1], fma(S.M[6 + i], p[2], S.o[i])));
+        d[i] = fma(S.M[i], dl[0], fma(S.M[3 + i], dl[1], S.M[6 + i] * dl[2]));
+    }
+}
+
+}  // namespace phosim

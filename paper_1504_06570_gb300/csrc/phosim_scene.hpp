@@ -1,0 +1,41 @@
+// Host-side scene object behind the phosim C ABI.
+#pragma once
+
+#include <vector>
+
+#include "phosim_device.cuh"
+
+struct phosim_scene {
+    phosim::TraceParams base;       // scalars and device table pointers; per-call fields filled by a trace
+    int precision = PHOSIM_PLAIN_FP64;
+    bool optics_loaded = false, seds_loaded = false;
+    int sm_count = 0;
+    int threads = 256;
+    int tile_photons = 0;           // 0 = chosen per call from the workload
+    int n_sed = 0;
+    int sersic_tables = 0;
+    // host copy of the loaded optics (for the adjoint)
+    std::vector<phosim_surface> surfaces;
+    // device memory owned by the scene
+    std::vector<void*> table_mem;   // sensor tables
+    std::vector<void*> optics_mem;  // coating tables
+    std::vector<void*> screen_mem;  // gradient screens
+    std::vector<void*> sed_mem;
+    std::vector<void*> sersic_mem;
+    // per-call scratch, grown on demand
+    phosim::DSource* d_src = nullptr;
+    size_t cap_src = 0;
+    unsigned long long* d_prefix = nullptr;
+    size_t cap_prefix = 0;
+    unsigned long long* d_counters = nullptr;   // [0] tile counter, [1..9] counters
+    uint32_t* d_stage = nullptr;                // staging image for host image pointers
+    size_t cap_stage = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace phosim {
+cudaError_t launch_trace(const TraceParams& P, bool mixed, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_chief_rays(const TraceParams& P, DSource* sources, int n_src, double* moments, cudaStream_t st);
+cudaError_t trace_occupancy(bool mixed, int threads, int* blocks_per_sm);
+void free_all(std::vector<void*>& v);
+}  // namespace phosim

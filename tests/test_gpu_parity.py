@@ -1,0 +1,128 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, photon by photon, on seeded inputs.
+
+Tolerances (written from the arithmetic): the FP64 path and the oracle evaluate the same formulas with
+different operation order and contraction, so final positions agree to ~1e-12 mm; the gate is the
+spec one, 1e-4 pixel for at least 99.999 % of the photons detected by both, with identical fates
+except for photons within 1e-7 mm / 1e-6 nm of an accept boundary.  The mixed path keeps positions and
+intersections in FP64 and rounds the deflections, the wavelength blur and the sensor draws to FP32, so it
+is held to the moment gate (0.1 %) and to 1e-2 pixel per photon for 99.9 % of the photons.
+"""
+import numpy as np
+import pytest
+
+from paper_1504_06570_gb300 import inputs as I
+from paper_1504_06570_gb300 import phosim as P
+from tests import gpu_helpers as G
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1504_06570_gb300 import build
+    build.build()
+
+
+def test_tiny_paraboloid_fp64_per_photon(oracle_mod):
+    """1 on-axis star, 1e5 photons, 5800 K blackbody 400-700 nm, one 512^2 Kolmogorov screen at 5 km,
+    D = 1 m f/10 paraboloid, 256^2 chip of 10 um pixels with 100 um of silicon, FP64 throughout."""
+    sc = I.paraboloid_scene(n_photons=100_000)
+    gpu = G.run_gpu(sc, P.PLAIN_FP64)
+    ora = G.oracle_trace(oracle_mod, sc)
+    r = G.compare_records(sc, gpu, ora, pos_tol_px=1e-4, min_frac=0.99999)
+    assert r["max_err_px"] < 1e-6, r
+    assert r["lam_err"] < 1e-9
+    # the image is the histogram of the records' pixels, and the oracle's image away from boundaries
+    assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
+    diff = np.abs(gpu["image"].astype(np.int64) - ora["image"].astype(np.int64)).sum()
+    assert diff <= 2 * r["n_boundary"]
+    G.compare_moments(gpu["moments"], G.oracle_moments(ora, 1), rel=1e-6)
+    c = gpu["counters"]
+    assert c[0] == 100_000 and c[1] == ((ora["flags"] & 1) == 1).sum()
+    assert c[0] == c[1] + c[2:].sum()
+
+
+def test_tiny_paraboloid_mixed(oracle_mod):
+    sc = I.paraboloid_scene(n_photons=100_000)
+    gpu = G.run_gpu(sc, P.MIXED)
+    ora = G.oracle_trace(oracle_mod, sc)
+    rec = gpu["rec"]
+    both = ((rec["flags"] & 1) == 1) & ((ora["flags"] & 1) == 1)
+    err = np.hypot(rec["x"][both] - ora["x"][both], rec["y"][both] - ora["y"][both]) / sc.detector.pixel
+    assert np.mean(err < 1e-2) > 0.999, np.percentile(err, [50, 99, 99.9, 100])
+    assert np.mean(rec["flags"] != ora["flags"]) < 1e-3
+    G.compare_moments(gpu["moments"], G.oracle_moments(ora, 1), rel=1e-3)
+
+
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED])
+def test_catadioptric_system_all_surface_features(oracle_mod, precision):
+    """Annular paraboloid with Zernike figure and tilt, decentred aspheric lens, coated filter, silicon;
+    two layers of two scales with wind; point, Sersic and Gaussian sources with redshifts; ragged counts."""
+    counts = [0, 1, 31, 33, 1000, 4097, 20000, 7, 2500]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts))
+    gpu = G.run_gpu(sc, precision)
+    ora = G.oracle_trace(oracle_mod, sc)
+    if precision == P.PLAIN_FP64:
+        r = G.compare_records(sc, gpu, ora)
+        assert r["max_err_px"] < 1e-6, r
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
+    else:
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+    assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
+
+
+@pytest.mark.parametrize("schedule", [(32, 32), (64, 96), (256, 1024), (128, 0)])
+def test_schedule_does_not_change_results(oracle_mod, schedule):
+    """Counter-based streams: the result depends on neither the block size nor the tile size."""
+    counts = [3, 500, 1200, 64]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=9))
+    ref = G.run_gpu(sc, P.PLAIN_FP64)
+    gpu = G.run_gpu(sc, P.PLAIN_FP64, schedule=schedule)
+    assert np.array_equal(gpu["rec"], ref["rec"])
+    assert np.array_equal(gpu["image"], ref["image"])
+
+
+def test_photon_ranges_compose():
+    """Tracing photons [0, a) then [a, n) of each source gives the records and image of [0, n)."""
+    counts = np.array([700, 1500, 33], np.uint64)
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=4))
+    full = G.run_gpu(sc, P.PLAIN_FP64)
+    a = np.array([300, 1, 32], np.uint64)
+    p1 = G.run_gpu(sc, P.PLAIN_FP64, n_photons=a)
+    p2 = G.run_gpu(sc, P.PLAIN_FP64, n_photons=counts - a, first=a)
+    assert np.array_equal(p1["image"] + p2["image"], full["image"])
+    off = np.r_[0, np.cumsum(counts)]
+    o1, o2 = np.r_[0, np.cumsum(a)], np.r_[0, np.cumsum(counts - a)]
+    for s in range(3):
+        joined = np.concatenate([p1["rec"][o1[s]:o1[s + 1]], p2["rec"][o2[s]:o2[s + 1]]])
+        assert np.array_equal(joined, full["rec"][off[s]:off[s + 1]])
+
+
+def test_host_image_is_staged():
+    sc = I.paraboloid_scene(n_photons=20000)
+    dev = G.run_gpu(sc, P.PLAIN_FP64, records=False)
+    host = G.run_gpu(sc, P.PLAIN_FP64, records=False, host_image=True)
+    assert np.array_equal(dev["image"], host["image"])
+
+
+def test_sensor_off_and_atmosphere_off(oracle_mod):
+    sc = G.test_system_scene(n_photons=5000, sensor=False, atmosphere=False)
+    gpu = G.run_gpu(sc, P.PLAIN_FP64)
+    ora = G.oracle_trace(oracle_mod, sc)
+    r = G.compare_records(sc, gpu, ora)
+    assert r["max_err_px"] < 1e-6
+
+
+def test_invalid_sources_are_rejected():
+    sc = I.paraboloid_scene(n_photons=10)
+    s = P.Scene(sc)
+    bad = sc.sources.subset([0])
+    bad.sed = np.array([5], np.int32)            # no such SED
+    s.set_sources(bad)
+    img = torch.zeros((256, 256), dtype=torch.int32, device="cuda")
+    with pytest.raises(P.PhosimError) as e:
+        s.trace(img)
+    assert e.value.code == -1
+    s.close()
