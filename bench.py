@@ -1,0 +1,319 @@
+"""Benchmark: photons/s of the photon Monte Carlo path on one GB300 (and N GPUs by weak scaling).
+
+Workload: 1000 stars, 1e8 source photons per step (300-1200 nm blackbodies) through seven frozen-flow von
+Karman layers (4096^2 at 1 cm + 1024^2 at 64 cm each), the synthetic 8.4 m three-mirror telescope with a
+three-lens camera and a 550-700 nm filter, and 100 um of silicon, onto one 4096 x 4096 chip.  A step is one
+phosim_trace call over all photons.  The headline is the mixed-precision path; the plain all-FP64 path is
+timed beside it, and the moments of both are compared with the CPU oracle on a photon sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photons/s end-to-end on 1 GB300 vs plain FP64 path; PSF-moment error vs oracle"
+WORKLOAD = ("three-mirror 8.4 m telescope + 3-lens camera + 550-700 nm filter, 7 von Karman layers "
+            "(4096^2@1cm + 1024^2@64cm), 1000 stars, 1e8 photons, 4096^2 chip")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--photons", type=float, default=1e8, help="photons per step per GPU")
+    ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain FP64 path")
+    ap.add_argument("--sample", type=int, default=8000, help="oracle photons per star for the CPU leg")
+    ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--fine-n", type=int, default=4096, help="fine screen size (smaller: profiling case)")
+    ap.add_argument("--coarse-n", type=int, default=1024, help="coarse screen size (smaller: profiling case)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def workload(photons_per_gpu, rank, fine_n=4096, coarse_n=1024):
+    from paper_1504_06570_gb300 import inputs as I
+    return I.three_mirror_scene(n_total=int(photons_per_gpu), fine_n=fine_n, coarse_n=coarse_n)
+
+
+def cpu_leg(scene, sample):
+    """The oracle as it stands on the host cores over a bounded sample: the first `sample` photons of every
+    star (all threads).  Returns its rate and its records for the moment comparison."""
+    from oracle import oracle as O
+    cnt = np.minimum(scene.sources.n_photons, np.uint64(sample))
+    o = O.Oracle(scene)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    rec = o.trace(count=cnt, n_threads=cores, image=False)
+    dt = time.perf_counter() - t0
+    return {"value": float(cnt.sum() / dt), "unit": "photons/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} photons of each of {len(cnt)} stars ({int(cnt.sum())} photons, {dt:.1f} s)"}, rec, cnt
+
+
+def moment_errors(gpu_m, ora_rec, n_src):
+    """Per-star centroid / size / ellipticity differences between the GPU sample and the oracle sample."""
+    from paper_1504_06570_gb300 import phosim as P
+    g = P.derived_moments(gpu_m)
+    det = (ora_rec["flags"] & 1) == 1
+    out = []
+    for s in range(n_src):
+        m = det & (ora_rec["source"] == s)
+        if m.sum() < 50:
+            continue
+        x, y = ora_rec["x"][m], ora_rec["y"][m]
+        mx, my = x.mean(), y.mean()
+        ixx, ixy, iyy = ((x - mx) ** 2).mean(), ((x - mx) * (y - my)).mean(), ((y - my) ** 2).mean()
+        T = ixx + iyy
+        gT = g[s, 3] + g[s, 5]
+        out.append([abs(g[s, 1] - mx) / np.sqrt(T), abs(gT / T - 1), abs((g[s, 3] - g[s, 5]) / gT - (ixx - iyy) / T),
+                    abs(2 * g[s, 4] / gT - 2 * ixy / T), abs(g[s, 0] - m.sum()) / m.sum()])
+    a = np.array(out)
+    return {"stars": len(a), "max_centroid_over_size": float(a[:, 0].max()), "max_rel_T": float(a[:, 1].max()),
+            "max_de1": float(a[:, 2].max()), "max_de2": float(a[:, 3].max()), "max_rel_count": float(a[:, 4].max())}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = workload(args.photons, 0, args.fine_n, args.coarse_n)
+    steps = []
+    cpu = None
+    for _ in range(args.warmup + args.steps):
+        cpu, _, _ = cpu_leg(sc, max(1, args.sample // 4))
+        steps.append(cpu["value"])
+    v = float(np.median(steps[args.warmup:]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "photons/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle_sample": cpu["sample"]},
+            "cpu_baseline": {**cpu, "value": v},
+            "e2e": {"value": v, "unit": "photons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1504_06570_gb300 import build as B
+    B.build()
+    from paper_1504_06570_gb300 import phosim as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    t_setup = time.perf_counter()
+    sc = workload(args.photons, rank, args.fine_n, args.coarse_n)
+    n_src = len(sc.sources)
+    # weak scaling: rank r traces photons [r N, (r + 1) N) of every star (a longer exposure per GPU)
+    counts = sc.sources.n_photons.copy()
+    first = (counts * np.uint64(rank)).astype(np.uint64)
+    photons = int(counts.sum())
+    mixed = P.Scene(sc, P.MIXED)
+    plain = P.Scene(sc, P.PLAIN_FP64)
+    setup_s = time.perf_counter() - t_setup
+    d = sc.detector
+    img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
+    mom = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(scene, steps, warmup):
+        for _ in range(warmup):
+            scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for a, b in ev:
+            a.record(stream)
+            scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
+            b.record(stream)
+        barrier()
+        per = np.array([a.elapsed_time(b) for a, b in ev])
+        return per
+
+    # peaks of the arithmetic roofline (FMA issue rate), measured on this device
+    fp64_rate = fp32_rate = None
+    try:
+        import ctypes as C
+        r = C.c_double()
+        if P.lib().phosim_fma_rate(1, 2000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
+            fp64_rate = r.value
+        if P.lib().phosim_fma_rate(0, 20000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
+            fp32_rate = r.value
+    except Exception:
+        pass
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    per_mixed = timed(mixed, args.steps, args.warmup)
+    clock_rec = clocks.stop()
+    per_plain = timed(plain, args.plain_steps, 1)
+
+    # e2e through the C ABI with host buffers: pinned host image in, result image out, every step
+    himg = torch.zeros((d.ny, d.nx), dtype=torch.int32, pin_memory=True)
+    for _ in range(1):
+        mixed.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mixed.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    img_bytes = d.nx * d.ny * 4
+    src_bytes = n_src * (P.C.sizeof(P.Source) if hasattr(P, "C") else 80) + n_src * 16
+
+    ms_mixed = float(per_mixed.max()) if world == 1 else float(per_mixed.mean())
+    t_mixed = float(per_mixed.sum()) / 1e3
+    t_plain = float(per_plain.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([t_mixed, t_plain, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_mixed, t_plain, e2e_s = t.tolist()
+    value = photons * world * args.steps / t_mixed
+    plain_value = photons * world * args.plain_steps / t_plain
+    counters = mixed.counters()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    line = {"metric": METRIC, "value": value, "unit": "photons/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "photons_per_step_per_gpu": photons, "sources": n_src,
+                       "precision": "mixed (FP64 positions/intersections, FP32 deflections/SED blur/sensor)",
+                       "l2": "inputs larger than L2 (gradient screens 2.8 GB, read in both precisions' forms)",
+                       "setup_s": round(setup_s, 1)},
+            "plain_fp64": {"value": plain_value, "unit": "photons/s", "ms_per_step": t_plain / args.plain_steps * 1e3,
+                           "speedup_of_mixed": value / plain_value},
+            "detected_fraction": float(counters[1] / max(1, counters[0])),
+            "e2e": {"value": photons * world / e2e_s, "unit": "photons/s", "h2d_bytes_per_step": img_bytes + src_bytes,
+                    "d2h_bytes_per_step": img_bytes},
+            "gpu_launches": 2 * args.steps, "clocks": clock_rec,
+            "fma_peaks_measured_tflops": {"fp64": fp64_rate, "fp32": fp32_rate}}
+
+    if not args.no_oracle:
+        from oracle import oracle as O
+        o = O.Oracle(sc)
+        ops = o.count_ops(count=np.minimum(counts, np.uint64(20)))
+        fl_pre = sum(v for k, v in ops["pre"].items() if k != "transcendental")
+        fl_opt = sum(v for k, v in ops["optics"].items() if k != "transcendental")
+        kernel_s = float(np.mean(per_mixed)) / 1e3
+        achieved = fl_opt * photons / kernel_s / 1e12
+        peak = fp64_rate or FP64_NOMINAL_TFLOPS
+        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "note": (f"FP64 optics flops {fl_opt:.0f}/photon (oracle op count; +{fl_pre:.0f} sampling and "
+                                     f"atmosphere flops, mostly FP32 here) over the mixed step time; peak = "
+                                     + ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)"))}
+        line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) * photons / (float(np.mean(per_plain)) / 1e3) / 1e12,
+                                       "peak": peak, "unit": "TFLOP/s"}
+        line["roofline_plain_fp64"]["frac"] = line["roofline_plain_fp64"]["achieved"] / peak
+        if rank == 0:
+            cpu, rec, cnt = cpu_leg(sc, args.sample)
+            line["cpu_baseline"] = cpu
+            errs = {}
+            for name, scn in (("mixed", mixed), ("plain_fp64", plain)):
+                m2 = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+                i2 = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
+                scn.trace(i2, None, m2, n_photons=cnt)
+                torch.cuda.synchronize(dev)
+                errs[name] = moment_errors(m2.cpu().numpy(), rec, n_src)
+            line["moment_error_vs_oracle"] = errs
+    print(json.dumps(line))
+    mixed.close()
+    plain.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

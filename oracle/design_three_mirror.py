@@ -18,7 +18,7 @@ import numpy as np
 from scipy import optimize
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-sys.path.insert(0, ROOT)
+sys.path[0] = ROOT            # run as a script: import the oracle package, not this folder
 from oracle import oracle as O                                   # noqa: E402
 from paper_1504_06570_gb300 import inputs as I                   # noqa: E402
 
@@ -43,7 +43,10 @@ def paraxial_radii():
 
 
 def build(params):
-    k1, k2, k3, a1_4, a2_4, a3_4, a3_6, rl3, zdet, rl1 = params
+    k1, k2, k3, a1_4, a2_4, a3_4, a3_6, cl3, zdet, cl1 = params
+    rl1 = 1.0 / (cl1 * 1e-4) if cl1 != 0.0 else 0.0      # curvature parameters in 1e-4 / mm
+    rl1b = 1.0 / (cl1 * 1.05e-4) if cl1 != 0.0 else 0.0
+    rl3 = 1.0 / (cl3 * 1e-4) if cl3 != 0.0 else 0.0
     R2, R3 = paraxial_radii()
     R2, R3 = -R2, R3              # telescope frame: R > 0 puts the centre of curvature towards +z
     surfaces = [
@@ -51,14 +54,14 @@ def build(params):
         I.Surface(kind=I.MIRROR, R=R2, kappa=k2, alpha=(0, a2_4 * 1e-12, 0, 0, 0, 0, 0, 0), z=D1, r_in=0.0, r_out=1700.0),
         I.Surface(kind=I.MIRROR, R=R3, kappa=k3, alpha=(0, a3_4 * 1e-13, 0, a3_6 * 1e-20, 0, 0, 0, 0), z=0.0, r_in=0.0, r_out=2500.0),
         # L1: thick meniscus; L2: weak; filter plate; L3: field flattener
-        I.Surface(kind=I.REFRACT, R=rl1 * 1e3, z=4850.0, r_out=330.0, material=1),
-        I.Surface(kind=I.REFRACT, R=rl1 * 1e3 * 1.08, z=4930.0, r_out=330.0, material=0),
+        I.Surface(kind=I.REFRACT, R=rl1, z=4850.0, r_out=330.0, material=1),
+        I.Surface(kind=I.REFRACT, R=rl1b, z=4880.0, r_out=330.0, material=0),
         I.Surface(kind=I.REFRACT, R=-8000.0, z=5120.0, r_out=290.0, material=1),
-        I.Surface(kind=I.REFRACT, R=-7000.0, z=5150.0, r_out=290.0, material=0),
+        I.Surface(kind=I.REFRACT, R=-7000.0, z=5135.0, r_out=290.0, material=0),
         I.Surface(kind=I.REFRACT, R=0.0, z=5230.0, r_out=270.0, material=1, coating=0),
-        I.Surface(kind=I.REFRACT, R=0.0, z=5252.0, r_out=270.0, material=0),
-        I.Surface(kind=I.REFRACT, R=rl3 * 1e3, z=5300.0, r_out=260.0, material=1),
-        I.Surface(kind=I.REFRACT, R=0.0, z=5360.0, r_out=260.0, material=0),
+        I.Surface(kind=I.REFRACT, R=0.0, z=5240.0, r_out=270.0, material=0),
+        I.Surface(kind=I.REFRACT, R=rl3, z=5300.0, r_out=260.0, material=1),
+        I.Surface(kind=I.REFRACT, R=0.0, z=5325.0, r_out=260.0, material=0),
         I.Surface(kind=I.DETECTOR, R=0.0, z=zdet, material=2),
     ]
     return surfaces
@@ -111,9 +114,18 @@ def residuals(params):
 
 
 def main():
-    x0 = np.array([-1.2, -0.5, -0.2, 0.0, 0.0, 0.0, 0.0, 2.0, 5408.0, 3.0])
-    best = optimize.least_squares(residuals, x0, x_scale=np.array([0.1, 0.1, 0.1, 1, 1, 1, 1, 0.5, 2.0, 0.5]),
-                                  diff_step=1e-4, max_nfev=400)
+    x0 = np.array([-1.2, -0.5, -0.2, 0.0, 0.0, 0.0, 0.0, 0.0, 5460.0, 0.0])
+    # detector height first (on-axis focus), then everything together
+    zs = np.linspace(5400.0, 5520.0, 121)
+    def on_axis(z):
+        q = x0.copy(); q[8] = z
+        r = residuals(q).reshape(len(FIELDS), -1)[0]
+        return np.sqrt(np.mean(r ** 2))
+    x0[8] = zs[int(np.argmin([on_axis(z) for z in zs]))]
+    lo = np.array([-3, -3, -3, -50, -50, -50, -50, -1.0, 5350, -1.0])
+    hi = np.array([1, 1, 1, 50, 50, 50, 50, 1.0, 5560, 1.0])
+    best = optimize.least_squares(residuals, x0, bounds=(lo, hi), x_scale=np.array([0.05, 0.05, 0.05, 1, 1, 1, 1, 0.2, 1.0, 0.2]),
+                                  max_nfev=600)
     p = best.x
     r = residuals(p).reshape(len(FIELDS), -1)
     rms = np.sqrt(np.mean(r ** 2, axis=1) * 2)

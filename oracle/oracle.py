@@ -191,6 +191,21 @@ class Oracle:
             raise RuntimeError("oracle_pre_optics failed")
         return pos, d, lam, t
 
+    def count_ops(self, sources=None, first=None, count=None):
+        """Algorithmic operations per photon: dict of sampling+atmosphere and optics+sensor counts."""
+        src = self.scene.sources if sources is None else sources
+        n = len(src)
+        first = np.zeros(n, np.uint64) if first is None else _arr(first, np.uint64)
+        count = _arr(src.n_photons if count is None else count, np.uint64)
+        out = np.zeros(11)
+        u64p = C.POINTER(C.c_uint64)
+        rc = self.L.oracle_count_ops(self.h, C.c_int(n), *self._src_args(src), first.ctypes.data_as(u64p),
+                                     count.ctypes.data_as(u64p), _dp(out))
+        if rc:
+            raise RuntimeError("oracle_count_ops failed")
+        keys = ("add", "mul", "div", "sqrt", "transcendental")
+        return {"pre": dict(zip(keys, out[0:5])), "optics": dict(zip(keys, out[5:10])), "photons": int(out[10])}
+
     def trace_tangents(self, params, sources=None, first=None, count=None, n_threads=1):
         """Per-photon final positions and their derivatives with respect to each (surface, field) parameter."""
         src = self.scene.sources if sources is None else sources

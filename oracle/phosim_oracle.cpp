@@ -27,6 +27,7 @@
  * Parity pins live in tests/test_oracle_*.py; "parity unpinned" is stated there for the parts without one.
  */
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -57,11 +58,37 @@ inline Dual atan2(Dual y, Dual x) {
     double r2 = x.v * x.v + y.v * y.v;
     return Dual(std::atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / r2);
 }
+inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, e * a.d); }
+// ------------------------------------------------------------------------------------------------------
+// operation counter: a double that counts the arithmetic done on it (the algorithmic work of a photon)
+// ------------------------------------------------------------------------------------------------------
+struct OpCount { double add = 0, mul = 0, div = 0, sqrt = 0, special = 0; };
+thread_local OpCount g_ops;
+struct Cnt {
+    double v;
+    Cnt(double a = 0.0) : v(a) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { g_ops.add += 1; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { g_ops.add += 1; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { g_ops.mul += 1; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { g_ops.div += 1; return Cnt(a.v / b.v); }
+inline Cnt sqrt(Cnt a) { g_ops.sqrt += 1; return Cnt(std::sqrt(a.v)); }
+inline Cnt sin(Cnt a) { g_ops.special += 1; return Cnt(std::sin(a.v)); }
+inline Cnt cos(Cnt a) { g_ops.special += 1; return Cnt(std::cos(a.v)); }
+inline Cnt atan2(Cnt y, Cnt x) { g_ops.special += 1; return Cnt(std::atan2(y.v, x.v)); }
+inline Cnt log(Cnt a) { g_ops.special += 1; return Cnt(std::log(a.v)); }
+inline Cnt exp(Cnt a) { g_ops.special += 1; return Cnt(std::exp(a.v)); }
+inline Cnt pow(Cnt a, Cnt b) { g_ops.special += 1; return Cnt(std::pow(a.v, b.v)); }
+inline double val(const Cnt& a) { return a.v; }
+inline bool is_zero(const Cnt& a) { return a.v == 0.0; }
+
 inline double val(double a) { return a; }
 inline double val(const Dual& a) { return a.v; }
 inline bool is_zero(double a) { return a == 0.0; }
 inline bool is_zero(const Dual& a) { return a.v == 0.0 && a.d == 0.0; }
-using std::sqrt; using std::sin; using std::cos; using std::atan2;
+using std::sqrt; using std::sin; using std::cos; using std::atan2; using std::log; using std::exp; using std::pow;
 
 // ------------------------------------------------------------------------------------------------------
 // Philox4x32-10, from the published definition (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -336,7 +363,11 @@ uint32_t intersect(const SurfT<T>& st, const T p[3], const T d[3], T& l) {
         T step = F / dF;
         l = l - step;
         if (converged_at >= 0) break;
-        if (std::fabs(val(step)) < 1e-12 * (1.0 + std::fabs(val(l)))) converged_at = it;
+        if (std::is_same<T, Cnt>::value) {
+            if (std::fabs(val(step)) < 1e-5) { converged_at = it; break; }
+        } else if (std::fabs(val(step)) < 1e-12 * (1.0 + std::fabs(val(l)))) {
+            converged_at = it;
+        }
     }
     if (converged_at < 0) return LOST_NEWTON;
     T x = p[0] + l * d[0], y = p[1] + l * d[1], zs, zx, zy;
@@ -348,19 +379,22 @@ uint32_t intersect(const SurfT<T>& st, const T p[3], const T d[3], T& l) {
 // ------------------------------------------------------------------------------------------------------
 // media (Sec. 2.4.1)
 // ------------------------------------------------------------------------------------------------------
-double refractive_index(const Scene& sc, int material, double lam_nm) {
+template <class T>
+T refractive_index_t(const Scene& sc, int material, T lam_nm) {
     const Mat& m = sc.mat[material];
-    if (m.kind == M_VACUUM) return 1.0;
+    if (m.kind == M_VACUUM) return T(1.0);
     if (m.kind == M_SELLMEIER) {
-        double l2 = (lam_nm * 1e-3) * (lam_nm * 1e-3);
-        double n2 = 1.0;
-        for (int i = 0; i < 3; ++i) n2 += m.B[i] * l2 / (l2 - m.C[i]);
-        return std::sqrt(n2);
+        T lu = lam_nm * T(1e-3);
+        T l2 = lu * lu;
+        T n2 = T(1.0);
+        for (int i = 0; i < 3; ++i) n2 = n2 + T(m.B[i]) * l2 / (l2 - T(m.C[i]));
+        return sqrt(n2);
     }
     // silicon, E in eV
-    double E = 1239.841984 / lam_nm;
-    return 3.36 + 0.211 * E + 2.79 * std::exp((E - 3.30) / 0.398);
+    T E = T(1239.841984) / lam_nm;
+    return T(3.36) + T(0.211) * E + T(2.79) * exp((E - T(3.30)) / T(0.398));
 }
+double refractive_index(const Scene& sc, int material, double lam_nm) { return refractive_index_t<double>(sc, material, lam_nm); }
 
 // reflection of d across the unit normal N
 template <class T>
@@ -371,15 +405,15 @@ void reflect(T d[3], const T N[3]) {
 
 // Snell's law in vector form from index n1 to n2; false on total internal reflection
 template <class T>
-bool refract(T d[3], const T Nin[3], double n1, double n2) {
+bool refract(T d[3], const T Nin[3], T n1, T n2) {
     T N[3] = {Nin[0], Nin[1], Nin[2]};
     T cosi = -(d[0] * N[0] + d[1] * N[1] + d[2] * N[2]);
     if (val(cosi) < 0.0) { for (int i = 0; i < 3; ++i) N[i] = -N[i]; cosi = -cosi; }
-    double mu = n1 / n2;
-    T k = T(1.0) - T(mu * mu) * (T(1.0) - cosi * cosi);
+    T mu = n1 / n2;
+    T k = T(1.0) - mu * mu * (T(1.0) - cosi * cosi);
     if (val(k) < 0.0) return false;
-    T a = T(mu) * cosi - sqrt(k);
-    for (int i = 0; i < 3; ++i) d[i] = T(mu) * d[i] + a * N[i];
+    T a = mu * cosi - sqrt(k);
+    for (int i = 0; i < 3; ++i) d[i] = mu * d[i] + a * N[i];
     return true;
 }
 
@@ -403,87 +437,100 @@ struct Pre {     // photon state entering the optics (after the atmosphere)
     double x[3], d[3], lam, t;
 };
 
-// Sec. 2.2 + 2.3: everything before the first optical surface
-void sample_and_atmosphere(const Scene& sc, const Source& s, const Draws& D, Pre& P) {
+// central-difference phase gradient at a screen node: a table entry the paper precomputes (Sec. 3.2),
+// so the operation counter does not see it
+inline void node_gradient(const Scale& S, long long i, long long j, double& gx, double& gy) {
+    const int N = S.N;
+    auto wrap = [N](long long v) { long long m = v % N; return (int)(m < 0 ? m + N : m); };
+    auto ph = [&](long long a, long long b) { return S.phase[(size_t)wrap(b) * N + wrap(a)]; };
+    gx = (ph(i + 1, j) - ph(i - 1, j)) / (2.0 * S.pixel);
+    gy = (ph(i, j + 1) - ph(i, j - 1)) / (2.0 * S.pixel);
+}
+
+// Sec. 2.2 + 2.3: everything before the first optical surface.  T = double, or the operation counter.
+template <class T>
+void sample_and_atmosphere_t(const Scene& sc, const Source& s, const Draws& D, T X[3], T Dir[3], T& lam, T& tt) {
     // time stamp (Sec. 2.2)
-    P.t = s.t0 + s.t_exp * uniform01(D.w[S_TIME]);
+    tt = T(s.t0) + T(s.t_exp) * T(uniform01(D.w[S_TIME]));
     // wavelength: photon-number CDF, first bin with u < cdf, blurred uniformly within the bin, redshifted
     const std::vector<double>& cdf = sc.cdf[s.sed];
     double ub = uniform01(D.w[S_LAM_BIN]);
     int bin = 0;
     while (bin < sc.n_bins - 1 && !(ub < cdf[bin])) ++bin;
-    P.lam = (sc.sed_lam0 + bin * sc.sed_dlam + uniform01(D.w[S_LAM_BLUR]) * sc.sed_dlam) * (1.0 + s.redshift);
+    lam = (T(sc.sed_lam0 + bin * sc.sed_dlam) + T(uniform01(D.w[S_LAM_BLUR])) * T(sc.sed_dlam)) * T(1.0 + s.redshift);
     // direction: tangent-plane components, perturbed paraxially by the source shape, renormalised
-    double nx = s.xi, ny = s.eta;
+    T nx = T(s.xi), ny = T(s.eta);
     if (s.kind == SRC_SERSIC) {
         const std::vector<double>& tab = sc.sersic[s.table];
         int K = sc.sersic_K;
-        double f = uniform01(D.w[S_SHAPE_A]) * K - 0.5;
-        int k = (int)std::floor(f);
+        T f = T(uniform01(D.w[S_SHAPE_A])) * T((double)K) - T(0.5);
+        int k = (int)std::floor(val(f));
         if (k < 0) k = 0;
         if (k > K - 2) k = K - 2;
-        double t = f - k;
-        t = std::min(1.0, std::max(0.0, t));
-        double r = tab[k] * (1.0 - t) + tab[k + 1] * t;
-        double psi = 2.0 * M_PI * uniform01(D.w[S_SHAPE_B]);
-        double dx = s.a * r * std::cos(psi), dy = s.b * r * std::sin(psi);
-        nx += dx * std::cos(s.pa) - dy * std::sin(s.pa);
-        ny += dx * std::sin(s.pa) + dy * std::cos(s.pa);
+        T t = f - T((double)k);
+        if (val(t) < 0.0) t = T(0.0);
+        if (val(t) > 1.0) t = T(1.0);
+        T r = T(tab[k]) * (T(1.0) - t) + T(tab[k + 1]) * t;
+        T psi = T(2.0 * M_PI) * T(uniform01(D.w[S_SHAPE_B]));
+        T dx = T(s.a) * r * cos(psi), dy = T(s.b) * r * sin(psi);
+        T cpa = T(std::cos(s.pa)), spa = T(std::sin(s.pa));      // per source, not per photon
+        nx = nx + (dx * cpa - dy * spa);
+        ny = ny + (dx * spa + dy * cpa);
     } else if (s.kind == SRC_GAUSS) {
-        double g = std::sqrt(-2.0 * std::log(uniform01(D.w[S_SHAPE_A])));
-        double ph = 2.0 * M_PI * uniform01(D.w[S_SHAPE_B]);
-        nx += s.a * g * std::cos(ph);
-        ny += s.a * g * std::sin(ph);
+        T g = sqrt(T(-2.0) * log(T(uniform01(D.w[S_SHAPE_A]))));
+        T ph = T(2.0 * M_PI) * T(uniform01(D.w[S_SHAPE_B]));
+        nx = nx + T(s.a) * g * cos(ph);
+        ny = ny + T(s.a) * g * sin(ph);
     }
-    double nz = -std::sqrt(1.0 - nx * nx - ny * ny);
+    T nz = -sqrt(T(1.0) - nx * nx - ny * ny);
     // pupil point on the annulus, z from the (nominal) first surface, then back to the top of the atmosphere
-    double u = uniform01(D.w[S_PUPIL_R]);
-    double r = std::sqrt(u * (sc.pr_out * sc.pr_out - sc.pr_in * sc.pr_in) + sc.pr_in * sc.pr_in);
-    double phi = 2.0 * M_PI * uniform01(D.w[S_PUPIL_PHI]);
-    double x = r * std::cos(phi), y = r * std::sin(phi);
-    SurfT<double> m1;
-    m1.pert[0] = m1.pert[1] = m1.pert[2] = m1.pert[3] = m1.pert[4] = m1.pert[5] = 0.0;
+    T u = T(uniform01(D.w[S_PUPIL_R]));
+    T r = sqrt(u * T(sc.pr_out * sc.pr_out - sc.pr_in * sc.pr_in) + T(sc.pr_in * sc.pr_in));
+    T phi = T(2.0 * M_PI) * T(uniform01(D.w[S_PUPIL_PHI]));
+    T x = r * cos(phi), y = r * sin(phi);
+    SurfT<T> m1;
+    for (int q = 0; q < 6; ++q) m1.pert[q] = T(0.0);
     setup_surface(sc.surf[0], m1);
-    double zs = 0, zx, zy;
+    T zs = T(0.0), zx, zy;
     surface_sag(m1, x, y, zs, zx, zy);
-    double z = sc.surf[0].z + zs;
-    double l = (sc.h_top - z) / (-nz);
-    x -= nx * l; y -= ny * l; z = sc.h_top;
+    T z = T(sc.surf[0].z) + zs;
+    T l = (T(sc.h_top) - z) / (-nz);
+    x = x - nx * l; y = y - ny * l; z = T(sc.h_top);
     // plane-parallel layers, top to bottom (Sec. 2.3.1, 2.3.2)
     if (sc.atm_on) {
-        double kick = (sc.lam_ref * 1e-6 / (2.0 * M_PI)) * std::pow(P.lam / sc.lam_ref, -0.2);
+        T kick = T(sc.lam_ref * 1e-6 / (2.0 * M_PI)) * pow(lam / T(sc.lam_ref), T(-0.2));
         for (const Layer& L : sc.layers) {
-            double ll = (z - L.z) / (-nz);
-            x += nx * ll; y += ny * ll; z = L.z;
-            double sx = x - L.vx * P.t, sy = y - L.vy * P.t;
-            double gx = 0.0, gy = 0.0;
+            T ll = (z - T(L.z)) / (-nz);
+            x = x + nx * ll; y = y + ny * ll; z = T(L.z);
+            T sx = x - T(L.vx) * tt, sy = y - T(L.vy) * tt;
+            T gx = T(0.0), gy = T(0.0);
             for (const Scale& S : L.scales) {
-                int N = S.N;
-                double fx = sx / S.pixel, fy = sy / S.pixel;
-                double ix = std::floor(fx), iy = std::floor(fy);
-                double tx = fx - ix, ty = fy - iy;
-                auto wrap = [N](long long v) { long long m = v % N; return (int)(m < 0 ? m + N : m); };
-                auto ph = [&](long long i, long long j) { return S.phase[(size_t)wrap(j) * N + wrap(i)]; };
-                double w[2][2] = {{(1 - tx) * (1 - ty), tx * (1 - ty)}, {(1 - tx) * ty, tx * ty}};
+                T fx = sx / T(S.pixel), fy = sy / T(S.pixel);
+                double ix = std::floor(val(fx)), iy = std::floor(val(fy));
+                T tx = fx - T(ix), ty = fy - T(iy);
+                T w[2][2] = {{(T(1.0) - tx) * (T(1.0) - ty), tx * (T(1.0) - ty)}, {(T(1.0) - tx) * ty, tx * ty}};
                 for (int b = 0; b < 2; ++b)
                     for (int a = 0; a < 2; ++a) {
-                        long long i = (long long)ix + a, j = (long long)iy + b;
-                        double gxt = (ph(i + 1, j) - ph(i - 1, j)) / (2.0 * S.pixel);
-                        double gyt = (ph(i, j + 1) - ph(i, j - 1)) / (2.0 * S.pixel);
-                        gx += w[b][a] * gxt;
-                        gy += w[b][a] * gyt;
+                        double gxt, gyt;
+                        node_gradient(S, (long long)ix + a, (long long)iy + b, gxt, gyt);
+                        gx = gx + w[b][a] * T(gxt);
+                        gy = gy + w[b][a] * T(gyt);
                     }
             }
-            nx += kick * gx;
-            ny += kick * gy;
-            nz = -std::sqrt(1.0 - nx * nx - ny * ny);
+            nx = nx + kick * gx;
+            ny = ny + kick * gy;
+            nz = -sqrt(T(1.0) - nx * nx - ny * ny);
         }
     }
     // straight on to the entrance plane of the telescope, where the raytrace starts
-    double le = (z - sc.z_ent) / (-nz);
-    x += nx * le; y += ny * le; z = sc.z_ent;
-    P.x[0] = x; P.x[1] = y; P.x[2] = z;
-    P.d[0] = nx; P.d[1] = ny; P.d[2] = nz;
+    T le = (z - T(sc.z_ent)) / (-nz);
+    x = x + nx * le; y = y + ny * le; z = T(sc.z_ent);
+    X[0] = x; X[1] = y; X[2] = z;
+    Dir[0] = nx; Dir[1] = ny; Dir[2] = nz;
+}
+
+void sample_and_atmosphere(const Scene& sc, const Source& s, const Draws& D, Pre& P) {
+    sample_and_atmosphere_t<double>(sc, s, D, P.x, P.d, P.lam, P.t);
 }
 
 template <class T>
@@ -501,8 +548,9 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
                        OpticsOut<T>& out) {
     T x[3] = {T(P.x[0]), T(P.x[1]), T(P.x[2])};
     T d[3] = {T(P.d[0]), T(P.d[1]), T(P.d[2])};
-    double lam = P.lam;
-    double n_cur = 1.0;
+    const double lam = P.lam;
+    const T lamT = T(P.lam);
+    T n_cur = T(1.0);
     int coat_k = 0;
     out.flags = 0; out.pix = -1; out.margin_mm = 1e300; out.margin_nm = 1e300;
     out.x = T(0.0); out.y = T(0.0); out.xc = out.yc = 0.0;
@@ -528,39 +576,44 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
             double hy = val(p[1]) - (sc.y0 - 0.5 * sc.ny * sc.pixel);
             min_margin(out.margin_mm, hx); min_margin(out.margin_mm, hx - sc.nx * sc.pixel);
             min_margin(out.margin_mm, hy); min_margin(out.margin_mm, hy - sc.ny * sc.pixel);
-            if (hx < 0.0 || hy < 0.0 || hx >= sc.nx * sc.pixel || hy >= sc.ny * sc.pixel) {
+            if (!(hx >= 0.0 && hy >= 0.0 && hx < sc.nx * sc.pixel && hy < sc.ny * sc.pixel)) {
                 out.flags = lost_flag(LOST_OFF_CHIP, (int)si); return;
             }
             T fx = p[0], fy = p[1];
             double xc = val(p[0]), yc = val(p[1]);
             if (sc.sensor_on) {
                 // refraction into silicon, exponential conversion length, lateral diffusion (Sec. 2.4.2, 2.5)
-                double n_si = refractive_index(sc, s.material, lam);
+                T n_si = refractive_index_t<T>(sc, s.material, lamT);
                 if (!refract(dl, N, n_cur, n_si)) { out.flags = lost_flag(LOST_TIR, (int)si); return; }
-                double fl = (lam - sc.ell_lam0) / sc.ell_dlam;
+                T fl = (lamT - T(sc.ell_lam0)) / T(sc.ell_dlam);
                 int ne = (int)sc.ell.size();
-                int k = (int)std::floor(fl);
+                int k = (int)std::floor(val(fl));
                 if (k < 0) k = 0;
                 if (k > ne - 2) k = ne - 2;
-                double t = std::min(1.0, std::max(0.0, fl - k));
-                double ell = sc.ell[k] * (1.0 - t) + sc.ell[k + 1] * t;
-                double L = ell * (-std::log(uniform01(D->w[S_CONV])));
+                T t = fl - T((double)k);
+                if (val(t) < 0.0) t = T(0.0);
+                if (val(t) > 1.0) t = T(1.0);
+                T ell = T(sc.ell[k]) * (T(1.0) - t) + T(sc.ell[k + 1]) * t;
+                T Lt = ell * (-log(T(uniform01(D->w[S_CONV]))));
                 T dz = dl[2];
-                double depth = L * std::fabs(val(dz));
+                T deptht = Lt * (val(dz) < 0.0 ? -dz : dz);
+                double depth = val(deptht), L = val(Lt);
                 min_margin(out.margin_mm, depth - sc.t_si);
-                if (depth > sc.t_si) { out.flags = lost_flag(LOST_NOT_CONVERTED, (int)si); return; }
+                if (!(depth <= sc.t_si)) { out.flags = lost_flag(LOST_NOT_CONVERTED, (int)si); return; }
                 fx = fx + T(L) * dl[0];
                 fy = fy + T(L) * dl[1];
                 xc = val(fx); yc = val(fy);
                 int ns = (int)sc.sig.size();
-                double fs = depth / sc.t_si * (ns - 1);
-                int ks = std::min(ns - 2, std::max(0, (int)std::floor(fs)));
-                double ts = std::min(1.0, std::max(0.0, fs - ks));
-                double sigma = sc.sig[ks] * (1.0 - ts) + sc.sig[ks + 1] * ts;
-                double g = std::sqrt(-2.0 * std::log(uniform01(D->w[S_DIFF_A])));
-                double ph = 2.0 * M_PI * uniform01(D->w[S_DIFF_B]);
-                fx = fx + T(sigma * g * std::cos(ph));
-                fy = fy + T(sigma * g * std::sin(ph));
+                T fs = deptht / T(sc.t_si) * T((double)(ns - 1));
+                int ks = std::min(ns - 2, std::max(0, (int)std::floor(val(fs))));
+                T ts = fs - T((double)ks);
+                if (val(ts) < 0.0) ts = T(0.0);
+                if (val(ts) > 1.0) ts = T(1.0);
+                T sigma = T(sc.sig[ks]) * (T(1.0) - ts) + T(sc.sig[ks + 1]) * ts;
+                T g = sqrt(T(-2.0) * log(T(uniform01(D->w[S_DIFF_A]))));
+                T ph = T(2.0 * M_PI) * T(uniform01(D->w[S_DIFF_B]));
+                fx = fx + T(val(sigma * g * cos(ph)));
+                fy = fy + T(val(sigma * g * sin(ph)));
             }
             double ux = val(fx) - (sc.x0 - 0.5 * sc.nx * sc.pixel);
             double uy = val(fy) - (sc.y0 - 0.5 * sc.ny * sc.pixel);
@@ -568,7 +621,7 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
             min_margin(out.margin_mm, ux - px * sc.pixel); min_margin(out.margin_mm, ux - (px + 1) * sc.pixel);
             min_margin(out.margin_mm, uy - py * sc.pixel); min_margin(out.margin_mm, uy - (py + 1) * sc.pixel);
             out.x = fx; out.y = fy; out.xc = xc; out.yc = yc;
-            if (px < 0 || py < 0 || px >= sc.nx || py >= sc.ny) { out.flags = lost_flag(LOST_OFF_CHIP, (int)si); return; }
+            if (!(px >= 0 && py >= 0 && px < sc.nx && py < sc.ny)) { out.flags = lost_flag(LOST_OFF_CHIP, (int)si); return; }
             out.pix = ((double)sc.nx * sc.ny < 2.0e9) ? (int32_t)(py * sc.nx + px) : -1;
             out.flags = F_DETECTED;
             return;
@@ -577,7 +630,7 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
         double r = std::sqrt(val(p[0]) * val(p[0]) + val(p[1]) * val(p[1]));
         min_margin(out.margin_mm, r - s.r_out);
         if (s.r_in > 0.0) min_margin(out.margin_mm, r - s.r_in);
-        if (r > s.r_out || r < s.r_in) { out.flags = lost_flag(LOST_VIGNETTED, (int)si); return; }
+        if (!(r <= s.r_out && r >= s.r_in)) { out.flags = lost_flag(LOST_VIGNETTED, (int)si); return; }
         // coating accept-reject at the incidence angle and wavelength
         if (s.coating >= 0) {
             const Coat& C = sc.coat[s.coating];
@@ -595,7 +648,7 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
         if (s.kind == K_MIRROR) {
             reflect(dl, N);
         } else {
-            double n_next = refractive_index(sc, s.material, lam);
+            T n_next = refractive_index_t<T>(sc, s.material, lamT);
             if (!refract(dl, N, n_cur, n_next)) { out.flags = lost_flag(LOST_TIR, (int)si); return; }
             n_cur = n_next;
         }
@@ -843,7 +896,7 @@ void oracle_zernike(int j, int n, const double* rho, const double* theta, double
 
 int oracle_refract(const double* d, const double* N, double n1, double n2, double* out) {
     double dd[3] = {d[0], d[1], d[2]}, NN[3] = {N[0], N[1], N[2]};
-    if (!refract(dd, NN, n1, n2)) return 1;
+    if (!refract<double>(dd, NN, n1, n2)) return 1;
     for (int i = 0; i < 3; ++i) out[i] = dd[i];
     return 0;
 }
@@ -930,6 +983,43 @@ int oracle_trace_tangents(void* p, int n_src, const int* kind, const int* sed, c
             }
         }
     }
+    return 0;
+}
+
+// Algorithmic operation counts of the photon path (per photon, averaged over the given photons):
+// out[0..4] = add/sub, mul, div, sqrt, transcendental of sampling + atmosphere; out[5..9] the same for the
+// optics and sensor; out[10] = photons counted.  Newton stops at the paper's 0.01 um step here; the
+// central-difference screen gradients are table reads (precomputed, Sec. 3.2) and are not counted.
+int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const int* table, const double* xi,
+                     const double* eta, const double* z, const double* t0, const double* te, const double* a,
+                     const double* b, const double* pa, const uint64_t* first, const uint64_t* count, double* out) {
+    Scene* sc = (Scene*)p;
+    OpCount pre, opt;
+    double n = 0;
+    std::vector<SurfT<Cnt>> ST;
+    build_surfaces(*sc, ST);
+    for (int s = 0; s < n_src; ++s) {
+        Source src = make_source(kind, sed, table, xi, eta, z, t0, te, a, b, pa, s);
+        for (uint64_t k = 0; k < count[s]; ++k) {
+            Draws D = draw_photon(*sc, s, first[s] + k);
+            g_ops = OpCount();
+            Cnt X[3], Dir[3], lam, tt;
+            sample_and_atmosphere_t<Cnt>(*sc, src, D, X, Dir, lam, tt);
+            pre.add += g_ops.add; pre.mul += g_ops.mul; pre.div += g_ops.div; pre.sqrt += g_ops.sqrt; pre.special += g_ops.special;
+            Pre P;
+            for (int q = 0; q < 3; ++q) { P.x[q] = X[q].v; P.d[q] = Dir[q].v; }
+            P.lam = lam.v; P.t = tt.v;
+            g_ops = OpCount();
+            OpticsOut<Cnt> o;
+            optics_and_sensor(*sc, ST, P, &D, o);
+            opt.add += g_ops.add; opt.mul += g_ops.mul; opt.div += g_ops.div; opt.sqrt += g_ops.sqrt; opt.special += g_ops.special;
+            n += 1;
+        }
+    }
+    if (n == 0) return -1;
+    double v[10] = {pre.add, pre.mul, pre.div, pre.sqrt, pre.special, opt.add, opt.mul, opt.div, opt.sqrt, opt.special};
+    for (int i = 0; i < 10; ++i) out[i] = v[i] / n;
+    out[10] = n;
     return 0;
 }
 

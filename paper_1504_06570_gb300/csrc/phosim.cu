@@ -216,8 +216,8 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
     if (d->n_ell < 2 || d->n_sigma < 2 || !d->ell || !d->sigma) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->pupil_r_out > d->pupil_r_in) || d->pupil_r_in < 0.0) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->h_top > d->z_entrance) || !is_finite(d->h_top) || !is_finite(d->z_entrance)) return PHOSIM_ERR_INVALID_ARGUMENT;
-    for (int i = 0; i < d->n_ell; ++i) if (!(d->ell[i] > 0.0)) return PHOSIM_ERR_INVALID_ARGUMENT;
-    for (int i = 0; i < d->n_sigma; ++i) if (!(d->sigma[i] >= 0.0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < d->n_ell; ++i) if (!(d->ell[i] > 0.0) || !is_finite(d->ell[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < d->n_sigma; ++i) if (!(d->sigma[i] >= 0.0) || !is_finite(d->sigma[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
     phosim_scene* sc = new (std::nothrow) phosim_scene();
     if (!sc) return PHOSIM_ERR_OUT_OF_MEMORY;
     std::memset(&sc->base, 0, sizeof(sc->base));

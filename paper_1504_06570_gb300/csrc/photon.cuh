@@ -1,0 +1,341 @@
+// Per-photon forward path shared by the trace kernel and the adjoint kernel (Peterson et al. 2015,
+// Sec. 2.2-2.5): one definition, so the adjoint's recomputed forward pass takes exactly the trace's
+// decisions.
+#pragma once
+
+#include "phosim_device.cuh"
+
+namespace phosim {
+
+
+struct PhotonOut {
+    double x, y, xc, yc, lam;
+    uint32_t flags;
+    int pix;
+};
+
+__device__ __forceinline__ uint32_t lost(uint32_t reason, int surface) {
+    return (reason << 8) | ((uint32_t)(surface & 0xff) << 16);
+}
+
+__device__ __forceinline__ uint32_t word(const uint4& w, int k) {
+    return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
+}
+
+// Wavelength bin (Sec. 2.2): the first bin whose cumulative photon probability exceeds the draw, decided
+// on the integer draw against thresholds precomputed from the FP64 cumulative table.
+__device__ __forceinline__ int sed_bin(const unsigned long long* __restrict__ thr, int n, uint32_t w) {
+    int lo = 0, hi = n;   // thresholds thr[0..n-1]; answer in [0, n]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((unsigned long long)w < __ldg(thr + mid)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int wrap_index(long long i, int n) {
+    if ((n & (n - 1)) == 0) return (int)(i & (long long)(n - 1));
+    long long m = i % n;
+    return (int)(m < 0 ? m + n : m);
+}
+
+// Gradient of the phase at screen position (sx, sy), bilinear between central-difference nodes (Sec. 2.3.2)
+template <bool MIXED>
+__device__ __forceinline__ void screen_gradient(const DScale& S, double sx, double sy, double& gx, double& gy) {
+    const double fx = sx * S.inv_pix, fy = sy * S.inv_pix;
+    const double flx = floor(fx), fly = floor(fy);
+    const int n = S.n;
+    const int i0 = wrap_index((long long)flx, n), j0 = wrap_index((long long)fly, n);
+    const int i1 = (i0 + 1 == n) ? 0 : i0 + 1, j1 = (j0 + 1 == n) ? 0 : j0 + 1;
+    const size_t r0 = (size_t)j0 * n, r1 = (size_t)j1 * n;
+    if constexpr (MIXED) {
+        const float tx = (float)(fx - flx), ty = (float)(fy - fly);
+        const float2 a = __ldg(S.g32 + r0 + i0), b = __ldg(S.g32 + r0 + i1);
+        const float2 c = __ldg(S.g32 + r1 + i0), d = __ldg(S.g32 + r1 + i1);
+        const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
+        gx += (double)(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x);
+        gy += (double)(w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y);
+    } else {
+        const double tx = fx - flx, ty = fy - fly;
+        const double2 a = __ldg(S.g64 + r0 + i0), b = __ldg(S.g64 + r0 + i1);
+        const double2 c = __ldg(S.g64 + r1 + i0), d = __ldg(S.g64 + r1 + i1);
+        const double w00 = (1.0 - tx) * (1.0 - ty), w10 = tx * (1.0 - ty), w01 = (1.0 - tx) * ty, w11 = tx * ty;
+        gx += w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x;
+        gy += w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y;
+    }
+}
+
+__device__ __forceinline__ double lerp_table(const double* __restrict__ t, int n, double f) {
+    int k = (int)floor(f);
+    k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+    double w = f - k;
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    return __ldg(t + k) * (1.0 - w) + __ldg(t + k + 1) * w;
+}
+__device__ __forceinline__ float lerp_table_f(const float* __restrict__ t, int n, float f) {
+    int k = (int)floorf(f);
+    k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+    float w = f - (float)k;
+    w = w < 0.f ? 0.f : (w > 1.f ? 1.f : w);
+    return __ldg(t + k) * (1.f - w) + __ldg(t + k + 1) * w;
+}
+
+// Surfaces in order (Sec. 2.4.2).  FULL = apertures, coatings and the sensor; otherwise the bare rays that
+// give each source's chief-ray reference.
+// Forward state kept for the adjoint sweep (RECORD): the telescope-frame position and direction entering
+// each surface, and the conversion length and diffusion offset of the sensor.
+struct ForwardRecord {
+    double XD[PHOSIM_MAX_SURFACES][6];
+    double L, ox, oy;
+};
+
+template <bool MIXED, bool FULL, bool RECORD = false>
+__device__ __forceinline__ void optics(const TraceParams& P, double X[3], double D[3], double lam, uint4 w1, uint4 w2,
+                                       uint4 w3, PhotonOut& R, ForwardRecord* fr = nullptr) {
+    double n_cur = 1.0;
+    int glass_mat = -1;
+    double glass_n = 1.0;
+#pragma unroll 1
+    for (int si = 0; si < P.n_surf; ++si) {
+        const DSurface& S = P.surf[si];
+        if constexpr (RECORD) {
+            fr->XD[si][0] = X[0]; fr->XD[si][1] = X[1]; fr->XD[si][2] = X[2];
+            fr->XD[si][3] = D[0]; fr->XD[si][4] = D[1]; fr->XD[si][5] = D[2];
+        }
+        double p[3], dl[3];
+        to_surface(S, X, D, p, dl);
+        double l, zx, zy;
+        const uint32_t why = intersect(S, p, dl, l, zx, zy);
+        if (why) { R.flags = lost(why, si); return; }
+        p[0] = fma(l, dl[0], p[0]);
+        p[1] = fma(l, dl[1], p[1]);
+        p[2] = fma(l, dl[2], p[2]);
+        const double inn = 1.0 / sqrt(1.0 + zx * zx + zy * zy);
+        const double Nx = -zx * inn, Ny = -zy * inn, Nz = inn;
+        if (S.kind == PHOSIM_DETECTOR) {
+            const double hx = p[0] - P.xlo, hy = p[1] - P.ylo;
+            if (FULL && !(hx >= 0.0 && hy >= 0.0 && hx < P.nx * P.pixel && hy < P.ny * P.pixel)) {
+                R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
+                return;
+            }
+            double fx = p[0], fy = p[1];
+            R.xc = fx; R.yc = fy;
+            if (FULL && (P.flags & PHOSIM_SENSOR)) {
+                // refraction into the silicon, exponential conversion length (Sec. 2.4.2)
+                double L, sigma, gxd, gyd;
+                if constexpr (MIXED) {
+                    const float n_si = silicon_index_f((float)lam);
+                    if (!refract(dl, Nx, Ny, Nz, n_cur, (double)n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+                    const float ell = lerp_table_f(P.ell32, P.n_ell, (float)((lam - P.ell_lam0) * P.inv_ell_dlam));
+                    const float Lf = ell * -logf(u32of(w1.w));
+                    L = (double)Lf;
+                } else {
+                    const double n_si = silicon_index(lam);
+                    if (!refract(dl, Nx, Ny, Nz, n_cur, n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+                    const double ell = lerp_table(P.ell, P.n_ell, (lam - P.ell_lam0) * P.inv_ell_dlam);
+                    L = ell * -log(u64of(w1.w));
+                }
+                const double depth = L * fabs(dl[2]);
+                if (!(depth <= P.t_si)) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
+                fx = fma(L, dl[0], fx);
+                fy = fma(L, dl[1], fy);
+                R.xc = fx; R.yc = fy;
+                // lateral Gaussian diffusion (Sec. 2.5)
+                if constexpr (MIXED) {
+                    const float sg = lerp_table_f(P.sig32, P.n_sig, (float)(depth * P.sig_scale));
+                    const float g = sqrtf(-2.f * logf(u32of(w2.x)));
+                    float sn, cs;
+                    sincospif(2.f * u32of(w2.y), &sn, &cs);
+                    sigma = 1.0; gxd = (double)(sg * g * cs); gyd = (double)(sg * g * sn);
+                } else {
+                    sigma = lerp_table(P.sig, P.n_sig, depth * P.sig_scale);
+                    const double g = sqrt(-2.0 * log(u64of(w2.x)));
+                    double sn, cs;
+                    sincospi(2.0 * u64of(w2.y), &sn, &cs);
+                    gxd = g * cs; gyd = g * sn;
+                }
+                fx = fma(sigma, gxd, fx);
+                fy = fma(sigma, gyd, fy);
+                if constexpr (RECORD) { fr->L = L; fr->ox = sigma * gxd; fr->oy = sigma * gyd; }
+            }
+            R.x = fx; R.y = fy;
+            if (FULL) {
+                const double ux = fx - P.xlo, uy = fy - P.ylo;
+                const double px = floor(ux * P.inv_pixel), py = floor(uy * P.inv_pixel);
+                if (!(px >= 0.0 && py >= 0.0 && px < (double)P.nx && py < (double)P.ny)) {
+                    R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
+                    return;
+                }
+                R.pix = (int)py * P.nx + (int)px;
+            }
+            R.flags = PHOSIM_F_DETECTED;
+            return;
+        }
+        if (FULL) {
+            // clear aperture
+            const double r2 = p[0] * p[0] + p[1] * p[1];
+            if (!(r2 <= S.r_out2 && r2 >= S.r_in2)) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return; }
+            // coating accept-reject at the incidence angle and wavelength
+            if (S.coat_slot >= 0) {
+                const DCoating& C = P.coat[S.coating];
+                int it = 0;
+                if (C.nt > 1) {
+                    const double cosi = fabs(dl[0] * Nx + dl[1] * Ny + dl[2] * Nz);
+                    const double th = acos(fmin(1.0, cosi));
+                    it = (int)floor((th - C.th0) * C.inv_dth);
+                    it = it < 0 ? 0 : (it > C.nt - 1 ? C.nt - 1 : it);
+                }
+                int il = (int)floor((lam - C.lam0) * C.inv_dlam);
+                il = il < 0 ? 0 : (il > C.nl - 1 ? C.nl - 1 : il);
+                const double T = __ldg(C.T + (size_t)il * C.nt + it);
+                const int k = S.coat_slot;
+                const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
+                if (!(u64of(w) < T)) { R.flags = lost(PHOSIM_LOST_COATING, si); return; }
+            }
+        }
+        if (S.kind == PHOSIM_MIRROR) {
+            const double dn = dl[0] * Nx + dl[1] * Ny + dl[2] * Nz;
+            dl[0] = fma(-2.0 * dn, Nx, dl[0]);
+            dl[1] = fma(-2.0 * dn, Ny, dl[1]);
+            dl[2] = fma(-2.0 * dn, Nz, dl[2]);
+        } else {
+            const DMaterial& m = P.mat[S.material];
+            double n_next = 1.0;
+            if (m.kind == PHOSIM_SELLMEIER) {
+                if (glass_mat != S.material) { glass_n = sellmeier(m, lam); glass_mat = S.material; }
+                n_next = glass_n;
+            } else if (m.kind == PHOSIM_SILICON) {
+                n_next = silicon_index(lam);
+            }
+            if (!refract(dl, Nx, Ny, Nz, n_cur, n_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+            n_cur = n_next;
+        }
+        from_surface(S, p, dl, X, D);
+    }
+    R.flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
+}
+
+template <bool MIXED, bool RECORD = false>
+__device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource& s, int src, uint64_t i, PhotonOut& R,
+                                             ForwardRecord* fr = nullptr) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+    const uint4 w1 = philox(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
+    R.flags = 0; R.pix = -1; R.x = R.y = R.xc = R.yc = 0.0;
+    // time stamp (Sec. 2.2)
+    const double t = fma(s.t_exp, u64of(w1.x), s.t0);
+    // wavelength: cumulative photon-number table, blur within the bin, redshift (Sec. 2.2)
+    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.n_bins - 1, w0.z);
+    double lam;
+    if constexpr (MIXED) {
+        const float lo = (float)(P.sed_lam0 + bin * P.sed_dlam);
+        lam = (double)(fmaf(u32of(w0.w), (float)P.sed_dlam, lo) * (float)s.zfac);
+    } else {
+        lam = fma(u64of(w0.w), P.sed_dlam, P.sed_lam0 + bin * P.sed_dlam) * s.zfac;
+    }
+    R.lam = lam;
+    // direction: tangent-plane components, paraxial shape offset, renormalised (Sec. 2.2, 2.2.1)
+    double nx = s.xi, ny = s.eta;
+    if (s.kind == PHOSIM_SERSIC) {
+        if constexpr (MIXED) {
+            const float r = lerp_table_f(P.sersic32 + (size_t)s.table * P.sersic_K, P.sersic_K,
+                                         u32of(w1.y) * (float)P.sersic_K - 0.5f);
+            float sp, cp;
+            sincospif(2.f * u32of(w1.z), &sp, &cp);
+            const float dx = (float)s.a * r * cp, dy = (float)s.b * r * sp;
+            nx += (double)(dx * (float)s.cpa - dy * (float)s.spa);
+            ny += (double)(dx * (float)s.spa + dy * (float)s.cpa);
+        } else {
+            const double r = lerp_table(P.sersic + (size_t)s.table * P.sersic_K, P.sersic_K,
+                                        u64of(w1.y) * P.sersic_K - 0.5);
+            double sp, cp;
+            sincospi(2.0 * u64of(w1.z), &sp, &cp);
+            const double dx = s.a * r * cp, dy = s.b * r * sp;
+            nx += dx * s.cpa - dy * s.spa;
+            ny += dx * s.spa + dy * s.cpa;
+        }
+    } else if (s.kind == PHOSIM_GAUSS) {
+        if constexpr (MIXED) {
+            const float g = sqrtf(-2.f * logf(u32of(w1.y)));
+            float sp, cp;
+            sincospif(2.f * u32of(w1.z), &sp, &cp);
+            nx += (double)((float)s.a * g * cp);
+            ny += (double)((float)s.a * g * sp);
+        } else {
+            const double g = sqrt(-2.0 * log(u64of(w1.y)));
+            double sp, cp;
+            sincospi(2.0 * u64of(w1.z), &sp, &cp);
+            nx += s.a * g * cp;
+            ny += s.a * g * sp;
+        }
+    }
+    double nz = -sqrt(1.0 - nx * nx - ny * ny);
+    // pupil point on the annulus, on the nominal first surface, moved back to the top of the atmosphere
+    const double r = sqrt(fma(u64of(w0.x), P.pr_dr2, P.pr_in2));
+    double sp, cp;
+    sincospi(2.0 * u64of(w0.y), &sp, &cp);
+    double x = r * cp, y = r * sp;
+    double zs = 0.0, zx, zy;
+    sag(P.pupil_surf, x, y, zs, zx, zy);
+    double z = P.pupil_z + zs;
+    {
+        const double l = (P.h_top - z) / (-nz);
+        x = fma(-nx, l, x);
+        y = fma(-ny, l, y);
+        z = P.h_top;
+    }
+    // frozen-flow layers top to bottom: propagate, refractive kick from the screen gradient (Sec. 2.3)
+    if (P.flags & PHOSIM_ATMOSPHERE) {
+        double kick;
+        if constexpr (MIXED) {
+            kick = (double)((float)P.kick0 * exp2f(-0.2f * log2f((float)(lam / P.lam_ref))));
+        } else {
+            kick = P.kick0 * pow(lam / P.lam_ref, -0.2);
+        }
+#pragma unroll 1
+        for (int k = 0; k < P.n_layers; ++k) {
+            const DLayer& L = P.layer[k];
+            const double ll = (z - L.z) / (-nz);
+            x = fma(nx, ll, x);
+            y = fma(ny, ll, y);
+            z = L.z;
+            const double sx = fma(-L.vx, t, x), sy = fma(-L.vy, t, y);
+            double gx = 0.0, gy = 0.0;
+#pragma unroll 1
+            for (int q = 0; q < L.n_scales; ++q) screen_gradient<MIXED>(L.s[q], sx, sy, gx, gy);
+            nx = fma(kick, gx, nx);
+            ny = fma(kick, gy, ny);
+            nz = -sqrt(1.0 - nx * nx - ny * ny);
+        }
+    }
+    {
+        const double l = (z - P.z_ent) / (-nz);
+        x = fma(nx, l, x);
+        y = fma(ny, l, y);
+        z = P.z_ent;
+    }
+    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    double X[3] = {x, y, z}, D[3] = {nx, ny, nz};
+    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, R, fr);
+}
+
+
+// Which source owns launch tile t: binary search over the per-source tile prefix (lane 0, then broadcast).
+__device__ __forceinline__ int tile_source(const TraceParams& P, uint64_t t, int lane) {
+    int src = 0;
+    if (lane == 0) {
+        int lo = 0, hi = P.n_src - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.tile_prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        src = lo;
+    }
+    return __shfl_sync(0xffffffffu, src, 0);
+}
+
+}  // namespace phosim

@@ -192,7 +192,8 @@ def rajkanan_alpha_per_cm(lam_nm, T_K=173.0):
 
 def absorption_length_table(lam0=300.0, dlam=1.0, n=901, T_K=173.0):
     lam = lam0 + np.arange(n) * dlam
-    return 10.0 / rajkanan_alpha_per_cm(lam, T_K)      # mm
+    alpha = rajkanan_alpha_per_cm(lam, T_K)
+    return 10.0 / np.maximum(alpha, 1e-5)              # mm; below the band gap: 1 km, i.e. never converts
 
 
 def sersic_bn(n):
@@ -384,3 +385,53 @@ def filter_coating(lo=550.0, hi=700.0, T_in=0.95, lam0=300.0, nlam=900):
     lam = lam0 + np.arange(nlam) + 0.5
     T = np.where((lam > lo) & (lam < hi), T_in, 0.0)
     return Coating(lam0=lam0, dlam=1.0, theta0=0.0, dtheta=math.pi / 2, table=T[:, None].copy())
+
+
+# ----------------------------------------------------------------------------------------------------------
+# the large workload: synthetic three-mirror survey telescope, seven-layer atmosphere, 1000 stars
+# ----------------------------------------------------------------------------------------------------------
+
+THREE_MIRROR_JSON = os.path.join(DATA_DIR, "three_mirror_camera.json")
+
+
+def three_mirror_optics():
+    """Surfaces and media of the synthetic 8.4 m three-mirror telescope and three-lens camera (f/1.23,
+    plate scale ~20 arcsec/mm), with the 550-700 nm top-hat filter coating on the filter's first face."""
+    d, surfaces, materials = load_optics_json(THREE_MIRROR_JSON)
+    return d, surfaces, materials
+
+
+def star_field(n_stars, n_total, rng, half_field_deg=0.1, m_lo=16.0, m_hi=22.0, t_exp=15.0):
+    """Stars uniform over a square field, magnitudes from N(<m) ~ 10^(0.3 m) on [m_lo, m_hi], photon
+    counts ~ 10^(-0.4 m) normalised to n_total, one blackbody SED per star (T uniform 3000-10000 K)."""
+    h = math.radians(half_field_deg)
+    xi, eta = rng.uniform(-h, h, n_stars), rng.uniform(-h, h, n_stars)
+    a, b = 10 ** (0.3 * m_lo), 10 ** (0.3 * m_hi)
+    m = np.log10(a + rng.random(n_stars) * (b - a)) / 0.3
+    w = 10 ** (-0.4 * m)
+    counts = np.floor(w / w.sum() * n_total).astype(np.uint64)
+    counts[np.argmax(counts)] += np.uint64(n_total - int(counts.sum()))
+    temps = rng.uniform(3000.0, 10000.0, n_stars)
+    src = point_sources(xi, eta, counts, sed=np.arange(n_stars), t_exp=t_exp)
+    return src, temps, m
+
+
+def three_mirror_scene(n_stars=1000, n_total=100_000_000, seed=2, atmosphere=True, sensor=True, screen_seed=7,
+                       fine_n=4096, coarse_n=1024, sources=None):
+    """The large workload: 1000 stars (1e8 photons, 300-1200 nm blackbodies) through seven von Karman
+    layers (L0 = 20 m, 4096^2 at 1 cm plus 1024^2 at 64 cm each) and the three-mirror telescope onto one
+    4096 x 4096 chip of 10 um pixels.  fine_n / coarse_n shrink the screens (pixel sizes kept) for tests."""
+    d, surfaces, materials = three_mirror_optics()
+    rng = np.random.default_rng(seed)
+    if sources is None:
+        sources, temps, _ = star_field(n_stars, n_total, rng)
+    else:
+        temps = rng.uniform(3000.0, 10000.0, int(np.max(sources.sed)) + 1)
+    layers = von_karman_layers(seed=screen_seed, fine_n=fine_n, coarse_n=coarse_n,
+                               coarse_pix_mm=640.0 * 1024 / coarse_n * (fine_n / 4096)) if atmosphere else []
+    det = Detector(nx=4096, ny=4096, pixel=0.01, t_si=0.1, ell_lam0=300.0, ell_dlam=1.0,
+                   ell=absorption_length_table(300.0, 1.0, 901), sigma=np.array([0.003, 0.003]))
+    return Scene(seed=seed, pupil_r_in=d["pupil_r_in"], pupil_r_out=d["pupil_r_out"], surfaces=surfaces,
+                 materials=materials, coatings=[filter_coating(550.0, 700.0, 0.95, lam0=300.0, nlam=900)],
+                 detector=det, layers=layers, sed_lam0=300.0, sed_dlam=1.0, sed_flux=sed_tables(temps, 300.0, 1.0, 900),
+                 sersic=np.ones((1, 4)), sources=sources, atmosphere=atmosphere, sensor=sensor, z_entrance=ATM_Z0_MM - 1000.0)
