@@ -221,6 +221,29 @@ phosim_status phosim_set_schedule(phosim_scene* scene, int threads_per_block, in
    reason r = 1..7 (PHOSIM_LOST_*).  n >= 9.  Synchronises the scene's last stream. */
 phosim_status phosim_get_counters(phosim_scene* scene, uint64_t* out, int n);
 
+/* Allocation-free variant of phosim_trace (the paper has no counterpart; it exists for callers of this
+   library that cannot call cudaMalloc, for example an application whose device memory is owned by an
+   outside pool that budgets every byte, or a latency-critical loop where an allocation would synchronise
+   the device and stall other work).  Same photons, same kernels and same results as phosim_trace, with
+   these differences:
+   - its per-call scratch (source list, tile prefix, work counters) lives in one file-scope device array of
+     PHOSIM_NOALLOC_SCRATCH_BYTES held by every GPU that loads the library until the process exits; it
+     allocates no memory and calls no allocating routine;
+   - n_src must be <= PHOSIM_NOALLOC_MAX_SOURCES (else PHOSIM_ERR_LIMIT), and image must be device memory
+     (else PHOSIM_ERR_INVALID_ARGUMENT: a host image would need a staging buffer);
+   - the first call on a device looks up the array's device address on that device (set-up, once per
+     device, with that device current); make that first call before any stream capture;
+   - every call shares the array and leaves its contents behind; each call clears the counters it needs.
+     Calls whose GPU work overlaps (different streams, or different threads on one device) race on the
+     array and must be serialised by the caller;
+   - phosim_get_counters does not report its photons.
+   Errors: as phosim_trace, plus LIMIT above. */
+#define PHOSIM_NOALLOC_MAX_SOURCES 4096
+#define PHOSIM_NOALLOC_SCRATCH_BYTES (1u << 20)
+phosim_status phosim_trace_noalloc(phosim_scene* scene, const phosim_source* sources, int n_src,
+                                   const uint64_t* n_photons, const uint64_t* first, uint32_t* image,
+                                   phosim_photon_record* records, double* moments, void* stream);
+
 void phosim_destroy_scene(phosim_scene* scene);
 const char* phosim_status_string(phosim_status status);
 
