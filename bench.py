@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain FP64 path")
     ap.add_argument("--sample", type=int, default=8000, help="oracle photons per star for the CPU leg")
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision-split, batched and adjoint legs")
+    ap.add_argument("--batched-scale", type=float, default=1.0, help="photon scale of the batched workload")
     ap.add_argument("--fine-n", type=int, default=4096, help="fine screen size (smaller: profiling case)")
     ap.add_argument("--coarse-n", type=int, default=1024, help="coarse screen size (smaller: profiling case)")
     return ap.parse_args()
@@ -144,6 +146,108 @@ def moment_errors(gpu_m, ora_rec, n_src):
             "max_de1": float(a[:, 2].max()), "max_de2": float(a[:, 3].max()), "max_rel_count": float(a[:, 4].max())}
 
 
+def precision_split(sc, mixed, plain, counts, dev):
+    """Mixed against all-FP64 on the same photons (every photon of the workload): per-photon distance of the
+    final positions (pixels) for photons both detect, fate agreement, and per-star moment differences."""
+    import torch
+    from paper_1504_06570_gb300 import phosim as P
+    n = int(counts.sum())
+    d = sc.detector
+    out = {}
+    recs, moms = [], []
+    for scn in (mixed, plain):
+        rec = torch.empty(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
+        mom = torch.zeros((len(counts), P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+        scn.trace(img, rec, mom, n_photons=counts)
+        torch.cuda.synchronize(dev)
+        recs.append(rec)
+        moms.append(mom.cpu().numpy())
+        del img
+    a, b = recs
+    # 48-byte records: x, y, xc, yc, lambda (float64), flags (uint32), pixel (int32)
+    xa, ya = a.view(torch.float64).view(-1, 6)[:, 0], a.view(torch.float64).view(-1, 6)[:, 1]
+    xb, yb = b.view(torch.float64).view(-1, 6)[:, 0], b.view(torch.float64).view(-1, 6)[:, 1]
+    fa = a.view(torch.int32).view(-1, 12)[:, 10]
+    fb = b.view(torch.int32).view(-1, 12)[:, 10]
+    both = ((fa & 1) == 1) & ((fb & 1) == 1)
+    err = torch.maximum((xa - xb).abs(), (ya - yb).abs())[both] / d.pixel
+    err, _ = torch.sort(err)
+    q = lambda f: float(err[min(len(err) - 1, int(f * (len(err) - 1)))].item())
+    out["photons"] = n
+    out["detected_by_both"] = int(both.sum().item())
+    out["fate_agreement"] = float((fa == fb).double().mean().item())
+    out["position_error_px"] = {"p50": q(0.5), "p90": q(0.9), "p99": q(0.99), "p99.9": q(0.999),
+                                "p99.999": q(0.99999), "max": float(err[-1].item())}
+    gm, gp = P.derived_moments(moms[0]), P.derived_moments(moms[1])
+    T = gp[:, 3] + gp[:, 5]
+    ok = gp[:, 0] > 100
+    e1m = (gm[:, 3] - gm[:, 5]) / (gm[:, 3] + gm[:, 5]); e1p = (gp[:, 3] - gp[:, 5]) / T
+    e2m = 2 * gm[:, 4] / (gm[:, 3] + gm[:, 5]); e2p = 2 * gp[:, 4] / T
+    out["per_star_vs_fp64"] = {"stars": int(ok.sum()), "max_de1": float(np.abs(e1m - e1p)[ok].max()),
+                               "max_de2": float(np.abs(e2m - e2p)[ok].max()),
+                               "max_rel_size": float(np.abs((gm[:, 3] + gm[:, 5]) / T - 1)[ok].max()),
+                               "max_centroid_px": float(np.hypot(gm[:, 1] - gp[:, 1], gm[:, 2] - gp[:, 2])[ok].max() / d.pixel)}
+    del recs, a, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched_leg(sc2, args, dev, stream):
+    """10^4 stars and Sersic galaxies with counts log-uniform 1e2-1e7 plus 1e9 sky photons on 15 arcsec
+    Gaussian nodes, one persistent launch per step with the autotuned schedule (same optics and atmosphere)."""
+    import torch
+    from paper_1504_06570_gb300 import inputs as I
+    from paper_1504_06570_gb300 import phosim as P
+    t0 = time.perf_counter()
+    sc = I.batched_scene(fine_n=16, coarse_n=16, photon_scale=args.batched_scale)
+    sc.layers = sc2.layers
+    scn = P.Scene(sc, P.MIXED, early_reject=True)
+    threads, tile = scn.autotune(sample_photons=20_000_000)
+    d = sc.detector
+    img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
+    mom = torch.zeros((len(sc.sources), P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+    scn.trace(img, None, mom, stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    steps = 2
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        scn.trace(img, None, mom, stream=stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    n = int(sc.sources.n_photons.sum())
+    scn.close()
+    kinds = np.bincount(sc.sources.kind, minlength=3)
+    return {"workload": f"{kinds[0]} stars + {kinds[1]} Sersic galaxies (counts log-uniform 1e2-1e7) + {kinds[2]} "
+                        f"sky nodes (1e9 photons), x{args.batched_scale} photons", "photons_per_step": n,
+            "value": n / (ms / 1e3), "unit": "photons/s", "ms_per_step": ms, "autotuned": {"threads": threads, "tile": tile},
+            "setup_s": round(time.perf_counter() - t0, 1)}
+
+
+def adjoint_leg(dev, stream):
+    """Adjoint raytrace on 64 stars on an 8 x 8 grid, 1e6 photons each, no atmosphere, 97 per-surface
+    parameters (M2 and each camera surface dx, dy, tx, ty; Z4-Z22 of the three mirrors)."""
+    import torch
+    from paper_1504_06570_gb300 import inputs as I
+    from paper_1504_06570_gb300 import phosim as P
+    sc, params, camera = I.grad_grid_scene()
+    scn = P.Scene(sc, P.PLAIN_FP64)
+    dL = np.random.default_rng(0).normal(size=(len(sc.sources), 5))
+    scn.grad(dL, params)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    reps = 2
+    for _ in range(reps):
+        g, m = scn.grad(dL, params)
+    dt = (time.perf_counter() - t0) / reps
+    n = int(sc.sources.n_photons.sum())
+    scn.close()
+    return {"photons": n, "params": len(params), "value": n / dt, "unit": "photons/s (forward moments + adjoint)",
+            "s_per_gradient": dt, "detected": int(m[:, 0].sum())}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -187,11 +291,13 @@ def main():
     sc = workload(args.photons, rank, args.fine_n, args.coarse_n)
     n_src = len(sc.sources)
     # weak scaling: rank r traces photons [r N, (r + 1) N) of every star (a longer exposure per GPU)
-    counts = sc.sources.n_photons.copy()
-    first = (counts * np.uint64(rank)).astype(np.uint64)
+    from paper_1504_06570_gb300 import sharding
+    first, counts = sharding.rank_photon_range(sc.sources.n_photons, rank, world)
     photons = int(counts.sum())
-    mixed = P.Scene(sc, P.MIXED)
-    plain = P.Scene(sc, P.PLAIN_FP64)
+    # both precisions with the paper's dynamic transmission (early coating rejection), which leaves the
+    # detected photons unchanged
+    mixed = P.Scene(sc, P.MIXED, early_reject=True)
+    plain = P.Scene(sc, P.PLAIN_FP64, early_reject=True)
     setup_s = time.perf_counter() - t_setup
     d = sc.detector
     img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
@@ -249,10 +355,7 @@ def main():
     ms_mixed = float(per_mixed.max()) if world == 1 else float(per_mixed.mean())
     t_mixed = float(per_mixed.sum()) / 1e3
     t_plain = float(per_plain.sum()) / 1e3
-    if world > 1:
-        t = torch.tensor([t_mixed, t_plain, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_mixed, t_plain, e2e_s = t.tolist()
+    t_mixed, t_plain, e2e_s = sharding.max_over_ranks([t_mixed, t_plain, e2e_s], device=dev)
     value = photons * world * args.steps / t_mixed
     plain_value = photons * world * args.plain_steps / t_plain
     counters = mixed.counters()
@@ -282,7 +385,7 @@ def main():
     if not args.no_oracle:
         from oracle import oracle as O
         o = O.Oracle(sc)
-        ops = o.count_ops(count=np.minimum(counts, np.uint64(20)))
+        ops = o.count_ops(count=np.minimum(counts, np.uint64(50)), early_reject=True)
         fl_pre = sum(v for k, v in ops["pre"].items() if k != "transcendental")
         fl_opt = sum(v for k, v in ops["optics"].items() if k != "transcendental")
         kernel_s = float(np.mean(per_mixed)) / 1e3
@@ -290,8 +393,9 @@ def main():
         peak = fp64_rate or FP64_NOMINAL_TFLOPS
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak, "traffic": None,
-                            "note": (f"FP64 optics flops {fl_opt:.0f}/photon (oracle op count; +{fl_pre:.0f} sampling and "
-                                     f"atmosphere flops, mostly FP32 here) over the mixed step time; peak = "
+                            "note": (f"FP64 optics flops {fl_opt:.0f} per sampled photon (oracle op count with the dynamic "
+                                     f"transmission rejection; +{fl_pre:.0f} sampling and atmosphere flops, mostly FP32 "
+                                     f"here) over the mixed step time; peak = "
                                      + ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)"))}
         line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) * photons / (float(np.mean(per_plain)) / 1e3) / 1e12,
                                        "peak": peak, "unit": "TFLOP/s"}
@@ -307,6 +411,10 @@ def main():
                 torch.cuda.synchronize(dev)
                 errs[name] = moment_errors(m2.cpu().numpy(), rec, n_src)
             line["moment_error_vs_oracle"] = errs
+    if not args.no_extras and rank == 0:
+        line["precision_split"] = precision_split(sc, mixed, plain, counts, dev)
+        line["batched"] = batched_leg(sc, args, dev, stream)
+        line["adjoint"] = adjoint_leg(dev, stream)
     print(json.dumps(line))
     mixed.close()
     plain.close()

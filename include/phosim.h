@@ -58,6 +58,11 @@ enum {
 /* scene flags */
 #define PHOSIM_ATMOSPHERE 1u     /* apply the phase-screen layers */
 #define PHOSIM_SENSOR 2u         /* silicon conversion and diffusion; otherwise the detector-surface hit */
+#define PHOSIM_EARLY_REJECT 4u   /* dynamic transmission (Sec. 3.2): decide each coating's accept draw against
+                                    the largest transmission over incidence angles at the photon's wavelength
+                                    before propagating it.  The detected photons, image and moments are
+                                    unchanged; a photon rejected this way is reported as a COATING loss at
+                                    that surface even if an earlier surface would have vignetted it. */
 
 /* record flags (phosim_photon_record.flags): bit 0 = detected; otherwise bits 8..15 hold the reason the
    photon was dropped and bits 16..23 the index of the surface where it happened */
@@ -216,6 +221,16 @@ phosim_status phosim_grad(phosim_scene* scene, const phosim_source* sources, int
 
 /* Launch shape of the trace kernel: threads per block and photons per warp tile (0 = keep current). */
 phosim_status phosim_set_schedule(phosim_scene* scene, int threads_per_block, int tile_photons);
+
+/* Autotuner of the trace launch: traces a sample of the workload (about sample_photons photons, spread
+   over the sources in proportion to their counts) with each candidate (threads per block in {64, 128, 256},
+   photons per warp tile in {64, 256, 1024, 4096}), times each on the stream with CUDA events (best of
+   two), and keeps the fastest through phosim_set_schedule.  Results never depend on the schedule (the
+   random numbers are counter-based), only the speed does.  out_threads / out_tile may be NULL.
+   Errors: as phosim_trace. */
+phosim_status phosim_autotune(phosim_scene* scene, const phosim_source* sources, int n_src,
+                              const uint64_t* n_photons, uint64_t sample_photons, void* stream,
+                              int* out_threads, int* out_tile);
 
 /* Totals of the last phosim_trace: out[0] = photons traced, out[1] = detected, out[1 + r] = dropped for
    reason r = 1..7 (PHOSIM_LOST_*).  n >= 9.  Synchronises the scene's last stream. */

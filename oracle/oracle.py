@@ -191,8 +191,9 @@ class Oracle:
             raise RuntimeError("oracle_pre_optics failed")
         return pos, d, lam, t
 
-    def count_ops(self, sources=None, first=None, count=None):
-        """Algorithmic operations per photon: dict of sampling+atmosphere and optics+sensor counts."""
+    def count_ops(self, sources=None, first=None, count=None, early_reject=False):
+        """Algorithmic operations per sampled photon: dict of sampling+atmosphere and optics+sensor counts.
+        early_reject: photons the dynamic transmission test drops before propagation count no operations."""
         src = self.scene.sources if sources is None else sources
         n = len(src)
         first = np.zeros(n, np.uint64) if first is None else _arr(first, np.uint64)
@@ -200,7 +201,7 @@ class Oracle:
         out = np.zeros(11)
         u64p = C.POINTER(C.c_uint64)
         rc = self.L.oracle_count_ops(self.h, C.c_int(n), *self._src_args(src), first.ctypes.data_as(u64p),
-                                     count.ctypes.data_as(u64p), _dp(out))
+                                     count.ctypes.data_as(u64p), C.c_int(int(early_reject)), _dp(out))
         if rc:
             raise RuntimeError("oracle_count_ops failed")
         keys = ("add", "mul", "div", "sqrt", "transcendental")

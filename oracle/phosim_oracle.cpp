@@ -992,7 +992,8 @@ int oracle_trace_tangents(void* p, int n_src, const int* kind, const int* sed, c
 // central-difference screen gradients are table reads (precomputed, Sec. 3.2) and are not counted.
 int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const int* table, const double* xi,
                      const double* eta, const double* z, const double* t0, const double* te, const double* a,
-                     const double* b, const double* pa, const uint64_t* first, const uint64_t* count, double* out) {
+                     const double* b, const double* pa, const uint64_t* first, const uint64_t* count, int early,
+                     double* out) {
     Scene* sc = (Scene*)p;
     OpCount pre, opt;
     double n = 0;
@@ -1002,6 +1003,25 @@ int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const 
         Source src = make_source(kind, sed, table, xi, eta, z, t0, te, a, b, pa, s);
         for (uint64_t k = 0; k < count[s]; ++k) {
             Draws D = draw_photon(*sc, s, first[s] + k);
+            n += 1;
+            if (early) {
+                // dynamic transmission (Sec. 3.2): a photon whose coating draw is not below the largest
+                // transmission over angles at its wavelength is dropped before any propagation
+                Pre P0;
+                sample_and_atmosphere(*sc, src, D, P0);
+                bool rejected = false;
+                int kq = 0;
+                for (const Surf& sf : sc->surf) {
+                    if (sf.coating < 0 || sf.kind == K_DETECTOR) continue;
+                    const Coat& C = sc->coat[sf.coating];
+                    int il = std::min(C.nl - 1, std::max(0, (int)std::floor((P0.lam - C.lam0) / C.dlam)));
+                    double tmax = 0.0;
+                    for (int it = 0; it < C.nt; ++it) tmax = std::max(tmax, C.T[(size_t)il * C.nt + it]);
+                    if (!(uniform01(D.w[S_COAT0 + kq]) < tmax)) rejected = true;
+                    ++kq;
+                }
+                if (rejected) continue;
+            }
             g_ops = OpCount();
             Cnt X[3], Dir[3], lam, tt;
             sample_and_atmosphere_t<Cnt>(*sc, src, D, X, Dir, lam, tt);
@@ -1013,7 +1033,6 @@ int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const 
             OpticsOut<Cnt> o;
             optics_and_sensor(*sc, ST, P, &D, o);
             opt.add += g_ops.add; opt.mul += g_ops.mul; opt.div += g_ops.div; opt.sqrt += g_ops.sqrt; opt.special += g_ops.special;
-            n += 1;
         }
     }
     if (n == 0) return -1;

@@ -12,6 +12,7 @@
 
 #include "phosim_device.cuh"
 #include "phosim_scene.hpp"
+#include "grad.hpp"
 
 using namespace phosim;
 
@@ -102,6 +103,30 @@ void rotation(const double* pert, double M[9]) {
         for (int k = 0; k < 3; ++k) M[3 * i + k] = R[k][i];
 }
 
+// derivatives of M = R^T with respect to tx, ty, tz
+void rotation_derivatives(const double* pert, double dM[3][9]) {
+    const double cx = std::cos(pert[3]), sx = std::sin(pert[3]);
+    const double cy = std::cos(pert[4]), sy = std::sin(pert[4]);
+    const double cz = std::cos(pert[5]), sz = std::sin(pert[5]);
+    const double Rx[3][3] = {{1, 0, 0}, {0, cx, -sx}, {0, sx, cx}}, dRx[3][3] = {{0, 0, 0}, {0, -sx, -cx}, {0, cx, -sx}};
+    const double Ry[3][3] = {{cy, 0, sy}, {0, 1, 0}, {-sy, 0, cy}}, dRy[3][3] = {{-sy, 0, cy}, {0, 0, 0}, {-cy, 0, -sy}};
+    const double Rz[3][3] = {{cz, -sz, 0}, {sz, cz, 0}, {0, 0, 1}}, dRz[3][3] = {{-sz, -cz, 0}, {cz, -sz, 0}, {0, 0, 0}};
+    auto mul = [](const double A[3][3], const double B[3][3], double C[3][3]) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                C[i][j] = 0.0;
+                for (int k = 0; k < 3; ++k) C[i][j] += A[i][k] * B[k][j];
+            }
+    };
+    double T[3][3], D[3][3];
+    mul(Ry, dRx, T); mul(Rz, T, D);
+    for (int i = 0; i < 3; ++i) for (int k = 0; k < 3; ++k) dM[0][3 * i + k] = D[k][i];
+    mul(dRy, Rx, T); mul(Rz, T, D);
+    for (int i = 0; i < 3; ++i) for (int k = 0; k < 3; ++k) dM[1][3 * i + k] = D[k][i];
+    mul(Ry, Rx, T); mul(dRz, T, D);
+    for (int i = 0; i < 3; ++i) for (int k = 0; k < 3; ++k) dM[2][3 * i + k] = D[k][i];
+}
+
 phosim_status build_surface(const phosim_surface& s, DSurface& d) {
     std::memset(&d, 0, sizeof(d));
     d.kind = s.kind;
@@ -113,6 +138,7 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
         flags |= SF_CONIC;
         d.c = 1.0 / s.R;
         d.k1c2 = (1.0 + s.kappa) / (s.R * s.R);
+        d.kc = (1.0 + s.kappa) / s.R;
     }
     for (int i = 0; i < 4; ++i) {
         d.ao[i] = s.alpha[2 * i];        // alpha_3, 5, 7, 9
@@ -120,6 +146,7 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
         if (d.ao[i] != 0.0) flags |= SF_ODD;
         if (d.ae[i] != 0.0) flags |= SF_EVEN;
     }
+    if (s.zern_rnorm > 0.0) d.zinv = 1.0 / s.zern_rnorm;
     if (s.n_zern > 0 && s.zern_rnorm > 0.0) {
         double P[7][7] = {}, Pj[7][7];
         bool any = false;
@@ -132,13 +159,13 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
         }
         if (any) {
             flags |= SF_ZERN;
-            d.zinv = 1.0 / s.zern_rnorm;
             int off = 0;
             for (int b = 0; b < 7; ++b)
                 for (int a = 0; a + b < 7; ++a) d.zp[off++] = P[b][a];
         }
     }
     if (!(flags & (SF_CONIC | SF_EVEN | SF_ODD | SF_ZERN))) flags |= SF_FLAT_ONLY;
+    if (s.pert[3] != 0.0 || s.pert[4] != 0.0 || s.pert[5] != 0.0) flags |= SF_ROTATED;
     d.flags = flags;
     rotation(s.pert, d.M);
     d.o[0] = s.pert[0];
@@ -284,6 +311,8 @@ void phosim_destroy_scene(phosim_scene* sc) {
     cudaFree(sc->d_prefix);
     cudaFree(sc->d_counters);
     cudaFree(sc->d_stage);
+    cudaFree(sc->d_grad_scratch);
+    cudaFree(sc->d_mom_scratch);
     (void)cudaGetLastError();
     delete sc;
 }
@@ -316,6 +345,7 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
         build_surface(surf[i], P.surf[i]);
         if (surf[i].coating >= 0 && surf[i].kind != PHOSIM_DETECTOR) {
             if (coated >= PHOSIM_MAX_COATED) return PHOSIM_ERR_LIMIT;
+            P.coated_surface[coated] = i;
             P.surf[i].coat_slot = coated++;
         }
     }
@@ -332,16 +362,36 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
     }
     std::vector<void*> mem;
     for (int k = 0; k < n_coat; ++k) {
-        double* d;
-        phosim_status st = upload(mem, coats[k].table, (size_t)coats[k].n_lambda * coats[k].n_theta, &d);
+        double *d, *dmax;
+        const int nl = coats[k].n_lambda, nt = coats[k].n_theta;
+        std::vector<double> tmax((size_t)nl, 0.0);
+        for (int il = 0; il < nl; ++il)
+            for (int it = 0; it < nt; ++it) tmax[il] = std::max(tmax[il], coats[k].table[(size_t)il * nt + it]);
+        phosim_status st = upload(mem, coats[k].table, (size_t)nl * nt, &d);
+        if (st == PHOSIM_OK) st = upload(mem, tmax.data(), tmax.size(), &dmax);
         if (st != PHOSIM_OK) { free_all(mem); return st; }
         DCoating& C = P.coat[k];
         C.lam0 = coats[k].lam0; C.inv_dlam = 1.0 / coats[k].dlam;
         C.th0 = coats[k].theta0; C.inv_dth = 1.0 / coats[k].dtheta;
         C.nl = coats[k].n_lambda; C.nt = coats[k].n_theta;
         C.T = d;
+        C.Tmax = dmax;
     }
     P.n_coat = n_coat;
+    {
+        std::vector<double> zm((size_t)PHOSIM_MAX_ZERNIKE * kZPoly, 0.0);
+        for (int j = 1; j <= PHOSIM_MAX_ZERNIKE; ++j) {
+            double Pj[7][7];
+            zernike_monomials(j, Pj);
+            int off = 0;
+            for (int b = 0; b < 7; ++b)
+                for (int a = 0; a + b < 7; ++a) zm[(size_t)(j - 1) * kZPoly + off++] = Pj[b][a];
+        }
+        double* dz;
+        phosim_status st = upload(mem, zm.data(), zm.size(), &dz);
+        if (st != PHOSIM_OK) { free_all(mem); return st; }
+        sc->d_zmono = dz;
+    }
     free_all(sc->optics_mem);
     sc->optics_mem = mem;
     sc->base = P;
@@ -477,6 +527,63 @@ phosim_status phosim_set_schedule(phosim_scene* sc, int threads, int tile) {
     return PHOSIM_OK;
 }
 
+phosim_status phosim_autotune(phosim_scene* sc, const phosim_source* src, int n_src, const uint64_t* n_photons,
+                              uint64_t sample, void* stream, int* out_threads, int* out_tile) {
+    if (!sc || n_src < 1 || !src || !n_photons || sample < 1) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
+    uint64_t total = 0;
+    for (int s = 0; s < n_src; ++s) total += n_photons[s];
+    if (total == 0) return PHOSIM_ERR_INVALID_ARGUMENT;
+    std::vector<uint64_t> cnt((size_t)n_src);
+    for (int s = 0; s < n_src; ++s) {
+        const double f = (double)n_photons[s] * (double)sample / (double)total;
+        cnt[s] = n_photons[s] ? std::max<uint64_t>(1, (uint64_t)std::llround(f)) : 0;
+        cnt[s] = std::min(cnt[s], n_photons[s]);
+    }
+    const size_t img_bytes = (size_t)sc->base.nx * sc->base.ny * sizeof(uint32_t);
+    if (sc->cap_stage < img_bytes) {
+        cudaFree(sc->d_stage);
+        sc->d_stage = nullptr; sc->cap_stage = 0;
+        CU(cudaMalloc(&sc->d_stage, img_bytes));
+        sc->cap_stage = img_bytes;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    const int saved_threads = sc->threads, saved_tile = sc->tile_photons;
+    const int threads_c[3] = {64, 128, 256};
+    const int tiles_c[4] = {64, 256, 1024, 4096};
+    float best = 1e30f;
+    int bt = saved_threads, bk = saved_tile;
+    phosim_status rs = PHOSIM_OK;
+    for (int a = 0; a < 3 && rs == PHOSIM_OK; ++a)
+        for (int b = 0; b < 4 && rs == PHOSIM_OK; ++b) {
+            sc->threads = threads_c[a];
+            sc->tile_photons = tiles_c[b];
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3 && rs == PHOSIM_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rs = phosim_trace(sc, src, n_src, cnt.data(), nullptr, sc->d_stage, nullptr, nullptr, stream);
+                cudaEventRecord(e1, st);
+                if (rs == PHOSIM_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_best = std::min(ms_best, ms);     // the first run warms up
+                }
+            }
+            if (ms_best < best) { best = ms_best; bt = threads_c[a]; bk = tiles_c[b]; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    sc->threads = rs == PHOSIM_OK ? bt : saved_threads;
+    sc->tile_photons = rs == PHOSIM_OK ? bk : saved_tile;
+    if (out_threads) *out_threads = sc->threads;
+    if (out_tile) *out_tile = sc->tile_photons;
+    return rs;
+}
+
 phosim_status phosim_get_counters(phosim_scene* sc, uint64_t* out, int n) {
     if (!sc || !out || n < kNumCounters) return PHOSIM_ERR_INVALID_ARGUMENT;
     unsigned long long h[kNumCounters];
@@ -585,9 +692,125 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
 phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src, const uint64_t* n_photons,
                           const double* dL, const int32_t* ps, const int32_t* pf, int n_params, double* grad,
                           double* moments_out, void* stream) {
-    (void)sc; (void)src; (void)n_src; (void)n_photons; (void)dL; (void)ps; (void)pf; (void)n_params;
-    (void)grad; (void)moments_out; (void)stream;
-    return PHOSIM_ERR_UNSUPPORTED;
+    if (!sc || n_src < 1 || !src || !n_photons || !dL || !ps || !pf || n_params < 1 || !grad)
+        return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
+    if (n_params > kMaxGradParams) return PHOSIM_ERR_LIMIT;
+    const TraceParams& B = sc->base;
+    GradParams G;
+    std::memset(&G, 0, sizeof(G));
+    G.n_params = n_params;
+    for (int s = 0; s < PHOSIM_MAX_SURFACES; ++s)
+        for (int f = 0; f < 6; ++f) G.pert_p[s][f] = -1;
+    for (int p = 0; p < n_params; ++p) {
+        const int s = ps[p], f = pf[p];
+        if (s < 0 || s >= B.n_surf) return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (f >= 0 && f < 6) {
+            if (G.pert_p[s][f] >= 0) return PHOSIM_ERR_INVALID_ARGUMENT;
+            G.pert_p[s][f] = p;
+        } else if (f >= 100 && f < 100 + PHOSIM_MAX_ZERNIKE) {
+            if (!(sc->surfaces[s].zern_rnorm > 0.0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+            for (int k = 0; k < G.n_zp[s]; ++k) if (G.zp_j[s][k] == f - 99) return PHOSIM_ERR_INVALID_ARGUMENT;
+            G.zp_j[s][G.n_zp[s]] = f - 99;
+            G.zp_p[s][G.n_zp[s]] = p;
+            ++G.n_zp[s];
+        } else {
+            return PHOSIM_ERR_INVALID_ARGUMENT;
+        }
+    }
+    int m = -1;
+    for (int s = 0; s < B.n_surf; ++s) {
+        G.mat_before[s] = m;
+        if (sc->surfaces[s].kind == PHOSIM_REFRACT) m = sc->surfaces[s].material;
+        rotation_derivatives(sc->surfaces[s].pert, G.dM[s]);
+    }
+    G.zmono = sc->d_zmono;
+    cudaStream_t st = (cudaStream_t)stream;
+    // forward pass in FP64: moment sums about each source's chief ray
+    const size_t mom_bytes = (size_t)n_src * PHOSIM_MOMENT_WORDS * sizeof(double);
+    if (sc->cap_mom < mom_bytes) {
+        cudaFree(sc->d_mom_scratch);
+        sc->d_mom_scratch = nullptr; sc->cap_mom = 0;
+        CU(cudaMalloc(&sc->d_mom_scratch, mom_bytes));
+        sc->cap_mom = mom_bytes;
+    }
+    const size_t img_bytes = (size_t)B.nx * B.ny * sizeof(uint32_t);
+    if (sc->cap_stage < img_bytes) {
+        cudaFree(sc->d_stage);
+        sc->d_stage = nullptr; sc->cap_stage = 0;
+        CU(cudaMalloc(&sc->d_stage, img_bytes));
+        sc->cap_stage = img_bytes;
+    }
+    CU(cudaMemsetAsync(sc->d_mom_scratch, 0, mom_bytes, st));
+    const int saved_precision = sc->precision;
+    sc->precision = PHOSIM_PLAIN_FP64;
+    phosim_status rs = phosim_trace(sc, src, n_src, n_photons, nullptr, sc->d_stage, nullptr, sc->d_mom_scratch, stream);
+    sc->precision = saved_precision;
+    if (rs != PHOSIM_OK) return rs;
+    std::vector<double> mom((size_t)n_src * PHOSIM_MOMENT_WORDS);
+    CU(cudaMemcpyAsync(mom.data(), sc->d_mom_scratch, mom_bytes, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    // cotangent seeds of the final positions: dL/dx_i = Ax + Bxx (x_i - mean x) + Bxy (y_i - mean y), ...
+    std::vector<double> seeds((size_t)n_src * 8, 0.0);
+    for (int s = 0; s < n_src; ++s) {
+        const double* M = &mom[(size_t)s * PHOSIM_MOMENT_WORDS];
+        const double n = M[0];
+        double mx = 0, my = 0, ixx = 0, ixy = 0, iyy = 0;
+        if (n > 0) {
+            const double ux = M[1] / n, uy = M[2] / n;
+            ixx = M[3] / n - ux * ux; ixy = M[4] / n - ux * uy; iyy = M[5] / n - uy * uy;
+            mx = M[6] + ux; my = M[7] + uy;
+            const double* g = dL + (size_t)s * 5;
+            double* q = &seeds[(size_t)s * 8];
+            q[0] = g[0] / n; q[1] = g[1] / n; q[2] = 2.0 * g[2] / n; q[3] = g[3] / n; q[4] = 2.0 * g[4] / n;
+            q[5] = mx; q[6] = my;
+        }
+        if (moments_out) {
+            double* o = moments_out + (size_t)s * 6;
+            o[0] = n; o[1] = mx; o[2] = my; o[3] = ixx; o[4] = ixy; o[5] = iyy;
+        }
+    }
+    const size_t gbytes = ((size_t)n_src * 8 + (size_t)n_src * n_params) * sizeof(double);
+    if (sc->cap_grad < gbytes) {
+        cudaFree(sc->d_grad_scratch);
+        sc->d_grad_scratch = nullptr; sc->cap_grad = 0;
+        CU(cudaMalloc(&sc->d_grad_scratch, gbytes));
+        sc->cap_grad = gbytes;
+    }
+    double* d_seeds = sc->d_grad_scratch;
+    double* d_grad = d_seeds + (size_t)n_src * 8;
+    CU(cudaMemcpyAsync(d_seeds, seeds.data(), seeds.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(d_grad, 0, (size_t)n_src * n_params * sizeof(double), st));
+    CU(cudaMemsetAsync(sc->d_counters, 0, sizeof(unsigned long long), st));
+    G.seeds = d_seeds;
+    G.grad = d_grad;
+    // the trace left its source list (with chief-ray references) and tile prefix in the scene's scratch
+    TraceParams P = sc->base;
+    P.sources = sc->d_src;
+    P.tile_prefix = sc->d_prefix;
+    P.n_src = n_src;
+    uint64_t total = 0;
+    for (int s = 0; s < n_src; ++s) total += n_photons[s];
+    int per_sm = 0;
+    CU(grad_occupancy(&per_sm));
+    per_sm = std::max(per_sm, 1);
+    const int blocks = sc->sm_count * per_sm;
+    uint64_t T = total / ((uint64_t)blocks * 4 * 8);
+    T = std::min<uint64_t>(1024, std::max<uint64_t>(32, (T + 31) / 32 * 32));
+    std::vector<unsigned long long> prefix((size_t)n_src + 1, 0);
+    for (int s = 0; s < n_src; ++s) prefix[s + 1] = prefix[s] + (n_photons[s] + T - 1) / T;
+    CU(cudaMemcpyAsync(sc->d_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    P.tile_photons = (uint32_t)T;
+    P.n_tiles = prefix[n_src];
+    P.tile_counter = sc->d_counters;
+    P.counters = sc->d_counters + 1;
+    P.image = nullptr;
+    P.moments = nullptr;
+    P.records = nullptr;
+    CU(launch_grad(P, G, blocks, st));
+    CU(cudaMemcpyAsync(grad, d_grad, (size_t)n_src * n_params * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return PHOSIM_OK;
 }
 
 }  // extern "C"

@@ -17,12 +17,12 @@ constexpr int kMaxMaterials = 8;
 constexpr int kMaxCoatings = 8;
 constexpr int kZPoly = 28;                 // monomials x^a y^b, a + b <= 6
 
-enum SurfFlags : int { SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FLAT_ONLY = 16 };
+enum SurfFlags : int { SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FLAT_ONLY = 16, SF_ROTATED = 32 };
 
 struct DSurface {
     int kind, material, coating, coat_slot;   // coat_slot: index of this surface's accept draw, -1 none
     int flags, pad0, pad1, pad2;
-    double c, k1c2;                           // 1/R, (1 + kappa) / R^2
+    double c, k1c2, kc;                       // 1/R, (1 + kappa) / R^2, (1 + kappa) / R
     double ae[4];                             // alpha_4, alpha_6, alpha_8, alpha_10
     double ao[4];                             // alpha_3, alpha_5, alpha_7, alpha_9
     double M[9];                              // telescope -> surface frame rotation (row-major)
@@ -41,6 +41,7 @@ struct DCoating {
     double lam0, inv_dlam, th0, inv_dth;
     int nl, nt, pad0, pad1;
     const double* T;                          // nl x nt
+    const double* Tmax;                       // nl: the largest transmission over angles at each wavelength
 };
 
 struct DScale {
@@ -71,6 +72,7 @@ struct TraceParams {
     uint32_t k0, k1;                          // Philox key
     uint32_t flags;
     int n_surf, n_layers, n_coated, n_mat, n_coat;
+    int coated_surface[PHOSIM_MAX_COATED];    // surface index of coated-surface draw k
     double pr_in2, pr_dr2;                    // pupil annulus
     double h_top, z_ent;
     double lam_ref, kick0;                    // kick0 = lambda_ref [mm] / 2 pi
@@ -199,8 +201,11 @@ __device__ __forceinline__ bool sag(const DSurface& S, double x, double y, doubl
     return true;
 }
 
-// Intersection (Sec. 2.4.2): exact root of the paraboloid with the vertex curvature as first guess, then
-// Newton's method on F(l) = p_z + l d_z - S(p_x + l d_x, p_y + l d_y) until the step is below 1e-8 mm.
+// Intersection (Sec. 2.4.2).  The paper's first guess is the root of a quadric approximating the surface;
+// here the quadric is the conic itself, c (x^2 + y^2) + (1 + kappa) c z^2 - 2 z = 0, solved exactly on the
+// vertex branch (1 - (1 + kappa) c z >= 0).  A pure conic needs nothing more: its slopes follow from the
+// same quadric, z_x = c x / (1 - (1 + kappa) c z).  Aspheric and Zernike terms are then added by Newton's
+// method on F(l) = p_z + l d_z - S(p_x + l d_x, p_y + l d_y) until the step is below 1e-8 mm.
 // On success l is the distance and (zx, zy) the slopes at the root (within 1e-8 mm of it).
 __device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[3], const double d[3], double& l,
                                               double& zx, double& zy) {
@@ -210,17 +215,21 @@ __device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[
         zx = 0.0; zy = 0.0;
         return 0;
     }
-    const double qa = 0.5 * S.c * (d[0] * d[0] + d[1] * d[1]);
-    const double qb = S.c * (p[0] * d[0] + p[1] * d[1]) - d[2];
-    const double qc = 0.5 * S.c * (p[0] * p[0] + p[1] * p[1]) - p[2];
-    const double disc = qb * qb - 4.0 * qa * qc;
-    if (qa == 0.0 || disc < 0.0) {
-        if (qb == 0.0) return PHOSIM_LOST_MISSED;
-        l = -qc / qb;
-    } else {
-        const double q = -0.5 * (qb + copysign(sqrt(disc), qb));
-        if (q == 0.0) return PHOSIM_LOST_MISSED;
-        l = qc / q;
+    const double A = S.c * fma(d[0], d[0], d[1] * d[1]) + S.kc * d[2] * d[2];
+    const double b = S.c * fma(p[0], d[0], p[1] * d[1]) + fma(S.kc * p[2], d[2], -d[2]);
+    const double C = S.c * fma(p[0], p[0], p[1] * p[1]) + fma(S.kc * p[2], p[2], -2.0 * p[2]);
+    const double disc = fma(b, b, -A * C);
+    if (disc < 0.0) return PHOSIM_LOST_MISSED;
+    const double q = -(b + copysign(sqrt(disc), b));
+    if (q == 0.0) return PHOSIM_LOST_MISSED;
+    l = C / q;
+    if (A != 0.0 && fma(-S.kc, fma(l, d[2], p[2]), 1.0) < 0.0) l = q / A;   // the other root is the vertex branch
+    if (!(S.flags & (SF_EVEN | SF_ODD | SF_ZERN))) {
+        const double x = fma(l, d[0], p[0]), y = fma(l, d[1], p[1]), z = fma(l, d[2], p[2]);
+        const double inv_s = 1.0 / fma(-S.kc, z, 1.0);
+        zx = S.c * x * inv_s;
+        zy = S.c * y * inv_s;
+        return 0;
     }
 #pragma unroll 1
     for (int it = 0; it < 20; ++it) {
@@ -272,6 +281,11 @@ __device__ __forceinline__ bool refract(double d[3], double Nx, double Ny, doubl
 __device__ __forceinline__ void to_surface(const DSurface& S, const double x[3], const double d[3], double p[3],
                                            double dl[3]) {
     const double rx = x[0] - S.o[0], ry = x[1] - S.o[1], rz = x[2] - S.o[2];
+    if (!(S.flags & SF_ROTATED)) {        // the identity rotation: the products below would be exact copies
+        p[0] = rx; p[1] = ry; p[2] = rz;
+        dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         p[i] = fma(S.M[3 * i], rx, fma(S.M[3 * i + 1], ry, S.M[3 * i + 2] * rz));
@@ -281,6 +295,11 @@ __device__ __forceinline__ void to_surface(const DSurface& S, const double x[3],
 
 __device__ __forceinline__ void from_surface(const DSurface& S, const double p[3], const double dl[3], double x[3],
                                              double d[3]) {
+    if (!(S.flags & SF_ROTATED)) {
+        x[0] = p[0] + S.o[0]; x[1] = p[1] + S.o[1]; x[2] = p[2] + S.o[2];
+        d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         x[i] = fma(S.M[i], p[0], fma(S.M[3 + i], p[1], fma(S.M[6 + i], p[2], S.o[i])));

@@ -31,6 +31,12 @@ struct phosim_scene {
     uint32_t* d_stage = nullptr;                // staging image for host image pointers
     size_t cap_stage = 0;
     cudaStream_t last_stream = nullptr;
+    // adjoint: Zernike monomial table (owned with the optics) and per-call scratch
+    double* d_zmono = nullptr;
+    double* d_grad_scratch = nullptr;           // seeds + gradient accumulators
+    size_t cap_grad = 0;
+    double* d_mom_scratch = nullptr;
+    size_t cap_mom = 0;
 };
 
 namespace phosim {

@@ -216,6 +216,47 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
     R.flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
 }
 
+// Wavelength (Sec. 2.2): cumulative photon-number table, blur within the bin, redshift.
+template <bool MIXED>
+__device__ __forceinline__ double sample_wavelength(const TraceParams& P, const DSource& s, const uint4& w0) {
+    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.n_bins - 1, w0.z);
+    if constexpr (MIXED) {
+        const float lo = (float)(P.sed_lam0 + bin * P.sed_dlam);
+        return (double)(fmaf(u32of(w0.w), (float)P.sed_dlam, lo) * (float)s.zfac);
+    } else {
+        return fma(u64of(w0.w), P.sed_dlam, P.sed_lam0 + bin * P.sed_dlam) * s.zfac;
+    }
+}
+
+// Dynamic transmission (Sec. 3.2): the index of the first coated surface whose accept draw is not below the
+// largest transmission any incidence angle allows at this wavelength (the photon is certainly rejected
+// there), or -1.
+__device__ __forceinline__ int early_coating_reject(const TraceParams& P, double lam, const uint4& w2, const uint4& w3) {
+#pragma unroll 1
+    for (int k = 0; k < P.n_coated; ++k) {
+        const int si = P.coated_surface[k];
+        const DCoating& C = P.coat[P.surf[si].coating];
+        int il = (int)floor((lam - C.lam0) * C.inv_dlam);
+        il = il < 0 ? 0 : (il > C.nl - 1 ? C.nl - 1 : il);
+        const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
+        if (!(u64of(w) < __ldg(C.Tmax + il))) return si;
+    }
+    return -1;
+}
+
+// The early-rejection decision of photon i alone (no propagation): -1 if it goes on, else the surface.
+template <bool MIXED>
+__device__ __forceinline__ int early_reject_surface(const TraceParams& P, const DSource& s, int src, uint64_t i,
+                                                    double& lam) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+    lam = sample_wavelength<MIXED>(P, s, w0);
+    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    return early_coating_reject(P, lam, w2, w3);
+}
+
 template <bool MIXED, bool RECORD = false>
 __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource& s, int src, uint64_t i, PhotonOut& R,
                                              ForwardRecord* fr = nullptr) {
@@ -225,15 +266,7 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
     R.flags = 0; R.pix = -1; R.x = R.y = R.xc = R.yc = 0.0;
     // time stamp (Sec. 2.2)
     const double t = fma(s.t_exp, u64of(w1.x), s.t0);
-    // wavelength: cumulative photon-number table, blur within the bin, redshift (Sec. 2.2)
-    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.n_bins - 1, w0.z);
-    double lam;
-    if constexpr (MIXED) {
-        const float lo = (float)(P.sed_lam0 + bin * P.sed_dlam);
-        lam = (double)(fmaf(u32of(w0.w), (float)P.sed_dlam, lo) * (float)s.zfac);
-    } else {
-        lam = fma(u64of(w0.w), P.sed_dlam, P.sed_lam0 + bin * P.sed_dlam) * s.zfac;
-    }
+    const double lam = sample_wavelength<MIXED>(P, s, w0);
     R.lam = lam;
     // direction: tangent-plane components, paraxial shape offset, renormalised (Sec. 2.2, 2.2.1)
     double nx = s.xi, ny = s.eta;
@@ -271,6 +304,13 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         }
     }
     double nz = -sqrt(1.0 - nx * nx - ny * ny);
+    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    if (P.flags & PHOSIM_EARLY_REJECT) {
+        const int si = early_coating_reject(P, lam, w2, w3);
+        if (si >= 0) { R.flags = lost(PHOSIM_LOST_COATING, si); return; }
+    }
     // pupil point on the annulus, on the nominal first surface, moved back to the top of the atmosphere
     const double r = sqrt(fma(u64of(w0.x), P.pr_dr2, P.pr_in2));
     double sp, cp;
@@ -315,9 +355,6 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         y = fma(ny, l, y);
         z = P.z_ent;
     }
-    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
-    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
     double X[3] = {x, y, z}, D[3] = {nx, ny, nz};
     optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, R, fr);
 }

@@ -26,9 +26,63 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Per-warp accumulation state of one tile: moment partials (FP64 in the plain path; FP32 with Kahan
+// compensation in the mixed path) and, in lane 0, the launch counters.
+struct TileAcc {
+    double m0, m1, m2, m3, m4, m5;
+    float f1, f2, f3, f4, f5, c1, c2, c3, c4, c5;
+};
+
+// Account for one batch of up to 32 photons that went through trace_photon: record, image, moments and
+// the detected / dropped counters.  Every lane of the warp calls it.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceParams P) {
+__device__ __forceinline__ void consume(const TraceParams& P, const PhotonOut& R, bool valid, uint64_t rec_index,
+                                        double rx, double ry, int lane, TileAcc& A, unsigned long long* cnt) {
+    if (valid && P.records) {
+        phosim_photon_record rec;
+        rec.x = R.x; rec.y = R.y; rec.xc = R.xc; rec.yc = R.yc; rec.lambda = R.lam;
+        rec.flags = R.flags; rec.pix = R.pix;
+        P.records[rec_index] = rec;
+    }
+    const bool det = valid && (R.flags & PHOSIM_F_DETECTED);
+    const unsigned dmask = __ballot_sync(0xffffffffu, det);
+    if (det) {
+        const unsigned same = __match_any_sync(dmask, R.pix);
+        if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
+        const double dx = R.x - rx, dy = R.y - ry;
+        if constexpr (MIXED) {
+            const float fx = (float)dx, fy = (float)dy;
+            kahan_add(A.f1, A.c1, fx);
+            kahan_add(A.f2, A.c2, fy);
+            kahan_add(A.f3, A.c3, fx * fx);
+            kahan_add(A.f4, A.c4, fx * fy);
+            kahan_add(A.f5, A.c5, fy * fy);
+            A.m0 += 1.0;
+        } else {
+            A.m0 += 1.0; A.m1 += dx; A.m2 += dy; A.m3 += dx * dx; A.m4 += dx * dy; A.m5 += dy * dy;
+        }
+    }
+    if (lane == 0) cnt[1] += __popc(dmask);
+    const uint32_t reason = valid ? ((R.flags >> 8) & 0xffu) : 0u;
+#pragma unroll
+    for (int q = 1; q <= 7; ++q) {
+        const unsigned b = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
+        if (lane == 0) cnt[1 + q] += __popc(b);
+    }
+}
+
+constexpr int kWarpsPerBlock = 8;
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ TraceParams P) {
+    // With early rejection most photons stop after their wavelength is drawn.  Survivors are queued per
+    // warp (photon offsets within the tile, in shared memory) and propagated 32 at a time, so the expensive
+    // part runs with full warps instead of the few lanes that survived in each batch.
+    __shared__ uint32_t queue_mem[kWarpsPerBlock][64];
     const int lane = threadIdx.x & 31;
+    uint32_t* queue = queue_mem[threadIdx.x >> 5];
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const bool early = (P.flags & PHOSIM_EARLY_REJECT) != 0;
     unsigned long long cnt[kNumCounters];
 #pragma unroll
     for (int k = 0; k < kNumCounters; ++k) cnt[k] = 0;
@@ -44,60 +98,55 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
         const uint32_t count = (uint32_t)min((uint64_t)P.tile_photons, s.count - off);
         const uint64_t first = s.first + off, rec_base = s.rec_off + off;
         const double rx = s.ref_x, ry = s.ref_y;
-        // moment partials: FP64 in the plain path; FP32 with Kahan compensation in the mixed path
-        double m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0, m5 = 0;
-        float f1 = 0, f2 = 0, f3 = 0, f4 = 0, f5 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
-        for (uint32_t base = 0; base < count; base += 32) {
-            const uint32_t k = base + lane;
-            const bool valid = k < count;
-            PhotonOut R;
-            R.flags = 0; R.pix = -1;
-            if (valid) {
-                trace_photon<MIXED>(P, s, src, first + k, R);
-                if (P.records) {
-                    phosim_photon_record rec;
-                    rec.x = R.x; rec.y = R.y; rec.xc = R.xc; rec.yc = R.yc; rec.lambda = R.lam;
-                    rec.flags = R.flags; rec.pix = R.pix;
-                    P.records[rec_base + k] = rec;
+        TileAcc A = {};
+        int queued = 0;
+        uint32_t base = 0;
+        for (;;) {
+            if (base < count) {
+                const uint32_t k = base + lane;
+                const bool valid = k < count;
+                const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                if (lane == 0) cnt[0] += __popc(vmask);
+                bool go_on = valid;
+                if (early) {
+                    // stage 1: the early coating decision alone
+                    double lam = 0.0;
+                    const int rej = valid ? early_reject_surface<MIXED>(P, s, src, first + k, lam) : -1;
+                    go_on = valid && rej < 0;
+                    PhotonOut R;
+                    R.flags = valid ? lost(PHOSIM_LOST_COATING, rej) : 0u;
+                    R.pix = -1; R.x = R.y = R.xc = R.yc = 0.0; R.lam = lam;
+                    consume<MIXED>(P, R, valid && !go_on, rec_base + k, rx, ry, lane, A, cnt);
                 }
+                // queue the photons that go on
+                const unsigned gmask = __ballot_sync(0xffffffffu, go_on);
+                if (go_on) queue[queued + __popc(gmask & lanes_below)] = k;
+                queued += __popc(gmask);
+                base += 32;
+                __syncwarp();
             }
-            const bool det = valid && (R.flags & PHOSIM_F_DETECTED);
-            const unsigned dmask = __ballot_sync(0xffffffffu, det);
-            if (det) {
-                const unsigned same = __match_any_sync(dmask, R.pix);
-                if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
-                const double dx = R.x - rx, dy = R.y - ry;
-                if constexpr (MIXED) {
-                    const float fx = (float)dx, fy = (float)dy;
-                    kahan_add(f1, c1, fx);
-                    kahan_add(f2, c2, fy);
-                    kahan_add(f3, c3, fx * fx);
-                    kahan_add(f4, c4, fx * fy);
-                    kahan_add(f5, c5, fy * fy);
-                    m0 += 1.0;
-                } else {
-                    m0 += 1.0; m1 += dx; m2 += dy; m3 += dx * dx; m4 += dx * dy; m5 += dy * dy;
-                }
+            const bool drained = base >= count;
+            if (queued >= 32 || (drained && queued > 0)) {
+                // stage 2: propagate a warp's worth of queued photons
+                const int take = queued < 32 ? queued : 32;
+                queued -= take;
+                const bool v = lane < take;
+                const uint32_t kk = v ? queue[queued + lane] : 0u;
+                __syncwarp();
+                PhotonOut Q;
+                Q.flags = 0; Q.pix = -1;
+                if (v) trace_photon<MIXED>(P, s, src, first + kk, Q);
+                consume<MIXED>(P, Q, v, rec_base + kk, rx, ry, lane, A, cnt);
             }
-            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-            if (lane == 0) {
-                cnt[0] += __popc(vmask);
-                cnt[1] += __popc(dmask);
-            }
-            const uint32_t reason = valid ? ((R.flags >> 8) & 0xffu) : 0u;
-#pragma unroll
-            for (int q = 1; q <= 7; ++q) {
-                const unsigned b = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
-                if (lane == 0) cnt[1 + q] += __popc(b);
-            }
+            if (drained && queued == 0) break;
         }
         if constexpr (MIXED) {
-            m1 = (double)f1 - (double)c1; m2 = (double)f2 - (double)c2; m3 = (double)f3 - (double)c3;
-            m4 = (double)f4 - (double)c4; m5 = (double)f5 - (double)c5;
+            A.m1 = (double)A.f1 - (double)A.c1; A.m2 = (double)A.f2 - (double)A.c2; A.m3 = (double)A.f3 - (double)A.c3;
+            A.m4 = (double)A.f4 - (double)A.c4; A.m5 = (double)A.f5 - (double)A.c5;
         }
         if (P.moments) {
-            m0 = warp_sum(m0); m1 = warp_sum(m1); m2 = warp_sum(m2);
-            m3 = warp_sum(m3); m4 = warp_sum(m4); m5 = warp_sum(m5);
+            const double m0 = warp_sum(A.m0), m1 = warp_sum(A.m1), m2 = warp_sum(A.m2);
+            const double m3 = warp_sum(A.m3), m4 = warp_sum(A.m4), m5 = warp_sum(A.m5);
             if (lane == 0 && m0 > 0.0) {
                 double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
                 atomicAdd(M + 0, m0); atomicAdd(M + 1, m1); atomicAdd(M + 2, m2);

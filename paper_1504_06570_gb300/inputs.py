@@ -435,3 +435,100 @@ def three_mirror_scene(n_stars=1000, n_total=100_000_000, seed=2, atmosphere=Tru
                  materials=materials, coatings=[filter_coating(550.0, 700.0, 0.95, lam0=300.0, nlam=900)],
                  detector=det, layers=layers, sed_lam0=300.0, sed_dlam=1.0, sed_flux=sed_tables(temps, 300.0, 1.0, 900),
                  sersic=np.ones((1, 4)), sources=sources, atmosphere=atmosphere, sensor=sensor, z_entrance=ATM_Z0_MM - 1000.0)
+
+
+def galaxy_and_star_catalog(n_sources, rng, half_field_deg=0.1, star_frac=0.7, lo=1e2, hi=1e7, n_index_levels=64,
+                            t_exp=15.0):
+    """Stars (70 %) and Sersic galaxies (30 %): index n uniform on [0.5, 4] (snapped to 64 levels so the
+    radial tables are shared), half-light radius log-uniform 0.2-3 arcsec, ellipticity |e| < 0.6 uniform in
+    the disk, photon counts log-uniform on [lo, hi].  Returns (sources, SED temperatures, Sersic tables)."""
+    h = math.radians(half_field_deg)
+    n_star = int(round(star_frac * n_sources))
+    kind = np.r_[np.full(n_star, POINT), np.full(n_sources - n_star, SERSIC)].astype(np.int32)
+    rng.shuffle(kind)
+    xi, eta = rng.uniform(-h, h, n_sources), rng.uniform(-h, h, n_sources)
+    counts = np.exp(rng.uniform(math.log(lo), math.log(hi), n_sources)).astype(np.uint64)
+    levels = 0.5 + np.arange(n_index_levels) * (3.5 / (n_index_levels - 1))
+    n_idx = rng.uniform(0.5, 4.0, n_sources)
+    table = np.clip(np.rint((n_idx - 0.5) / (3.5 / (n_index_levels - 1))), 0, n_index_levels - 1).astype(np.int32)
+    re = np.exp(rng.uniform(math.log(0.2), math.log(3.0), n_sources)) * ARCSEC
+    er, ephi = 0.6 * np.sqrt(rng.random(n_sources)), rng.uniform(0, math.pi, n_sources)
+    q = (1 - er) / (1 + er)
+    a, b = re / np.sqrt(q), re * np.sqrt(q)
+    a = np.where(kind == SERSIC, a, 0.0)
+    b = np.where(kind == SERSIC, b, 0.0)
+    temps = rng.uniform(3000.0, 10000.0, n_sources)
+    src = Sources(kind=kind, sed=np.arange(n_sources, dtype=np.int32), xi=xi, eta=eta, redshift=np.zeros(n_sources),
+                  t0=np.zeros(n_sources), t_exp=np.full(n_sources, t_exp), a=a, b=b, pa=ephi,
+                  table=np.where(kind == SERSIC, table, 0).astype(np.int32), n_photons=counts)
+    tables = np.stack([sersic_radius_table(n, 1024) for n in levels])
+    return src, temps, tables
+
+
+def background_nodes(n_photons, chip_half_mm, plate_arcsec_per_mm, sed_index, spacing_arcsec=15.0, t_exp=15.0):
+    """Diffuse sky as Gaussian sources (sigma = spacing) on a square grid every 15 arcsec covering the chip
+    plus one spacing of margin (Sec. 2.2.2); the photons are split equally."""
+    half = chip_half_mm * plate_arcsec_per_mm + spacing_arcsec
+    k = int(math.ceil(half / spacing_arcsec))
+    g = np.arange(-k, k + 1) * spacing_arcsec * ARCSEC
+    X, Y = np.meshgrid(g, g)
+    n = X.size
+    per = np.full(n, n_photons // n, np.uint64)
+    per[: int(n_photons - per.sum())] += np.uint64(1)
+    return Sources(kind=np.full(n, GAUSS, np.int32), sed=np.full(n, sed_index, np.int32), xi=X.ravel(), eta=Y.ravel(),
+                   redshift=np.zeros(n), t0=np.zeros(n), t_exp=np.full(n, t_exp), a=np.full(n, spacing_arcsec * ARCSEC),
+                   b=np.zeros(n), pa=np.zeros(n), table=np.zeros(n, np.int32), n_photons=per)
+
+
+def batched_scene(n_sources=10_000, background_photons=1_000_000_000, seed=4, fine_n=4096, coarse_n=1024,
+                  photon_scale=1.0):
+    """The batched workload: 10^4 stars and galaxies (counts log-uniform 1e2-1e7, ~5e9 photons) plus 1e9
+    sky-background photons on 15 arcsec nodes, through the three-mirror optics and seven-layer atmosphere.
+    photon_scale multiplies every count (sub-sampled runs)."""
+    d, surfaces, materials = three_mirror_optics()
+    rng = np.random.default_rng(seed)
+    src, temps, tables = galaxy_and_star_catalog(n_sources, rng)
+    sky = background_nodes(int(background_photons), 0.5 * 4096 * 0.01, d["plate_scale_arcsec_per_mm"], n_sources)
+    sources = concat_sources([src, sky])
+    if photon_scale != 1.0:
+        sources.n_photons = np.maximum(1, np.rint(sources.n_photons * photon_scale)).astype(np.uint64)
+    temps = np.r_[temps, 5800.0]
+    layers = von_karman_layers(fine_n=fine_n, coarse_n=coarse_n,
+                               coarse_pix_mm=640.0 * 1024 / coarse_n * (fine_n / 4096))
+    det = Detector(nx=4096, ny=4096, pixel=0.01, t_si=0.1, ell_lam0=300.0, ell_dlam=1.0,
+                   ell=absorption_length_table(300.0, 1.0, 901), sigma=np.array([0.003, 0.003]))
+    return Scene(seed=seed, pupil_r_in=d["pupil_r_in"], pupil_r_out=d["pupil_r_out"], surfaces=surfaces,
+                 materials=materials, coatings=[filter_coating(550.0, 700.0, 0.95, lam0=300.0, nlam=900)],
+                 detector=det, layers=layers, sed_lam0=300.0, sed_dlam=1.0, sed_flux=sed_tables(temps, 300.0, 1.0, 900),
+                 sersic=tables, sources=sources, atmosphere=True, sensor=True, z_entrance=ATM_Z0_MM - 1000.0)
+
+
+def grad_grid_scene(n_side=8, photons=1_000_000, seed=5, zernike_nm_max=50.0):
+    """The differentiation workload: 64 stars on an 8 x 8 grid over the 0.2 degree field, 1e6 photons each,
+    atmosphere off; M1/M2/M3 carry Zernike Z4-Z22 figure errors drawn at 0-50 nm rms.  Returns (scene,
+    params) with params = M2 and camera (lenses, filter, detector) dx, dy, tx, ty and Z4-Z22 of the three
+    mirrors, as (surface, field) pairs; camera parameters apply to each of its surfaces."""
+    d, surfaces, materials = three_mirror_optics()
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) - (n_side - 1) / 2) / (n_side - 1) * math.radians(0.2)
+    X, Y = np.meshgrid(g, g)
+    n = X.size
+    temps = rng.uniform(3000.0, 10000.0, n)
+    src = point_sources(X.ravel(), Y.ravel(), np.full(n, photons, np.uint64), sed=np.arange(n))
+    for m in range(3):
+        s = surfaces[m]
+        rms = rng.uniform(0.0, zernike_nm_max) * 1e-6
+        c = rng.normal(size=19)
+        c = c / np.sqrt(np.sum(c * c)) * rms
+        s.zern = tuple([0.0, 0.0, 0.0] + list(c))
+        s.zern_rnorm = s.r_out
+    det = Detector(nx=4096, ny=4096, pixel=0.01, t_si=0.1, ell_lam0=300.0, ell_dlam=1.0,
+                   ell=absorption_length_table(300.0, 1.0, 901), sigma=np.array([0.003, 0.003]))
+    sc = Scene(seed=seed, pupil_r_in=d["pupil_r_in"], pupil_r_out=d["pupil_r_out"], surfaces=surfaces,
+               materials=materials, coatings=[filter_coating(550.0, 700.0, 0.95, lam0=300.0, nlam=900)],
+               detector=det, layers=[], sed_lam0=300.0, sed_dlam=1.0, sed_flux=sed_tables(temps, 300.0, 1.0, 900),
+               sersic=np.ones((1, 4)), sources=src, atmosphere=False, sensor=True, z_entrance=ATM_Z0_MM - 1000.0)
+    camera = list(range(3, len(surfaces)))
+    params = [(1, f) for f in (0, 1, 3, 4)] + [(c, f) for c in camera for f in (0, 1, 3, 4)]
+    params += [(m, 100 + j) for m in range(3) for j in range(3, 22)]
+    return sc, params, camera

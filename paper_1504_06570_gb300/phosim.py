@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libphosim.so")
 
 MAX_SURFACES, MAX_LAYERS, MAX_SCALES, MAX_ZERNIKE = 16, 8, 2, 28
 PLAIN_FP64, MIXED = 0, 1
-ATMOSPHERE, SENSOR = 1, 2
+ATMOSPHERE, SENSOR, EARLY_REJECT = 1, 2, 4
 MOMENT_WORDS = 8
 F_DETECTED = 1
 
@@ -153,7 +153,7 @@ def surface_struct(s: I.Surface) -> Surface:
 class Scene:
     """A scene loaded into the CUDA library (device copies owned by the library)."""
 
-    def __init__(self, scene: I.Scene, precision=PLAIN_FP64):
+    def __init__(self, scene: I.Scene, precision=PLAIN_FP64, early_reject=False):
         L = lib()
         self.L = L
         self.scene = scene
@@ -162,7 +162,8 @@ class Scene:
         self._ell = np.ascontiguousarray(d.ell, np.float64)
         self._sig = np.ascontiguousarray(d.sigma, np.float64)
         desc = SceneDesc(seed=scene.seed, precision=precision,
-                         flags=(ATMOSPHERE if scene.atmosphere else 0) | (SENSOR if scene.sensor else 0),
+                         flags=(ATMOSPHERE if scene.atmosphere else 0) | (SENSOR if scene.sensor else 0)
+                         | (EARLY_REJECT if early_reject else 0),
                          pupil_r_in=scene.pupil_r_in, pupil_r_out=scene.pupil_r_out, h_top=scene.h_top,
                          z_entrance=scene.z_entrance, lambda_ref=scene.lambda_ref, nx=d.nx, ny=d.ny, pixel=d.pixel,
                          x0=d.x0, y0=d.y0, t_si=d.t_si, ell_lam0=d.ell_lam0, ell_dlam=d.ell_dlam,
@@ -236,6 +237,56 @@ class Scene:
             C.c_void_p(image.data_ptr()), None if records is None else C.c_void_p(records.data_ptr()),
             None if moments is None else C.c_void_p(moments.data_ptr()), C.c_void_p(stream) if stream else None))
 
+    def grad(self, dL_dmoments, params, n_photons=None, stream=None):
+        """phosim_grad: per-source gradients of sum_k dL[s, k] M_s[k], M = (mean x, mean y, Ixx, Ixy, Iyy),
+        with respect to params = [(surface, field)] (field 0..5 = dx, dy, dz, tx, ty, tz; 100 + j = Zernike
+        coefficient j + 1).  Returns (grad (n_src, n_params), moments (n_src, 6))."""
+        import torch
+        n = len(self.sources)
+        cnt = self.n_photons if n_photons is None else np.ascontiguousarray(n_photons, np.uint64)
+        dL = np.ascontiguousarray(dL_dmoments, np.float64).reshape(n, 5)
+        ps = np.ascontiguousarray([int(p[0]) for p in params], np.int32)
+        pf = np.ascontiguousarray([int(p[1]) for p in params], np.int32)
+        g = np.zeros((n, len(params)))
+        m = np.zeros((n, 6))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        i32p = C.POINTER(C.c_int32)
+        _check("phosim_grad", self.L.phosim_grad(self.h, self.src, n, cnt.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                                 _dptr(dL), ps.ctypes.data_as(i32p), pf.ctypes.data_as(i32p),
+                                                 len(params), g.ctypes.data_as(C.POINTER(C.c_double)),
+                                                 m.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(stream)))
+        return g, m
+
+    def set_parameters(self, params, values):
+        """Write surface misalignments / Zernike coefficients (same (surface, field) convention) into the
+        scene's optics and reload them."""
+        for (si, f), v in zip(params, np.asarray(values, np.float64)):
+            s = self.scene.surfaces[si]
+            if f < 6:
+                pert = list(s.pert) + [0.0] * (6 - len(s.pert))
+                pert[f] = float(v)
+                s.pert = tuple(pert)
+            else:
+                j = f - 100
+                z = list(s.zern) + [0.0] * max(0, j + 1 - len(s.zern))
+                z[j] = float(v)
+                s.zern = tuple(z)
+        self.load_optics(self.scene.surfaces, self.scene.materials, self.scene.coatings)
+
+    def autotune(self, sample_photons=5_000_000, n_photons=None, stream=None):
+        """phosim_autotune on this scene's sources; returns (threads per block, photons per tile)."""
+        import torch
+        cnt = self.n_photons if n_photons is None else np.ascontiguousarray(n_photons, np.uint64)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        t, k = C.c_int(), C.c_int()
+        _check("phosim_autotune", self.L.phosim_autotune(self.h, self.src, len(self.sources),
+                                                         cnt.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                                         C.c_uint64(int(sample_photons)), C.c_void_p(stream),
+                                                         C.byref(t), C.byref(k)))
+        return t.value, k.value
+
     def counters(self):
         out = (C.c_uint64 * 9)()
         _check("phosim_get_counters", self.L.phosim_get_counters(self.h, out, 9))
@@ -267,3 +318,32 @@ def derived_moments(m):
         ixy = m[:, 4] / n - mx * my
         iyy = m[:, 5] / n - my * my
     return np.stack([n, mx + m[:, 6], my + m[:, 7], ixx, ixy, iyy], 1)
+
+
+def _autograd_function():
+    import torch
+
+    class PSFMoments(torch.autograd.Function):
+        """Per-source PSF moments (mean x, mean y, Ixx, Ixy, Iyy) as a differentiable function of surface
+        parameters; the backward pass is the adjoint raytrace (phosim_grad) with common random numbers and
+        the forward pass's accept decisions."""
+
+        @staticmethod
+        def forward(ctx, theta, scene, params):
+            scene.set_parameters(params, theta.detach().cpu().numpy())
+            n = len(scene.sources)
+            _, m = scene.grad(np.zeros((n, 5)), params)
+            ctx.scene, ctx.params = scene, params
+            return torch.as_tensor(m[:, 1:], dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            grad, _ = ctx.scene.grad(g.detach().cpu().numpy(), ctx.params)
+            return torch.as_tensor(grad.sum(0), dtype=g.dtype, device=g.device), None, None
+
+    return PSFMoments
+
+
+def psf_moments(theta, scene, params):
+    """Differentiable per-source PSF moments; see PSFMoments."""
+    return _autograd_function().apply(theta, scene, params)

@@ -10,9 +10,9 @@ MARGIN_NM = 1e-6
 
 
 def run_gpu(scene, precision=P.PLAIN_FP64, records=True, moments=True, schedule=None, n_photons=None, first=None,
-            host_image=False):
+            host_image=False, early_reject=False):
     import torch
-    s = P.Scene(scene, precision)
+    s = P.Scene(scene, precision, early_reject=early_reject)
     if schedule:
         s.set_schedule(*schedule)
     cnt = scene.sources.n_photons if n_photons is None else np.asarray(n_photons, np.uint64)

@@ -115,6 +115,27 @@ def test_sensor_off_and_atmosphere_off(oracle_mod):
     assert r["max_err_px"] < 1e-6
 
 
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED])
+def test_early_rejection_keeps_the_detected_photons(oracle_mod, precision):
+    """Dynamic transmission (Sec. 3.2): deciding the coating draws up front changes only the reported reason
+    of photons lost anyway; detected photons, image and moments are those of the full trace."""
+    counts = [5000, 700, 12000]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=5))
+    full = G.run_gpu(sc, precision)
+    early = G.run_gpu(sc, precision, early_reject=True)
+    det_f = (full["rec"]["flags"] & 1) == 1
+    det_e = (early["rec"]["flags"] & 1) == 1
+    assert np.array_equal(det_f, det_e)
+    assert np.array_equal(full["rec"][det_f], early["rec"][det_e])
+    assert np.array_equal(full["image"], early["image"])
+    np.testing.assert_allclose(early["moments"], full["moments"], rtol=1e-12, atol=1e-15)
+    moved = (~det_e) & (full["rec"]["flags"] != early["rec"]["flags"])
+    assert np.all(((early["rec"]["flags"][moved] >> 8) & 0xFF) == 5)
+    if precision == P.PLAIN_FP64:
+        ora = G.oracle_trace(oracle_mod, sc)
+        assert np.array_equal(det_e, (ora["flags"] & 1) == 1)
+
+
 def test_invalid_sources_are_rejected():
     sc = I.paraboloid_scene(n_photons=10)
     s = P.Scene(sc)
