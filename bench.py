@@ -296,7 +296,7 @@ def main():
     photons = int(counts.sum())
     # both precisions with the paper's dynamic transmission (early coating rejection), which leaves the
     # detected photons unchanged
-    mixed = P.Scene(sc, P.MIXED, early_reject=True)
+    mixed = P.Scene(sc, P.MIXED, early_reject=True, graph=True)
     plain = P.Scene(sc, P.PLAIN_FP64, early_reject=True)
     setup_s = time.perf_counter() - t_setup
     d = sc.detector

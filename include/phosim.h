@@ -58,6 +58,9 @@ enum {
 /* scene flags */
 #define PHOSIM_ATMOSPHERE 1u     /* apply the phase-screen layers */
 #define PHOSIM_SENSOR 2u         /* silicon conversion and diffusion; otherwise the detector-surface hit */
+#define PHOSIM_GRAPH 8u          /* launch the chief-ray and trace kernels of phosim_trace as one CUDA graph,
+                                    captured on the first call (per precision) and replayed with each call's
+                                    parameters */
 #define PHOSIM_EARLY_REJECT 4u   /* dynamic transmission (Sec. 3.2): decide each coating's accept draw against
                                     the largest transmission over incidence angles at the photon's wavelength
                                     before propagating it.  The detected photons, image and moments are
@@ -193,6 +196,13 @@ phosim_status phosim_load_seds(phosim_scene* scene, const double* flux, int n_se
 /* Load Sersic radial tables (Sec. 2.2.1): radius / half-light radius at u = (k + 1/2) / n_nodes,
    n_tables x n_nodes, host.  Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
 phosim_status phosim_load_sersic(phosim_scene* scene, const double* table, int n_tables, int n_nodes);
+
+/* Load the second, statistical atmospheric kick (Sec. 2.3.2): the kick angle's quantiles (rad, at
+   lambda_ref) at u = (k + 1/2) / n of the long-exposure PSF of the screens above kappa_crit (including the
+   unscattered part as zero angles), non-decreasing.  Each photon that crossed the layers then draws an
+   angle (linear interpolation, scaled by (lambda / lambda_ref)^(-1/5)) and a uniform direction.  n = 0
+   removes it.  Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_load_hf_kick(phosim_scene* scene, const double* quantiles, int n);
 
 /* Trace photons first[s] .. first[s] + n_photons[s] - 1 of every source s (first = NULL: from 0).
    sources, n_photons and first are host arrays.  Photon i of source s always draws the same random

@@ -92,6 +92,9 @@ class Oracle:
                           C.c_int(flux.shape[1]), _dp(flux))
         sr = _arr(scene.sersic, np.float64)
         L.oracle_set_sersic(self.h, C.c_int(sr.shape[0]), C.c_int(sr.shape[1]), _dp(sr))
+        if getattr(scene, "hf_kick", None) is not None and len(scene.hf_kick):
+            hf = _arr(scene.hf_kick, np.float64)
+            L.oracle_set_hf_kick(self.h, C.c_int(len(hf)), _dp(hf))
 
     def _add_surface(self, s):
         alpha = np.zeros(8)

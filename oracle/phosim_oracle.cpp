@@ -115,7 +115,8 @@ enum Slot {
     S_PUPIL_R = 0, S_PUPIL_PHI = 1, S_LAM_BIN = 2, S_LAM_BLUR = 3,
     S_TIME = 4, S_SHAPE_A = 5, S_SHAPE_B = 6, S_CONV = 7,
     S_DIFF_A = 8, S_DIFF_B = 9, S_COAT0 = 10,   // coated surface k uses slot 10 + k (k < 6)
-    N_SLOTS = 16
+    S_HF_R = 16, S_HF_PSI = 17,                 // high-frequency kick: magnitude, direction
+    N_SLOTS = 20
 };
 
 inline double uniform01(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }  // (w + 1/2) 2^-32
@@ -167,6 +168,7 @@ struct Scene {
     std::vector<std::vector<double>> cdf;      // per SED, cumulative photon probability at bin ends
     int sersic_K = 0;
     std::vector<std::vector<double>> sersic;
+    std::vector<double> hf;      // quantiles of the high-frequency kick angle at lam_ref, u = (k + 1/2) / K
 };
 
 struct Source {
@@ -424,7 +426,7 @@ struct Draws { uint32_t w[N_SLOTS]; };
 
 Draws draw_photon(const Scene& sc, int src_id, uint64_t i) {
     Draws D;
-    for (uint32_t blk = 0; blk < 4; ++blk) {
+    for (uint32_t blk = 0; blk < 5; ++blk) {
         uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(i >> 32), (uint32_t)src_id, blk};
         philox4x32_10(ctr, (uint32_t)sc.seed, (uint32_t)(sc.seed >> 32), &D.w[4 * blk]);
     }
@@ -519,6 +521,23 @@ void sample_and_atmosphere_t(const Scene& sc, const Source& s, const Draws& D, T
             }
             nx = nx + kick * gx;
             ny = ny + kick * gy;
+            nz = -sqrt(T(1.0) - nx * nx - ny * ny);
+        }
+        // second kick (Sec. 2.3.2): a draw from the long-exposure PSF of the screens above kappa_crit,
+        // scaled like the refractive kick by (lambda / lambda_ref)^(-1/5)
+        if (!sc.hf.empty()) {
+            const int K = (int)sc.hf.size();
+            T f = T(uniform01(D.w[S_HF_R])) * T((double)K) - T(0.5);
+            int k = (int)std::floor(val(f));
+            if (k < 0) k = 0;
+            if (k > K - 2) k = K - 2;
+            T t = f - T((double)k);
+            if (val(t) < 0.0) t = T(0.0);
+            if (val(t) > 1.0) t = T(1.0);
+            T ang = (T(sc.hf[k]) * (T(1.0) - t) + T(sc.hf[k + 1]) * t) * (kick / T(sc.lam_ref * 1e-6 / (2.0 * M_PI)));
+            T psi = T(2.0 * M_PI) * T(uniform01(D.w[S_HF_PSI]));
+            nx = nx + ang * cos(psi);
+            ny = ny + ang * sin(psi);
             nz = -sqrt(T(1.0) - nx * nx - ny * ny);
         }
     }
@@ -775,6 +794,10 @@ void oracle_set_seds(void* p, double lam0, double dlam, int n_sed, int n_bins, c
 void oracle_get_cdf(void* p, int sed, double* out) {
     Scene* sc = (Scene*)p;
     for (int k = 0; k < sc->n_bins; ++k) out[k] = sc->cdf[sed][k];
+}
+void oracle_set_hf_kick(void* p, int K, const double* q) {
+    Scene* sc = (Scene*)p;
+    sc->hf.assign(q, q + K);
 }
 void oracle_set_sersic(void* p, int n_tab, int K, const double* r) {
     Scene* sc = (Scene*)p;

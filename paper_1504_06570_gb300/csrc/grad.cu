@@ -128,11 +128,12 @@ __device__ void surface_adjoint(const TraceParams& P, const GradParams& G, int s
     const double X[3] = {XD[0], XD[1], XD[2]}, D[3] = {XD[3], XD[4], XD[5]};
     double p[3], dl[3];
     to_surface(S, X, D, p, dl);
-    double l, zx, zy;
-    intersect(S, p, dl, l, zx, zy);
+    double l, Nfwd[3];
+    intersect(S, p, dl, l, Nfwd);
     const double h[3] = {fma(l, dl[0], p[0]), fma(l, dl[1], p[1]), fma(l, dl[2], p[2])};
     double zs, sx, sy, sxx, sxy, syy;
     sag_d2(S, nullptr, h[0], h[1], zs, sx, sy, sxx, sxy, syy);
+    const double zx = sx, zy = sy;            // the slopes that define the normal, at the root
     const double q = sqrt(1.0 + zx * zx + zy * zy);
     const double iq = 1.0 / q;
     const double N[3] = {-zx * iq, -zy * iq, iq};
@@ -147,7 +148,7 @@ __device__ void surface_adjoint(const TraceParams& P, const GradParams& G, int s
         hb[1] = fb[1];
         if (P.flags & PHOSIM_SENSOR) {
             const double n2 = silicon_index(lam);
-            refract(out, N[0], N[1], N[2], n1, n2);
+            refract(out, N[0], N[1], N[2], n1 / n2);
             ob[0] = L * fb[0];
             ob[1] = L * fb[1];
         }
@@ -158,7 +159,7 @@ __device__ void surface_adjoint(const TraceParams& P, const GradParams& G, int s
             out[1] = fma(-2.0 * dn, N[1], dl[1]);
             out[2] = fma(-2.0 * dn, N[2], dl[2]);
         } else {
-            refract(out, N[0], N[1], N[2], n1, material_index(P, S.material, lam));
+            refract(out, N[0], N[1], N[2], n1 / material_index(P, S.material, lam));
         }
         // X' = M^T h + o, D' = M^T out: adjoints into h, out, M and o
 #pragma unroll

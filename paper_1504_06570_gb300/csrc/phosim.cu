@@ -215,6 +215,66 @@ __global__ void sed_threshold_kernel(const double* __restrict__ flux, int n_sed,
     }
 }
 
+void destroy_graph(TraceGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = TraceGraph();
+}
+
+// The chief-ray and trace launches as one CUDA graph: captured once per precision on a private stream,
+// then replayed on the caller's stream with this call's kernel parameters and launch shapes.
+phosim_status launch_trace_graph(phosim_scene* sc, TraceParams& P, bool mixed, int blocks, int n_src, double* moments,
+                                 cudaStream_t st) {
+    TraceGraph& g = sc->graphs[mixed ? 1 : 0];
+    if (!g.exec) {
+        if (!sc->capture_stream) CU(cudaStreamCreateWithFlags(&sc->capture_stream, cudaStreamNonBlocking));
+        CU(cudaStreamBeginCapture(sc->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = launch_chief_rays(P, sc->d_src, n_src, moments, sc->capture_stream);
+        cudaError_t e2 = launch_trace(P, mixed, blocks, sc->threads, sc->capture_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e3 = cudaStreamEndCapture(sc->capture_stream, &graph);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            return PHOSIM_ERR_CUDA;
+        }
+        g.graph = graph;
+        if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+        size_t n = 0;
+        cudaGraphGetNodes(g.graph, nullptr, &n);
+        std::vector<cudaGraphNode_t> nodes(n);
+        cudaGraphGetNodes(g.graph, nodes.data(), &n);
+        for (cudaGraphNode_t node : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) continue;
+            if (kp.func == trace_kernel_ptr(mixed)) g.trace = node;
+            else if (kp.func == chief_kernel_ptr()) g.chief = node;
+        }
+        if (!g.trace || !g.chief) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    }
+    DSource* src_ptr = sc->d_src;
+    int n = n_src;
+    double* mom = moments;
+    void* chief_args[4] = {&P, &src_ptr, &n, &mom};
+    cudaKernelNodeParams kc = {};
+    kc.func = (void*)chief_kernel_ptr();
+    kc.gridDim = dim3((unsigned)((n_src + 127) / 128));
+    kc.blockDim = dim3(128);
+    kc.kernelParams = chief_args;
+    void* trace_args[1] = {&P};
+    cudaKernelNodeParams kt = {};
+    kt.func = (void*)trace_kernel_ptr(mixed);
+    kt.gridDim = dim3((unsigned)blocks);
+    kt.blockDim = dim3((unsigned)sc->threads);
+    kt.kernelParams = trace_args;
+    CU(cudaGraphExecKernelNodeSetParams(g.exec, g.chief, &kc));
+    CU(cudaGraphExecKernelNodeSetParams(g.exec, g.trace, &kt));
+    CU(cudaGraphLaunch(g.exec, st));
+    return PHOSIM_OK;
+}
+
 }  // namespace
 
 // =========================================================================================================
@@ -307,12 +367,16 @@ void phosim_destroy_scene(phosim_scene* sc) {
     free_all(sc->screen_mem);
     free_all(sc->sed_mem);
     free_all(sc->sersic_mem);
+    free_all(sc->hf_mem);
     cudaFree(sc->d_src);
     cudaFree(sc->d_prefix);
     cudaFree(sc->d_counters);
     cudaFree(sc->d_stage);
     cudaFree(sc->d_grad_scratch);
     cudaFree(sc->d_mom_scratch);
+    destroy_graph(sc->graphs[0]);
+    destroy_graph(sc->graphs[1]);
+    if (sc->capture_stream) cudaStreamDestroy(sc->capture_stream);
     (void)cudaGetLastError();
     delete sc;
 }
@@ -514,6 +578,26 @@ phosim_status phosim_load_sersic(phosim_scene* sc, const double* table, int n_ta
     return PHOSIM_OK;
 }
 
+phosim_status phosim_load_hf_kick(phosim_scene* sc, const double* q, int n) {
+    if (!sc || n < 0 || (n > 0 && (!q || n < 2))) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int i = 0; i < n; ++i) if (!(q[i] >= 0.0) || !is_finite(q[i]) || (i && q[i] < q[i - 1])) return PHOSIM_ERR_INVALID_ARGUMENT;
+    std::vector<void*> mem;
+    double* d = nullptr;
+    float* df = nullptr;
+    if (n > 0) {
+        std::vector<float> f(q, q + n);
+        phosim_status st = upload(mem, q, (size_t)n, &d);
+        if (st == PHOSIM_OK) st = upload(mem, f.data(), (size_t)n, &df);
+        if (st != PHOSIM_OK) { free_all(mem); return st; }
+    }
+    free_all(sc->hf_mem);
+    sc->hf_mem = mem;
+    sc->base.hf = d;
+    sc->base.hf32 = df;
+    sc->base.hf_K = n;
+    return PHOSIM_OK;
+}
+
 phosim_status phosim_set_schedule(phosim_scene* sc, int threads, int tile) {
     if (!sc || threads < 0 || tile < 0) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (threads) {
@@ -679,8 +763,13 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     P.image = d_image;
     P.moments = moments;
     P.records = records;
-    CU(launch_chief_rays(P, sc->d_src, n_src, moments, st));
-    CU(launch_trace(P, mixed, blocks, sc->threads, st));
+    if (P.flags & PHOSIM_GRAPH) {
+        phosim_status gs = launch_trace_graph(sc, P, mixed, blocks, n_src, moments, st);
+        if (gs != PHOSIM_OK) return gs;
+    } else {
+        CU(launch_chief_rays(P, sc->d_src, n_src, moments, st));
+        CU(launch_trace(P, mixed, blocks, sc->threads, st));
+    }
     sc->last_stream = st;
     if (host_image) {
         CU(cudaMemcpyAsync(image, d_image, img_bytes, cudaMemcpyDeviceToHost, st));

@@ -95,6 +95,9 @@ struct TraceParams {
     const unsigned long long* thr;            // n_sed x (n_bins - 1) integer thresholds on the bin draw
     const double* sersic;
     const float* sersic32;
+    int hf_K;                                 // quantiles of the high-frequency kick (0 = none)
+    const double* hf;
+    const float* hf32;
     // work and outputs: tile t of the launch is tile t - tile_prefix[s] of the source s with
     // tile_prefix[s] <= t < tile_prefix[s + 1]; a tile holds tile_photons consecutive photons
     const DSource* sources;
@@ -129,6 +132,7 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 //   block 1: time, shape a, shape b, conversion
 //   block 2: diffusion a, diffusion b, coated surface 0, coated surface 1
 //   block 3: coated surfaces 2..5
+//   block 4: high-frequency kick magnitude, direction
 __device__ __forceinline__ double u64of(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
 __device__ __forceinline__ float u32of(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
 
@@ -172,9 +176,9 @@ __device__ __forceinline__ bool sag(const DSurface& S, double x, double y, doubl
     if (S.flags & SF_CONIC) {
         const double arg = 1.0 - S.k1c2 * r2;
         if (arg < 0.0) return false;
-        const double sq = sqrt(arg);
-        z = S.c * r2 / (1.0 + sq);
-        g = S.c / sq;
+        const double rs = rsqrt(arg);
+        z = S.c * r2 / fma(arg, rs, 1.0);
+        g = S.c * rs;
     }
     if (S.flags & SF_EVEN) {
         const double pe = fma(r2, fma(r2, fma(r2, S.ae[3], S.ae[2]), S.ae[1]), S.ae[0]);
@@ -208,11 +212,11 @@ __device__ __forceinline__ bool sag(const DSurface& S, double x, double y, doubl
 // method on F(l) = p_z + l d_z - S(p_x + l d_x, p_y + l d_y) until the step is below 1e-8 mm.
 // On success l is the distance and (zx, zy) the slopes at the root (within 1e-8 mm of it).
 __device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[3], const double d[3], double& l,
-                                              double& zx, double& zy) {
+                                              double N[3]) {
     if (S.flags & SF_FLAT_ONLY) {
         if (d[2] == 0.0) return PHOSIM_LOST_MISSED;
         l = -p[2] / d[2];
-        zx = 0.0; zy = 0.0;
+        N[0] = 0.0; N[1] = 0.0; N[2] = 1.0;
         return 0;
     }
     const double A = S.c * fma(d[0], d[0], d[1] * d[1]) + S.kc * d[2] * d[2];
@@ -225,12 +229,14 @@ __device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[
     l = C / q;
     if (A != 0.0 && fma(-S.kc, fma(l, d[2], p[2]), 1.0) < 0.0) l = q / A;   // the other root is the vertex branch
     if (!(S.flags & (SF_EVEN | SF_ODD | SF_ZERN))) {
+        // the quadric's gradient (-c x, -c y, 1 - (1 + kappa) c z) is along (-z_x, -z_y, 1)
         const double x = fma(l, d[0], p[0]), y = fma(l, d[1], p[1]), z = fma(l, d[2], p[2]);
-        const double inv_s = 1.0 / fma(-S.kc, z, 1.0);
-        zx = S.c * x * inv_s;
-        zy = S.c * y * inv_s;
+        const double vx = -S.c * x, vy = -S.c * y, vz = fma(-S.kc, z, 1.0);
+        const double inv = rsqrt(fma(vx, vx, fma(vy, vy, vz * vz)));
+        N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
         return 0;
     }
+    double zx = 0.0, zy = 0.0;
 #pragma unroll 1
     for (int it = 0; it < 20; ++it) {
         const double x = fma(l, d[0], p[0]), y = fma(l, d[1], p[1]);
@@ -239,9 +245,14 @@ __device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[
         const double F = fma(l, d[2], p[2]) - zs;
         const double dF = d[2] - zx * d[0] - zy * d[1];
         if (dF == 0.0) return PHOSIM_LOST_NEWTON;
-        const double step = F / dF;
+        // a single-precision reciprocal of the slope: the iteration still contracts by ~1e-7 per step
+        const double step = F * (double)__frcp_rn((float)dF);
         l -= step;
-        if (fabs(step) < 1e-8) return 0;
+        if (fabs(step) < 1e-8) {
+            const double inv = rsqrt(fma(zx, zx, fma(zy, zy, 1.0)));
+            N[0] = -zx * inv; N[1] = -zy * inv; N[2] = inv;
+            return 0;
+        }
     }
     return PHOSIM_LOST_NEWTON;
 }
@@ -264,11 +275,10 @@ __device__ __forceinline__ float silicon_index_f(float lam_nm) {
     return 3.36f + 0.211f * E + 2.79f * expf((E - 3.30f) * (1.0f / 0.398f));
 }
 
-// Snell's law in vector form (Sec. 2.4.2); false on total internal reflection
-__device__ __forceinline__ bool refract(double d[3], double Nx, double Ny, double Nz, double n1, double n2) {
+// Snell's law in vector form (Sec. 2.4.2) with mu = n1 / n2; false on total internal reflection
+__device__ __forceinline__ bool refract(double d[3], double Nx, double Ny, double Nz, double mu) {
     double cosi = -(d[0] * Nx + d[1] * Ny + d[2] * Nz);
     if (cosi < 0.0) { Nx = -Nx; Ny = -Ny; Nz = -Nz; cosi = -cosi; }
-    const double mu = n1 / n2;
     const double k = 1.0 - mu * mu * (1.0 - cosi * cosi);
     if (k < 0.0) return false;
     const double a = mu * cosi - sqrt(k);

@@ -5,6 +5,13 @@
 
 #include "phosim_device.cuh"
 
+// One captured [chief rays, trace] launch pair, replayed with updated kernel parameters.
+struct TraceGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t chief = nullptr, trace = nullptr;
+};
+
 struct phosim_scene {
     phosim::TraceParams base;       // scalars and device table pointers; per-call fields filled by a trace
     int precision = PHOSIM_PLAIN_FP64;
@@ -22,6 +29,7 @@ struct phosim_scene {
     std::vector<void*> screen_mem;  // gradient screens
     std::vector<void*> sed_mem;
     std::vector<void*> sersic_mem;
+    std::vector<void*> hf_mem;      // high-frequency kick quantiles
     // per-call scratch, grown on demand
     phosim::DSource* d_src = nullptr;
     size_t cap_src = 0;
@@ -37,11 +45,16 @@ struct phosim_scene {
     size_t cap_grad = 0;
     double* d_mom_scratch = nullptr;
     size_t cap_mom = 0;
+    // CUDA graphs of the trace launch (PHOSIM_GRAPH), one per precision, captured on a private stream
+    TraceGraph graphs[2];
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace phosim {
 cudaError_t launch_trace(const TraceParams& P, bool mixed, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_chief_rays(const TraceParams& P, DSource* sources, int n_src, double* moments, cudaStream_t st);
 cudaError_t trace_occupancy(bool mixed, int threads, int* blocks_per_sm);
+const void* trace_kernel_ptr(bool mixed);
+const void* chief_kernel_ptr();
 void free_all(std::vector<void*>& v);
 }  // namespace phosim

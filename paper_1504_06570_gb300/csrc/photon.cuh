@@ -95,7 +95,7 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                                        uint4 w3, PhotonOut& R, ForwardRecord* fr = nullptr) {
     double n_cur = 1.0;
     int glass_mat = -1;
-    double glass_n = 1.0;
+    double glass_n = 1.0, glass_inv = 1.0;
 #pragma unroll 1
     for (int si = 0; si < P.n_surf; ++si) {
         const DSurface& S = P.surf[si];
@@ -105,14 +105,13 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
         }
         double p[3], dl[3];
         to_surface(S, X, D, p, dl);
-        double l, zx, zy;
-        const uint32_t why = intersect(S, p, dl, l, zx, zy);
+        double l, Nv[3];
+        const uint32_t why = intersect(S, p, dl, l, Nv);
         if (why) { R.flags = lost(why, si); return; }
         p[0] = fma(l, dl[0], p[0]);
         p[1] = fma(l, dl[1], p[1]);
         p[2] = fma(l, dl[2], p[2]);
-        const double inn = 1.0 / sqrt(1.0 + zx * zx + zy * zy);
-        const double Nx = -zx * inn, Ny = -zy * inn, Nz = inn;
+        const double Nx = Nv[0], Ny = Nv[1], Nz = Nv[2];
         if (S.kind == PHOSIM_DETECTOR) {
             const double hx = p[0] - P.xlo, hy = p[1] - P.ylo;
             if (FULL && !(hx >= 0.0 && hy >= 0.0 && hx < P.nx * P.pixel && hy < P.ny * P.pixel)) {
@@ -126,13 +125,13 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                 double L, sigma, gxd, gyd;
                 if constexpr (MIXED) {
                     const float n_si = silicon_index_f((float)lam);
-                    if (!refract(dl, Nx, Ny, Nz, n_cur, (double)n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+                    if (!refract(dl, Nx, Ny, Nz, n_cur / (double)n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
                     const float ell = lerp_table_f(P.ell32, P.n_ell, (float)((lam - P.ell_lam0) * P.inv_ell_dlam));
                     const float Lf = ell * -logf(u32of(w1.w));
                     L = (double)Lf;
                 } else {
                     const double n_si = silicon_index(lam);
-                    if (!refract(dl, Nx, Ny, Nz, n_cur, n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+                    if (!refract(dl, Nx, Ny, Nz, n_cur / n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
                     const double ell = lerp_table(P.ell, P.n_ell, (lam - P.ell_lam0) * P.inv_ell_dlam);
                     L = ell * -log(u64of(w1.w));
                 }
@@ -201,14 +200,20 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
             dl[2] = fma(-2.0 * dn, Nz, dl[2]);
         } else {
             const DMaterial& m = P.mat[S.material];
-            double n_next = 1.0;
+            double n_next = 1.0, inv_next = 1.0;
             if (m.kind == PHOSIM_SELLMEIER) {
-                if (glass_mat != S.material) { glass_n = sellmeier(m, lam); glass_mat = S.material; }
+                if (glass_mat != S.material) {
+                    glass_n = sellmeier(m, lam);
+                    glass_inv = 1.0 / glass_n;
+                    glass_mat = S.material;
+                }
                 n_next = glass_n;
+                inv_next = glass_inv;
             } else if (m.kind == PHOSIM_SILICON) {
                 n_next = silicon_index(lam);
+                inv_next = 1.0 / n_next;
             }
-            if (!refract(dl, Nx, Ny, Nz, n_cur, n_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+            if (!refract(dl, Nx, Ny, Nz, n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
             n_cur = n_next;
         }
         from_surface(S, p, dl, X, D);
@@ -303,7 +308,9 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
             ny += s.a * g * sp;
         }
     }
-    double nz = -sqrt(1.0 - nx * nx - ny * ny);
+    // 1 / |n_z| = rsqrt(1 - n_x^2 - n_y^2): layer-to-layer distances are height differences times it
+    double w = fma(-nx, nx, fma(-ny, ny, 1.0));
+    double rinv = rsqrt(w);
     const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
     uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
     if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
@@ -320,7 +327,7 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
     sag(P.pupil_surf, x, y, zs, zx, zy);
     double z = P.pupil_z + zs;
     {
-        const double l = (P.h_top - z) / (-nz);
+        const double l = (P.h_top - z) * rinv;
         x = fma(-nx, l, x);
         y = fma(-ny, l, y);
         z = P.h_top;
@@ -331,12 +338,20 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         if constexpr (MIXED) {
             kick = (double)((float)P.kick0 * exp2f(-0.2f * log2f((float)(lam / P.lam_ref))));
         } else {
-            kick = P.kick0 * pow(lam / P.lam_ref, -0.2);
+            // (lambda / lambda_ref)^(-1/5): single-precision seed, then two Newton steps of y -> y (1 + (1 - a y^5) / 5)
+            const double a = lam / P.lam_ref;
+            double y5 = (double)powf((float)a, -0.2f);
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const double y2 = y5 * y5;
+                y5 = fma(y5 * 0.2, fma(-a * y2, y2 * y5, 1.0), y5);
+            }
+            kick = P.kick0 * y5;
         }
 #pragma unroll 1
         for (int k = 0; k < P.n_layers; ++k) {
             const DLayer& L = P.layer[k];
-            const double ll = (z - L.z) / (-nz);
+            const double ll = (z - L.z) * rinv;
             x = fma(nx, ll, x);
             y = fma(ny, ll, y);
             z = L.z;
@@ -346,11 +361,34 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
             for (int q = 0; q < L.n_scales; ++q) screen_gradient<MIXED>(L.s[q], sx, sy, gx, gy);
             nx = fma(kick, gx, nx);
             ny = fma(kick, gy, ny);
-            nz = -sqrt(1.0 - nx * nx - ny * ny);
+            w = fma(-nx, nx, fma(-ny, ny, 1.0));
+            rinv = rsqrt(w);
+        }
+        // second kick (Sec. 2.3.2): a draw from the long-exposure PSF of the screens above kappa_crit,
+        // scaled like the refractive kick by (lambda / lambda_ref)^(-1/5)
+        if (P.hf_K > 0) {
+            const uint4 w4 = philox(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
+            const double scale = kick / P.kick0;
+            if constexpr (MIXED) {
+                const float ang = lerp_table_f(P.hf32, P.hf_K, u32of(w4.x) * (float)P.hf_K - 0.5f) * (float)scale;
+                float sp, cp;
+                sincospif(2.f * u32of(w4.y), &sp, &cp);
+                nx += (double)(ang * cp);
+                ny += (double)(ang * sp);
+            } else {
+                const double ang = lerp_table(P.hf, P.hf_K, u64of(w4.x) * P.hf_K - 0.5) * scale;
+                double sp, cp;
+                sincospi(2.0 * u64of(w4.y), &sp, &cp);
+                nx = fma(ang, cp, nx);
+                ny = fma(ang, sp, ny);
+            }
+            w = fma(-nx, nx, fma(-ny, ny, 1.0));
+            rinv = rsqrt(w);
         }
     }
+    const double nz = -w * rinv;
     {
-        const double l = (z - P.z_ent) / (-nz);
+        const double l = (z - P.z_ent) * rinv;
         x = fma(nx, l, x);
         y = fma(ny, l, y);
         z = P.z_ent;

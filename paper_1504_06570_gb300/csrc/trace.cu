@@ -195,6 +195,11 @@ cudaError_t launch_trace(const TraceParams& P, bool mixed, int blocks, int threa
     return cudaGetLastError();
 }
 
+const void* trace_kernel_ptr(bool mixed) {
+    return mixed ? (const void*)trace_kernel<true> : (const void*)trace_kernel<false>;
+}
+const void* chief_kernel_ptr() { return (const void*)chief_ray_kernel; }
+
 cudaError_t trace_occupancy(bool mixed, int threads, int* blocks_per_sm) {
     if (mixed) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<true>, threads, 0);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<false>, threads, 0);

@@ -142,6 +142,7 @@ class Scene:
     atmosphere: bool = True
     sensor: bool = True          # False: record the hit on the detector surface, no silicon
     z_entrance: float = None     # plane (mm) where the raytrace starts, below every layer, above every optic
+    hf_kick: np.ndarray = None   # quantiles (rad at lambda_ref) of the high-frequency kick, or None
 
     def __post_init__(self):
         if self.z_entrance is None:
@@ -532,3 +533,76 @@ def grad_grid_scene(n_side=8, photons=1_000_000, seed=5, zernike_nm_max=50.0):
     params = [(1, f) for f in (0, 1, 3, 4)] + [(c, f) for c in camera for f in (0, 1, 3, 4)]
     params += [(m, 100 + j) for m in range(3) for j in range(3, 22)]
     return sc, params, camera
+
+
+# ----------------------------------------------------------------------------------------------------------
+# high-frequency atmospheric kick (Sec. 2.3.2): the long-exposure PSF of the kappa > kappa_crit screens
+# ----------------------------------------------------------------------------------------------------------
+
+def structure_function_highpass(rho_m, r0_m, L0_m, f_crit):
+    """Phase structure function of the part of the spectrum above f_crit (cycles/m):
+    D(rho) = 4 pi int_fcrit^inf [1 - J0(2 pi f rho)] PSD(f) f df (Sec. 2.3.2, high-pass form), by quadrature on
+    a logarithmic frequency grid; and the high-pass phase variance sigma^2 = 2 pi int PSD f df."""
+    from scipy import special
+    f = np.exp(np.linspace(math.log(f_crit), math.log(f_crit * 1e5), 200001))
+    w = phase_psd(f * f, r0_m, L0_m) * f * f          # PSD f df with df = f dlnf
+    dlnf = math.log(f[1] / f[0])
+    rho = np.atleast_1d(np.asarray(rho_m, np.float64))
+    out = np.empty_like(rho)
+    for i, r in enumerate(rho):
+        out[i] = 4.0 * math.pi * np.trapezoid(w * (1.0 - special.j0(2.0 * math.pi * f * r)), dx=dlnf)
+    sigma2 = 2.0 * math.pi * np.trapezoid(w, dx=dlnf)
+    return out, sigma2
+
+
+def long_exposure_psf_radial(D_of_rho, lam_m, drho, n=2048):
+    """Radially symmetric long-exposure PSF from a structure function: B(rho) = exp(-D/2) on an n x n grid of
+    spacing drho, Fourier transformed; returns (theta grid of the radial profile in rad, cumulative fraction
+    of the PSF within theta).  D_of_rho maps radii (m) to D."""
+    x = (np.arange(n) - n // 2) * drho
+    X, Y = np.meshgrid(x, x)
+    R = np.hypot(X, Y)
+    rr = np.unique(np.round(R.ravel() / drho * 8) / 8 * drho)
+    B = np.interp(R, rr, np.exp(-0.5 * D_of_rho(rr)))
+    psf = np.abs(np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(B))))
+    psf /= psf.sum()
+    dth = lam_m / (n * drho)
+    TH = np.hypot(*np.meshgrid(x / drho * dth, x / drho * dth))
+    order = np.argsort(TH.ravel())
+    th = TH.ravel()[order]
+    cdf = np.cumsum(psf.ravel()[order])
+    return th, cdf
+
+
+def fwhm_radial(D_of_rho, lam_m, drho, n=2048):
+    """Full width at half maximum (rad) of the long-exposure PSF of D_of_rho."""
+    x = (np.arange(n) - n // 2) * drho
+    X, Y = np.meshgrid(x, x)
+    R = np.hypot(X, Y)
+    rr = np.unique(np.round(R.ravel() / drho * 8) / 8 * drho)
+    B = np.interp(R, rr, np.exp(-0.5 * D_of_rho(rr)))
+    psf = np.real(np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(B))))
+    row = psf[n // 2, n // 2:] / psf[n // 2, n // 2]
+    k = int(np.argmax(row < 0.5))
+    frac = (row[k - 1] - 0.5) / (row[k - 1] - row[k])
+    return 2.0 * (k - 1 + frac) * lam_m / (n * drho)
+
+
+def high_frequency_kick_table(r0_m=0.15, L0_m=20.0, lam_ref_nm=500.0, K=4096, crit=1.5):
+    """Quantiles of the kick angle (rad, at lam_ref) of the second, statistical kick of Sec. 2.3.2: the
+    long-exposure PSF of the screens above kappa_crit = 2 pi / (crit r0), at u = (k + 1/2) / K.  The part
+    exp(-sigma^2) of the PSF that the high-pass screens leave unscattered has zero kick."""
+    lam = lam_ref_nm * 1e-9
+    f_crit = 1.0 / (crit * r0_m)
+    rho_tab = np.r_[0.0, np.exp(np.linspace(math.log(1e-4), math.log(50.0 * r0_m), 400))]
+    D_tab, sigma2 = structure_function_highpass(rho_tab[1:], r0_m, L0_m, f_crit)
+    D_tab = np.r_[0.0, D_tab]
+    Dfun = lambda r: np.interp(r, rho_tab, D_tab, right=2.0 * sigma2)
+    core = math.exp(-sigma2)
+    drho = r0_m / 40.0
+    th, cdf_total = long_exposure_psf_radial(Dfun, lam, drho)
+    # the FFT of B = (B - core) + core puts the unscattered part in the central sample: remove it
+    cdf_halo = np.clip((cdf_total - core) / (1.0 - core), 0.0, 1.0)
+    u = (np.arange(K) + 0.5) / K
+    q = np.where(u < core, 0.0, np.interp((u - core) / (1.0 - core), cdf_halo, th))
+    return q, sigma2

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libphosim.so")
 
 MAX_SURFACES, MAX_LAYERS, MAX_SCALES, MAX_ZERNIKE = 16, 8, 2, 28
 PLAIN_FP64, MIXED = 0, 1
-ATMOSPHERE, SENSOR, EARLY_REJECT = 1, 2, 4
+ATMOSPHERE, SENSOR, EARLY_REJECT, GRAPH = 1, 2, 4, 8
 MOMENT_WORDS = 8
 F_DETECTED = 1
 
@@ -103,6 +103,9 @@ def lib():
                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), vp]
         L.phosim_set_schedule.argtypes = [vp, C.c_int, C.c_int]
+        L.phosim_load_hf_kick.argtypes = [vp, C.POINTER(C.c_double), C.c_int]
+        L.phosim_autotune.argtypes = [vp, C.POINTER(Source), C.c_int, C.POINTER(C.c_uint64), C.c_uint64, vp,
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.phosim_get_counters.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int]
         L.phosim_destroy_scene.argtypes = [vp]
         L.phosim_destroy_scene.restype = None
@@ -153,7 +156,7 @@ def surface_struct(s: I.Surface) -> Surface:
 class Scene:
     """A scene loaded into the CUDA library (device copies owned by the library)."""
 
-    def __init__(self, scene: I.Scene, precision=PLAIN_FP64, early_reject=False):
+    def __init__(self, scene: I.Scene, precision=PLAIN_FP64, early_reject=False, graph=False):
         L = lib()
         self.L = L
         self.scene = scene
@@ -163,7 +166,7 @@ class Scene:
         self._sig = np.ascontiguousarray(d.sigma, np.float64)
         desc = SceneDesc(seed=scene.seed, precision=precision,
                          flags=(ATMOSPHERE if scene.atmosphere else 0) | (SENSOR if scene.sensor else 0)
-                         | (EARLY_REJECT if early_reject else 0),
+                         | (EARLY_REJECT if early_reject else 0) | (GRAPH if graph else 0),
                          pupil_r_in=scene.pupil_r_in, pupil_r_out=scene.pupil_r_out, h_top=scene.h_top,
                          z_entrance=scene.z_entrance, lambda_ref=scene.lambda_ref, nx=d.nx, ny=d.ny, pixel=d.pixel,
                          x0=d.x0, y0=d.y0, t_si=d.t_si, ell_lam0=d.ell_lam0, ell_dlam=d.ell_dlam,
@@ -179,6 +182,10 @@ class Scene:
                                                       scene.sed_lam0, scene.sed_dlam))
         sr = np.ascontiguousarray(scene.sersic, np.float64)
         _check("phosim_load_sersic", L.phosim_load_sersic(self.h, _dptr(sr), sr.shape[0], sr.shape[1]))
+        hf = getattr(scene, "hf_kick", None)
+        if hf is not None and len(hf):
+            hq = np.ascontiguousarray(hf, np.float64)
+            _check("phosim_load_hf_kick", L.phosim_load_hf_kick(self.h, _dptr(hq), len(hq)))
         self.src = None
         self.set_sources(scene.sources)
 

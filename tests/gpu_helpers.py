@@ -10,9 +10,9 @@ MARGIN_NM = 1e-6
 
 
 def run_gpu(scene, precision=P.PLAIN_FP64, records=True, moments=True, schedule=None, n_photons=None, first=None,
-            host_image=False, early_reject=False):
+            host_image=False, early_reject=False, graph=False):
     import torch
-    s = P.Scene(scene, precision, early_reject=early_reject)
+    s = P.Scene(scene, precision, early_reject=early_reject, graph=graph)
     if schedule:
         s.set_schedule(*schedule)
     cnt = scene.sources.n_photons if n_photons is None else np.asarray(n_photons, np.uint64)
@@ -94,7 +94,17 @@ def compare_moments(gpu_m, ora_m, rel=1e-3):
     return g
 
 
-def test_system_scene(n_photons=40000, sensor=True, atmosphere=True, chip=512, sources=None, screen_n=256):
+_HF = None
+
+
+def hf_table():
+    global _HF
+    if _HF is None:
+        _HF = I.high_frequency_kick_table(K=1024)[0]
+    return _HF
+
+
+def test_system_scene(n_photons=40000, sensor=True, atmosphere=True, chip=512, sources=None, screen_n=256, hf=False):
     """A small catadioptric system exercising every surface feature: an annular paraboloid with a
     Zernike figure and a tilt, a decentred aspheric meniscus lens, a coated filter plate, a detector."""
     mats = [I.Material(I.VACUUM), I.Material(I.SELLMEIER, I.FUSED_SILICA_B, I.FUSED_SILICA_C), I.Material(I.SILICON)]
@@ -125,7 +135,7 @@ def test_system_scene(n_photons=40000, sensor=True, atmosphere=True, chip=512, s
     return I.Scene(seed=12345, pupil_r_in=100.0, pupil_r_out=500.0, surfaces=surfaces, materials=mats, coatings=[coat],
                    detector=det, layers=layers, sed_lam0=400.0, sed_dlam=1.0, sed_flux=I.sed_tables([5800.0, 3500.0], 400.0, 1.0, nb),
                    sersic=np.stack([I.sersic_radius_table(1.0, 256), I.sersic_radius_table(3.5, 256)]), sources=sources,
-                   atmosphere=atmosphere, sensor=sensor)
+                   atmosphere=atmosphere, sensor=sensor, hf_kick=hf_table() if hf else None)
 
 
 def mixed_sources(counts, seed=3):

@@ -73,6 +73,24 @@ def test_catadioptric_system_all_surface_features(oracle_mod, precision):
     assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
 
 
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED])
+def test_second_atmospheric_kick(oracle_mod, precision):
+    """Sec. 2.3.2 second kick: the same scene with the high-frequency kick table loaded."""
+    counts = [4000, 2500, 33]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=8), hf=True)
+    gpu = G.run_gpu(sc, precision, early_reject=True)
+    ora = G.oracle_trace(oracle_mod, sc)
+    det_g, det_o = (gpu["rec"]["flags"] & 1) == 1, (ora["flags"] & 1) == 1
+    if precision == P.PLAIN_FP64:
+        assert np.all((det_g == det_o) | G.boundary_mask(ora))
+        both = det_g & det_o
+        err = np.maximum(np.abs(gpu["rec"]["x"][both] - ora["x"][both]), np.abs(gpu["rec"]["y"][both] - ora["y"][both]))
+        assert err.max() / sc.detector.pixel < 1e-6
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
+    else:
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+
+
 @pytest.mark.parametrize("schedule", [(32, 32), (64, 96), (256, 1024), (128, 0)])
 def test_schedule_does_not_change_results(oracle_mod, schedule):
     """Counter-based streams: the result depends on neither the block size nor the tile size."""
@@ -134,6 +152,32 @@ def test_early_rejection_keeps_the_detected_photons(oracle_mod, precision):
     if precision == P.PLAIN_FP64:
         ora = G.oracle_trace(oracle_mod, sc)
         assert np.array_equal(det_e, (ora["flags"] & 1) == 1)
+
+
+def test_graph_replay_matches_direct_launches():
+    """PHOSIM_GRAPH: the captured launch pair replays with each call's parameters (different photon ranges,
+    a different source count) and gives the direct launches' records and images."""
+    import torch
+    counts = np.array([700, 1500, 33], np.uint64)
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=4))
+    ref = P.Scene(sc, P.MIXED, early_reject=True)
+    gr = P.Scene(sc, P.MIXED, early_reject=True, graph=True)
+    d = sc.detector
+    for first, sub in ((None, None), (np.array([5, 0, 1], np.uint64), None), (None, [1])):
+        outs = []
+        for s in (ref, gr):
+            if sub is not None:
+                s.set_sources(sc.sources.subset(sub))
+            n = int(s.n_photons.sum())
+            img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+            rec = torch.zeros(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+            s.trace(img, rec, None, first=first)
+            torch.cuda.synchronize()
+            outs.append((img.cpu().numpy(), P.records_to_numpy(rec)))
+        assert np.array_equal(outs[0][0], outs[1][0])
+        assert np.array_equal(outs[0][1], outs[1][1])
+    ref.close()
+    gr.close()
 
 
 def test_invalid_sources_are_rejected():

@@ -480,3 +480,44 @@ def test_screen_structure_function_von_karman():
         val, _ = integrate.quad(lambda f: (1 - special.j0(2 * np.pi * f * r)) * I.phase_psd(f * f, r0, L0) * f,
                                 0, np.inf, limit=400)
         assert abs(Dm / (4 * np.pi * val) - 1) < 0.12, (r, Dm, 4 * np.pi * val)
+
+
+# ---------------------------------------------------------------------------------------------- Sec. 2.3.2 second kick
+def test_long_exposure_psf_generator_kolmogorov_fwhm():
+    """The long-exposure PSF of a Kolmogorov screen, B = exp(-D/2) with D = 6.88 (rho/r0)^(5/3), has a FWHM of
+    0.976 lambda / r0 (Fried 1966; Roddier 1981): pins the Fourier transform behind the second-kick table."""
+    lam, r0 = 500e-9, 0.15
+    fw = I.fwhm_radial(lambda r: 6.88 * (r / r0) ** (5 / 3), lam, r0 / 40)
+    assert abs(fw / (lam / r0) - 0.976) < 0.005
+
+
+def test_high_pass_phase_variance_closed_form():
+    """Variance of the screens above f_crit: 2 pi int_fc^inf 0.023 r0^(-5/3) f^(-11/3) f df
+    = 2 pi 0.023 (3/5) r0^(-5/3) f_crit^(-5/3) (Kolmogorov, closed form)."""
+    r0, fc = 0.15, 1.0 / (1.5 * 0.15)
+    _, s2 = I.structure_function_highpass(np.array([0.01]), r0, np.inf, fc)
+    assert abs(s2 / (2 * np.pi * 0.023 * 0.6 * r0 ** (-5 / 3) * fc ** (-5 / 3)) - 1) < 2e-3
+
+
+def test_second_kick_distribution(oracle_mod):
+    """Sec. 2.3.2: with a flat screen only the second kick acts.  A fraction exp(-sigma^2) of the photons is
+    not kicked (binomial), directions are uniform (KS), and at another wavelength the kicks of the same
+    photons scale by (lambda_1 / lambda_2)^(-1/5)."""
+    q, s2 = I.high_frequency_kick_table(K=2048)
+    N, p = 64, 20.0
+    flat = I.Layer(z=5.0e6, scales=[I.ScreenScale(p, np.zeros((N, N)))])
+    outs = []
+    for lo in (450.0, 900.0):
+        sc = mirror_scene(20000.0, -1.0, 10000.0, atmosphere=True, layers=[flat], n_photons=20000,
+                          lam_lo=lo, lam_hi=lo + 1.0)
+        sc.hf_kick = q
+        o, (pos, d, lam, t) = _pre(oracle_mod, sc, 20000)
+        outs.append((np.hypot(d[:, 0], d[:, 1]), np.arctan2(d[:, 1], d[:, 0]), lam))
+    (a1, psi1, l1), (a2, psi2, l2) = outs
+    n = len(a1)
+    core = np.exp(-s2)
+    zero = np.mean(a1 < 1e-12)
+    assert abs(zero - core) < 4 * np.sqrt(core * (1 - core) / n) + 1.0 / 2048
+    k = a1 > 1e-12
+    assert stats.kstest((psi1[k] + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-3
+    np.testing.assert_allclose(a1[k] / a2[k], (l1[k] / l2[k]) ** -0.2, rtol=1e-9)
