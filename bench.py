@@ -97,6 +97,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "launches_three_mirror_1e8.md")
+KERNEL_SOURCES = ("paper_1504_06570_gb300/csrc/photon.cuh", "paper_1504_06570_gb300/csrc/trace.cu",
+                  "paper_1504_06570_gb300/csrc/phosim_device.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(photons):
+    """DRAM bytes per launch of the mixed trace kernel from the committed ncu summary, scaled to this launch's
+    photons, or None when the kernel sources changed since that capture."""
+    import re
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_record: bytes=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text)
+    if not m or m.group(3) != kernel_source_hash():
+        return None
+    return int(m.group(1)) * photons / int(m.group(2))
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -144,6 +172,15 @@ def moment_errors(gpu_m, ora_rec, n_src):
     a = np.array(out)
     return {"stars": len(a), "max_centroid_over_size": float(a[:, 0].max()), "max_rel_T": float(a[:, 1].max()),
             "max_de1": float(a[:, 2].max()), "max_de2": float(a[:, 3].max()), "max_rel_count": float(a[:, 4].max())}
+
+
+def gather_bytes_per_launch(sc, ops, photons):
+    """Algorithmic screen bytes: one 32-byte 2 x 2 gradient block per scale and layer for every photon that
+    survives the dynamic transmission test (fraction from the oracle's count, photons with no work)."""
+    n_scales = sum(len(L.scales) for L in sc.layers)
+    surv = ops.get("survivors", None)
+    frac = surv if surv is not None else 1.0
+    return int(32 * n_scales * frac * photons)
 
 
 def precision_split(sc, mixed, plain, counts, dev):
@@ -392,7 +429,9 @@ def main():
         achieved = fl_opt * photons / kernel_s / 1e12
         peak = fp64_rate or FP64_NOMINAL_TFLOPS
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": None,
+                            "frac": achieved / peak, "traffic": recorded_traffic(photons),
+                            "traffic_unit": "DRAM bytes per launch (ncu, committed summary)",
+                            "algorithmic_gather_bytes": gather_bytes_per_launch(sc, ops, photons),
                             "note": (f"FP64 optics flops {fl_opt:.0f} per sampled photon (oracle op count with the dynamic "
                                      f"transmission rejection; +{fl_pre:.0f} sampling and atmosphere flops, mostly FP32 "
                                      f"here) over the mixed step time; peak = "

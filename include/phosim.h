@@ -61,6 +61,10 @@ enum {
 #define PHOSIM_GRAPH 8u          /* launch the chief-ray and trace kernels of phosim_trace as one CUDA graph,
                                     captured on the first call (per precision) and replayed with each call's
                                     parameters */
+#define PHOSIM_BACK_REFLECT 16u  /* back-side reflection (Sec. 2.4.2): a photon whose conversion length takes it
+                                    past the back of the silicon is reflected there with the Fresnel probability
+                                    of the silicon / vacuum interface at normal incidence, ((n - 1) / (n + 1))^2,
+                                    and converts on its way back (no interference fringing) */
 #define PHOSIM_EARLY_REJECT 4u   /* dynamic transmission (Sec. 3.2): decide each coating's accept draw against
                                     the largest transmission over incidence angles at the photon's wavelength
                                     before propagating it.  The detected photons, image and moments are
@@ -72,7 +76,7 @@ enum {
 #define PHOSIM_F_DETECTED 1u
 enum {
     PHOSIM_LOST_VIGNETTED = 1, PHOSIM_LOST_MISSED = 2, PHOSIM_LOST_NEWTON = 3, PHOSIM_LOST_TIR = 4,
-    PHOSIM_LOST_COATING = 5, PHOSIM_LOST_OFF_CHIP = 6, PHOSIM_LOST_NOT_CONVERTED = 7
+    PHOSIM_LOST_COATING = 5, PHOSIM_LOST_OFF_CHIP = 6, PHOSIM_LOST_NOT_CONVERTED = 7, PHOSIM_LOST_DEAD_LAYER = 8
 };
 
 /* Scene description (Sec. 2.2 pupil and top of the atmosphere; Sec. 2.4.1 detector device; Sec. 2.4.2
@@ -94,6 +98,8 @@ typedef struct phosim_scene_desc {
     const double* ell;          /* mm, linear interpolation, clamped at the ends */
     int32_t n_sigma;            /* >= 2 */
     const double* sigma;        /* diffusion sigma (mm) at depths k t_si / (n_sigma - 1) below the entrance */
+    double dead_layer;          /* field-free layer at the entrance (Sec. 2.4.2), mm: photons converting in it
+                                   are lost; 0 = none */
 } phosim_scene_desc;
 
 /* One optical surface (Sec. 2.4.1, Table 1): z(r) = r^2 / (R (1 + sqrt(1 - (1 + kappa) r^2 / R^2)))
@@ -243,7 +249,7 @@ phosim_status phosim_autotune(phosim_scene* scene, const phosim_source* sources,
                               int* out_threads, int* out_tile);
 
 /* Totals of the last phosim_trace: out[0] = photons traced, out[1] = detected, out[1 + r] = dropped for
-   reason r = 1..7 (PHOSIM_LOST_*).  n >= 9.  Synchronises the scene's last stream. */
+   reason r = 1..8 (PHOSIM_LOST_*).  n >= 10.  Synchronises the scene's last stream. */
 phosim_status phosim_get_counters(phosim_scene* scene, uint64_t* out, int n);
 
 /* Allocation-free variant of phosim_trace (the paper has no counterpart; it exists for callers of this
@@ -268,6 +274,15 @@ phosim_status phosim_get_counters(phosim_scene* scene, uint64_t* out, int n);
 phosim_status phosim_trace_noalloc(phosim_scene* scene, const phosim_source* sources, int n_src,
                                    const uint64_t* n_photons, const uint64_t* first, uint32_t* image,
                                    phosim_photon_record* records, double* moments, void* stream);
+
+/* Saturation and bleeding (Sec. 2.5) as a pass over a finished image: in each half of every row (the halves
+   meet at the centre implant, column nx / 2), pixels are visited left to right and electrons above
+   full_well move to the closest pixels below full well in that half-row, alternating left then right at
+   equal distance; electrons that find no room in the half-row are removed.  image: device, nx * ny,
+   updated in place on stream.  removed: NULL or a device uint64 that receives the count of removed
+   electrons (added to).  Errors: INVALID_ARGUMENT, CUDA. */
+phosim_status phosim_bleed(uint32_t* image, int nx, int ny, uint32_t full_well, unsigned long long* removed,
+                           void* stream);
 
 void phosim_destroy_scene(phosim_scene* scene);
 const char* phosim_status_string(phosim_status status);

@@ -92,6 +92,8 @@ class Oracle:
                           C.c_int(flux.shape[1]), _dp(flux))
         sr = _arr(scene.sersic, np.float64)
         L.oracle_set_sersic(self.h, C.c_int(sr.shape[0]), C.c_int(sr.shape[1]), _dp(sr))
+        L.oracle_set_sensor_options(self.h, C.c_int(int(getattr(scene, "back_reflect", False))),
+                                    C.c_double(float(getattr(scene.detector, "dead_layer", 0.0))))
         if getattr(scene, "hf_kick", None) is not None and len(scene.hf_kick):
             hf = _arr(scene.hf_kick, np.float64)
             L.oracle_set_hf_kick(self.h, C.c_int(len(hf)), _dp(hf))
@@ -201,14 +203,15 @@ class Oracle:
         n = len(src)
         first = np.zeros(n, np.uint64) if first is None else _arr(first, np.uint64)
         count = _arr(src.n_photons if count is None else count, np.uint64)
-        out = np.zeros(11)
+        out = np.zeros(12)
         u64p = C.POINTER(C.c_uint64)
         rc = self.L.oracle_count_ops(self.h, C.c_int(n), *self._src_args(src), first.ctypes.data_as(u64p),
                                      count.ctypes.data_as(u64p), C.c_int(int(early_reject)), _dp(out))
         if rc:
             raise RuntimeError("oracle_count_ops failed")
         keys = ("add", "mul", "div", "sqrt", "transcendental")
-        return {"pre": dict(zip(keys, out[0:5])), "optics": dict(zip(keys, out[5:10])), "photons": int(out[10])}
+        return {"pre": dict(zip(keys, out[0:5])), "optics": dict(zip(keys, out[5:10])), "photons": int(out[10]),
+                "survivors": float(out[11])}
 
     def trace_tangents(self, params, sources=None, first=None, count=None, n_threads=1):
         """Per-photon final positions and their derivatives with respect to each (surface, field) parameter."""
@@ -246,6 +249,16 @@ def zernike(j, rho, theta):
     out = np.zeros_like(rho)
     lib().oracle_zernike(C.c_int(j), C.c_int(len(rho)), _dp(rho), _dp(theta), _dp(out))
     return out
+
+
+def bleed(image, full_well):
+    """Saturation and bleeding of a finished image (in place on a copy); returns (image, removed)."""
+    img = np.ascontiguousarray(image, dtype=np.uint32).copy()
+    L = lib()
+    L.oracle_bleed.restype = C.c_uint64
+    removed = L.oracle_bleed(img.ctypes.data_as(C.POINTER(C.c_uint32)), C.c_int(img.shape[1]), C.c_int(img.shape[0]),
+                             C.c_uint32(int(full_well)))
+    return img, int(removed)
 
 
 def refract(d, N, n1, n2):

@@ -116,6 +116,7 @@ enum Slot {
     S_TIME = 4, S_SHAPE_A = 5, S_SHAPE_B = 6, S_CONV = 7,
     S_DIFF_A = 8, S_DIFF_B = 9, S_COAT0 = 10,   // coated surface k uses slot 10 + k (k < 6)
     S_HF_R = 16, S_HF_PSI = 17,                 // high-frequency kick: magnitude, direction
+    S_BACK = 18,                                // back-side reflection
     N_SLOTS = 20
 };
 
@@ -132,7 +133,7 @@ enum { SRC_POINT = 0, SRC_SERSIC = 1, SRC_GAUSS = 2 };
 enum : uint32_t {
     F_DETECTED = 1u,
     LOST_VIGNETTED = 1u, LOST_MISSED = 2u, LOST_NEWTON = 3u, LOST_TIR = 4u, LOST_COATING = 5u,
-    LOST_OFF_CHIP = 6u, LOST_NOT_CONVERTED = 7u,
+    LOST_OFF_CHIP = 6u, LOST_NOT_CONVERTED = 7u, LOST_DEAD_LAYER = 8u,
 };
 inline uint32_t lost_flag(uint32_t reason, int surface) { return (reason << 8) | ((uint32_t)(surface & 0xff) << 16); }
 
@@ -152,7 +153,8 @@ struct Layer { double z, vx, vy; std::vector<Scale> scales; };
 struct Scene {
     uint64_t seed = 1;
     double pr_in = 0, pr_out = 0, h_top = 1e8, lam_ref = 500.0, z_ent = 0;
-    int atm_on = 1, sensor_on = 1;
+    int atm_on = 1, sensor_on = 1, back_reflect = 0;
+    double dead_layer = 0.0;
     std::vector<Surf> surf;
     std::vector<Mat> mat;
     std::vector<Coat> coat;
@@ -618,7 +620,27 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
                 T deptht = Lt * (val(dz) < 0.0 ? -dz : dz);
                 double depth = val(deptht), L = val(Lt);
                 min_margin(out.margin_mm, depth - sc.t_si);
-                if (!(depth <= sc.t_si)) { out.flags = lost_flag(LOST_NOT_CONVERTED, (int)si); return; }
+                if (!(depth <= sc.t_si)) {
+                    // back-side reflection with the normal-incidence Fresnel probability of the Si/vacuum
+                    // interface; the photon converts on its way back towards the entrance
+                    bool back = false;
+                    if (sc.back_reflect) {
+                        T rf = (n_si - T(1.0)) / (n_si + T(1.0));
+                        double r_back = val(rf * rf);
+                        double u = uniform01(D->w[S_BACK]);
+                        if (std::fabs(u - r_back) < 1e-12) out.margin_mm = 0.0;
+                        if (u < r_back) {
+                            deptht = T(2.0 * sc.t_si) - deptht;
+                            depth = val(deptht);
+                            back = depth >= 0.0;
+                            min_margin(out.margin_mm, depth);
+                        }
+                    }
+                    if (!back) { out.flags = lost_flag(LOST_NOT_CONVERTED, (int)si); return; }
+                }
+                // charge converted in the field-free dead layer at the entrance is not collected
+                if (sc.dead_layer > 0.0) min_margin(out.margin_mm, depth - sc.dead_layer);
+                if (depth < sc.dead_layer) { out.flags = lost_flag(LOST_DEAD_LAYER, (int)si); return; }
                 fx = fx + T(L) * dl[0];
                 fy = fy + T(L) * dl[1];
                 xc = val(fx); yc = val(fy);
@@ -795,6 +817,42 @@ void oracle_get_cdf(void* p, int sed, double* out) {
     Scene* sc = (Scene*)p;
     for (int k = 0; k < sc->n_bins; ++k) out[k] = sc->cdf[sed][k];
 }
+void oracle_set_sensor_options(void* p, int back_reflect, double dead_layer) {
+    Scene* sc = (Scene*)p;
+    sc->back_reflect = back_reflect;
+    sc->dead_layer = dead_layer;
+}
+
+// Saturation and bleeding (Sec. 2.5) on a finished image: in each half of every row, pixels above the full
+// well, visited left to right, give their excess electron by electron to the closest pixel of the half-row
+// that is below the full well (the left one first at equal distance); what finds no room is removed.
+uint64_t oracle_bleed(uint32_t* img, int nx, int ny, uint32_t w) {
+    uint64_t removed = 0;
+    for (int y = 0; y < ny; ++y) {
+        for (int half = 0; half < 2; ++half) {
+            const int lo = half ? nx / 2 : 0, hi = half ? nx : nx / 2;    // [lo, hi)
+            uint32_t* row = img + (size_t)y * nx;
+            for (int x = lo; x < hi; ++x) {
+                if (row[x] <= w) continue;
+                uint64_t excess = row[x] - w;
+                row[x] = w;
+                for (int d = 1; excess > 0; ++d) {
+                    const bool has_l = x - d >= lo, has_r = x + d < hi;
+                    if (!has_l && !has_r) { removed += excess; excess = 0; break; }
+                    // electrons alternate left, right, left, ... while both sides have room
+                    while (excess > 0) {
+                        bool moved = false;
+                        if (has_l && row[x - d] < w) { row[x - d] += 1; --excess; moved = true; }
+                        if (excess > 0 && has_r && row[x + d] < w) { row[x + d] += 1; --excess; moved = true; }
+                        if (!moved) break;
+                    }
+                }
+            }
+        }
+    }
+    return removed;
+}
+
 void oracle_set_hf_kick(void* p, int K, const double* q) {
     Scene* sc = (Scene*)p;
     sc->hf.assign(q, q + K);
@@ -1011,7 +1069,7 @@ int oracle_trace_tangents(void* p, int n_src, const int* kind, const int* sed, c
 
 // Algorithmic operation counts of the photon path (per photon, averaged over the given photons):
 // out[0..4] = add/sub, mul, div, sqrt, transcendental of sampling + atmosphere; out[5..9] the same for the
-// optics and sensor; out[10] = photons counted.  Newton stops at the paper's 0.01 um step here; the
+// optics and sensor; out[10] = photons counted; out[11] = fraction not removed by the early test.  Newton stops at the paper's 0.01 um step here; the
 // central-difference screen gradients are table reads (precomputed, Sec. 3.2) and are not counted.
 int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const int* table, const double* xi,
                      const double* eta, const double* z, const double* t0, const double* te, const double* a,
@@ -1019,7 +1077,7 @@ int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const 
                      double* out) {
     Scene* sc = (Scene*)p;
     OpCount pre, opt;
-    double n = 0;
+    double n = 0, survivors = 0;
     std::vector<SurfT<Cnt>> ST;
     build_surfaces(*sc, ST);
     for (int s = 0; s < n_src; ++s) {
@@ -1045,6 +1103,7 @@ int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const 
                 }
                 if (rejected) continue;
             }
+            survivors += 1;
             g_ops = OpCount();
             Cnt X[3], Dir[3], lam, tt;
             sample_and_atmosphere_t<Cnt>(*sc, src, D, X, Dir, lam, tt);
@@ -1062,6 +1121,7 @@ int oracle_count_ops(void* p, int n_src, const int* kind, const int* sed, const 
     double v[10] = {pre.add, pre.mul, pre.div, pre.sqrt, pre.special, opt.add, opt.mul, opt.div, opt.sqrt, opt.special};
     for (int i = 0; i < 10; ++i) out[i] = v[i] / n;
     out[10] = n;
+    out[11] = survivors / n;
     return 0;
 }
 

@@ -241,7 +241,13 @@ __device__ void surface_adjoint(const TraceParams& P, const GradParams& G, int s
 
 __global__ void __launch_bounds__(128) grad_kernel(const __grid_constant__ TraceParams P,
                                                     const __grid_constant__ GradParams G) {
+    // As in the trace kernel, photons the dynamic transmission test removes are dropped first and the
+    // survivors are queued per warp, so the recomputed forward pass and the reverse sweep run on full warps.
+    __shared__ uint32_t queue_mem[4][64];
     const int lane = threadIdx.x & 31;
+    uint32_t* queue = queue_mem[threadIdx.x >> 5];
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const bool early = (P.flags & PHOSIM_EARLY_REJECT) != 0;
     double gacc[kMaxGradParams];
     for (;;) {
         unsigned long long t = 0;
@@ -255,18 +261,45 @@ __global__ void __launch_bounds__(128) grad_kernel(const __grid_constant__ Trace
         const double* sd = G.seeds + (size_t)src * 8;
         const double Ax = sd[0], Ay = sd[1], Bxx = sd[2], Bxy = sd[3], Byy = sd[4], xm = sd[5], ym = sd[6];
         for (int p = 0; p < G.n_params; ++p) gacc[p] = 0.0;
-        for (uint32_t k = lane; k < count; k += 32) {
-            ForwardRecord fr;
-            PhotonOut R;
-            trace_photon<false, true>(P, s, src, s.first + off + k, R, &fr);
-            if (!(R.flags & PHOSIM_F_DETECTED)) continue;
-            const double dx = R.x - xm, dy = R.y - ym;
-            const double fb[2] = {Ax + Bxx * dx + Bxy * dy, Ay + Byy * dy + Bxy * dx};
-            double Xb[3] = {0.0, 0.0, 0.0}, Db[3] = {0.0, 0.0, 0.0};
-            const int last = P.n_surf - 1;
-            surface_adjoint(P, G, last, fr.XD[last], R.lam, true, fb, fr.L, Xb, Db, gacc);
-            for (int si = last - 1; si >= 0; --si)
-                surface_adjoint(P, G, si, fr.XD[si], R.lam, false, fb, 0.0, Xb, Db, gacc);
+        int queued = 0;
+        uint32_t base = 0;
+        for (;;) {
+            if (base < count) {
+                const uint32_t k = base + lane;
+                bool go_on = k < count;
+                if (early && go_on) {
+                    double lam;
+                    go_on = early_reject_surface<false>(P, s, src, s.first + off + k, lam) < 0;
+                }
+                const unsigned gmask = __ballot_sync(0xffffffffu, go_on);
+                if (go_on) queue[queued + __popc(gmask & lanes_below)] = k;
+                queued += __popc(gmask);
+                base += 32;
+                __syncwarp();
+            }
+            const bool drained = base >= count;
+            if (queued >= 32 || (drained && queued > 0)) {
+                const int take = queued < 32 ? queued : 32;
+                queued -= take;
+                const bool v = lane < take;
+                const uint32_t kk = v ? queue[queued + lane] : 0u;
+                __syncwarp();
+                if (v) {
+                    ForwardRecord fr;
+                    PhotonOut R;
+                    trace_photon<false, true>(P, s, src, s.first + off + kk, R, &fr);
+                    if (R.flags & PHOSIM_F_DETECTED) {
+                        const double dx = R.x - xm, dy = R.y - ym;
+                        const double fb[2] = {Ax + Bxx * dx + Bxy * dy, Ay + Byy * dy + Bxy * dx};
+                        double Xb[3] = {0.0, 0.0, 0.0}, Db[3] = {0.0, 0.0, 0.0};
+                        const int last = P.n_surf - 1;
+                        surface_adjoint(P, G, last, fr.XD[last], R.lam, true, fb, fr.L, Xb, Db, gacc);
+                        for (int si = last - 1; si >= 0; --si)
+                            surface_adjoint(P, G, si, fr.XD[si], R.lam, false, fb, 0.0, Xb, Db, gacc);
+                    }
+                }
+            }
+            if (drained && queued == 0) break;
         }
         double* out = G.grad + (size_t)src * G.n_params;
         for (int p = 0; p < G.n_params; ++p) {

@@ -177,18 +177,26 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
 }
 
 // ----------------------------------------------------------------------------------------- device kernels
-// central-difference gradient of a periodic phase screen, rad per mm (Sec. 2.3.2)
-__global__ void gradient_screen_kernel(const double* __restrict__ ph, int n, double two_pix, double2* g64, float2* g32) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= n) return;
+// central-difference gradient of a periodic phase screen, rad per mm (Sec. 2.3.2), stored per node as the
+// 2 x 2 block of gradients the bilinear interpolation reads (see DScale)
+__device__ __forceinline__ double2 central_gradient(const double* __restrict__ ph, int n, double two_pix, int i, int j) {
     const int ip = i + 1 == n ? 0 : i + 1, im = i == 0 ? n - 1 : i - 1;
     const int jp = j + 1 == n ? 0 : j + 1, jm = j == 0 ? n - 1 : j - 1;
     const size_t r = (size_t)j * n;
-    const double gx = (ph[r + ip] - ph[r + im]) / two_pix;
-    const double gy = (ph[(size_t)jp * n + i] - ph[(size_t)jm * n + i]) / two_pix;
-    g64[r + i] = make_double2(gx, gy);
-    g32[r + i] = make_float2((float)gx, (float)gy);
+    return make_double2((ph[r + ip] - ph[r + im]) / two_pix, (ph[(size_t)jp * n + i] - ph[(size_t)jm * n + i]) / two_pix);
+}
+
+__global__ void gradient_screen_kernel(const double* __restrict__ ph, int n, double two_pix, double2* g64, float4* g32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= n) return;
+    const int i1 = i + 1 == n ? 0 : i + 1, j1 = j + 1 == n ? 0 : j + 1;
+    const double2 a = central_gradient(ph, n, two_pix, i, j), b = central_gradient(ph, n, two_pix, i1, j);
+    const double2 c = central_gradient(ph, n, two_pix, i, j1), d = central_gradient(ph, n, two_pix, i1, j1);
+    const size_t node = (size_t)j * n + i;
+    g64[4 * node] = a; g64[4 * node + 1] = b; g64[4 * node + 2] = c; g64[4 * node + 3] = d;
+    g32[2 * node] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    g32[2 * node + 1] = make_float4((float)c.x, (float)c.y, (float)d.x, (float)d.y);
 }
 
 // Photon-number cumulative table of each SED (flux x wavelength x bin width, summed in bin order with
@@ -303,6 +311,7 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
     if (d->n_ell < 2 || d->n_sigma < 2 || !d->ell || !d->sigma) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->pupil_r_out > d->pupil_r_in) || d->pupil_r_in < 0.0) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->h_top > d->z_entrance) || !is_finite(d->h_top) || !is_finite(d->z_entrance)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!(d->dead_layer >= 0.0) || !(d->dead_layer < d->t_si)) return PHOSIM_ERR_INVALID_ARGUMENT;
     for (int i = 0; i < d->n_ell; ++i) if (!(d->ell[i] > 0.0) || !is_finite(d->ell[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
     for (int i = 0; i < d->n_sigma; ++i) if (!(d->sigma[i] >= 0.0) || !is_finite(d->sigma[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
     phosim_scene* sc = new (std::nothrow) phosim_scene();
@@ -326,6 +335,7 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
     P.ell_lam0 = d->ell_lam0; P.inv_ell_dlam = 1.0 / d->ell_dlam;
     P.n_ell = d->n_ell; P.n_sig = d->n_sigma;
     P.sig_scale = (d->n_sigma - 1) / d->t_si;
+    P.dead_layer = d->dead_layer;
     sc->precision = d->precision;
     std::vector<float> f(d->ell, d->ell + d->n_ell), g(d->sigma, d->sigma + d->n_sigma);
     double* pd;
@@ -487,11 +497,11 @@ phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, 
             double* ph = nullptr;
             void *g64 = nullptr, *g32 = nullptr;
             cudaError_t e = cudaMalloc(&ph, nn * sizeof(double));
-            if (e == cudaSuccess) e = cudaMalloc(&g64, nn * sizeof(double2));
-            if (e == cudaSuccess) { mem.push_back(g64); e = cudaMalloc(&g32, nn * sizeof(float2)); }
+            if (e == cudaSuccess) e = cudaMalloc(&g64, 4 * nn * sizeof(double2));
+            if (e == cudaSuccess) { mem.push_back(g64); e = cudaMalloc(&g32, 2 * nn * sizeof(float4)); }
             if (e == cudaSuccess) { mem.push_back(g32); e = cudaMemcpy(ph, S.phase, nn * sizeof(double), cudaMemcpyHostToDevice); }
             if (e == cudaSuccess) {
-                gradient_screen_kernel<<<dim3((S.n + 255) / 256, S.n), 256>>>(ph, S.n, 2.0 * S.pixel, (double2*)g64, (float2*)g32);
+                gradient_screen_kernel<<<dim3((S.n + 255) / 256, S.n), 256>>>(ph, S.n, 2.0 * S.pixel, (double2*)g64, (float4*)g32);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -504,7 +514,7 @@ phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, 
             D.s[q].n = S.n;
             D.s[q].inv_pix = 1.0 / S.pixel;
             D.s[q].g64 = (const double2*)g64;
-            D.s[q].g32 = (const float2*)g32;
+            D.s[q].g32 = (const float4*)g32;
         }
     }
     P.n_layers = n_layers;
@@ -831,10 +841,14 @@ phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src,
         sc->cap_stage = img_bytes;
     }
     CU(cudaMemsetAsync(sc->d_mom_scratch, 0, mom_bytes, st));
+    // FP64 and the dynamic transmission test (it leaves the detected photons unchanged) for both passes
     const int saved_precision = sc->precision;
+    const uint32_t saved_flags = sc->base.flags;
     sc->precision = PHOSIM_PLAIN_FP64;
+    sc->base.flags = (saved_flags | PHOSIM_EARLY_REJECT) & ~PHOSIM_GRAPH;
     phosim_status rs = phosim_trace(sc, src, n_src, n_photons, nullptr, sc->d_stage, nullptr, sc->d_mom_scratch, stream);
     sc->precision = saved_precision;
+    sc->base.flags = saved_flags;
     if (rs != PHOSIM_OK) return rs;
     std::vector<double> mom((size_t)n_src * PHOSIM_MOMENT_WORDS);
     CU(cudaMemcpyAsync(mom.data(), sc->d_mom_scratch, mom_bytes, cudaMemcpyDeviceToHost, st));
@@ -875,6 +889,7 @@ phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src,
     G.grad = d_grad;
     // the trace left its source list (with chief-ray references) and tile prefix in the scene's scratch
     TraceParams P = sc->base;
+    P.flags |= PHOSIM_EARLY_REJECT;
     P.sources = sc->d_src;
     P.tile_prefix = sc->d_prefix;
     P.n_src = n_src;

@@ -44,11 +44,14 @@ struct DCoating {
     const double* Tmax;                       // nl: the largest transmission over angles at each wavelength
 };
 
+// A screen scale's central-difference gradient (rad / mm), stored per node (i, j) as the 2 x 2 block of
+// nodes the bilinear interpolation needs, (i, j), (i+1, j), (i, j+1), (i+1, j+1) (periodic): one lookup is
+// one aligned 32-byte (FP32) or 64-byte (FP64) read instead of two rows of scattered 8- or 16-byte taps.
 struct DScale {
     int n, pad;
     double inv_pix;
-    const double2* g64;                       // central-difference gradient (rad / mm), n x n
-    const float2* g32;
+    const double2* g64;                       // 4 double2 per node, n x n nodes
+    const float4* g32;                        // 2 float4 per node: (g00, g10), (g01, g11)
 };
 
 struct DLayer {
@@ -65,7 +68,7 @@ struct DSource {
 };
 
 // counters: [0] traced, [1] detected, [1 + r] dropped for reason r
-constexpr int kNumCounters = 9;
+constexpr int kNumCounters = 10;
 
 struct TraceParams {
     // scene
@@ -84,7 +87,7 @@ struct TraceParams {
     DLayer layer[PHOSIM_MAX_LAYERS];
     // sensor / detector
     int nx, ny, n_ell, n_sig;
-    double pixel, inv_pixel, xlo, ylo, t_si, ell_lam0, inv_ell_dlam, sig_scale;
+    double pixel, inv_pixel, xlo, ylo, t_si, ell_lam0, inv_ell_dlam, sig_scale, dead_layer;
     const double* ell;
     const float* ell32;
     const double* sig;
@@ -132,7 +135,7 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 //   block 1: time, shape a, shape b, conversion
 //   block 2: diffusion a, diffusion b, coated surface 0, coated surface 1
 //   block 3: coated surfaces 2..5
-//   block 4: high-frequency kick magnitude, direction
+//   block 4: high-frequency kick magnitude, direction, back-side reflection
 __device__ __forceinline__ double u64of(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
 __device__ __forceinline__ float u32of(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
 

@@ -47,19 +47,17 @@ __device__ __forceinline__ void screen_gradient(const DScale& S, double sx, doub
     const double flx = floor(fx), fly = floor(fy);
     const int n = S.n;
     const int i0 = wrap_index((long long)flx, n), j0 = wrap_index((long long)fly, n);
-    const int i1 = (i0 + 1 == n) ? 0 : i0 + 1, j1 = (j0 + 1 == n) ? 0 : j0 + 1;
-    const size_t r0 = (size_t)j0 * n, r1 = (size_t)j1 * n;
+    const size_t node = (size_t)j0 * n + i0;
     if constexpr (MIXED) {
         const float tx = (float)(fx - flx), ty = (float)(fy - fly);
-        const float2 a = __ldg(S.g32 + r0 + i0), b = __ldg(S.g32 + r0 + i1);
-        const float2 c = __ldg(S.g32 + r1 + i0), d = __ldg(S.g32 + r1 + i1);
+        const float4 A = __ldg(S.g32 + 2 * node), B = __ldg(S.g32 + 2 * node + 1);
         const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
-        gx += (double)(w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x);
-        gy += (double)(w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y);
+        gx += (double)(w00 * A.x + w10 * A.z + w01 * B.x + w11 * B.z);
+        gy += (double)(w00 * A.y + w10 * A.w + w01 * B.y + w11 * B.w);
     } else {
         const double tx = fx - flx, ty = fy - fly;
-        const double2 a = __ldg(S.g64 + r0 + i0), b = __ldg(S.g64 + r0 + i1);
-        const double2 c = __ldg(S.g64 + r1 + i0), d = __ldg(S.g64 + r1 + i1);
+        const double2* q = S.g64 + 4 * node;
+        const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
         const double w00 = (1.0 - tx) * (1.0 - ty), w10 = tx * (1.0 - ty), w01 = (1.0 - tx) * ty, w11 = tx * ty;
         gx += w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x;
         gy += w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y;
@@ -92,7 +90,7 @@ struct ForwardRecord {
 
 template <bool MIXED, bool FULL, bool RECORD = false>
 __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double D[3], double lam, uint4 w1, uint4 w2,
-                                       uint4 w3, PhotonOut& R, ForwardRecord* fr = nullptr) {
+                                       uint4 w3, uint4 w4, PhotonOut& R, ForwardRecord* fr = nullptr) {
     double n_cur = 1.0;
     int glass_mat = -1;
     double glass_n = 1.0, glass_inv = 1.0;
@@ -122,21 +120,35 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
             R.xc = fx; R.yc = fy;
             if (FULL && (P.flags & PHOSIM_SENSOR)) {
                 // refraction into the silicon, exponential conversion length (Sec. 2.4.2)
-                double L, sigma, gxd, gyd;
+                double L, sigma, gxd, gyd, r_back;
                 if constexpr (MIXED) {
                     const float n_si = silicon_index_f((float)lam);
                     if (!refract(dl, Nx, Ny, Nz, n_cur / (double)n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
                     const float ell = lerp_table_f(P.ell32, P.n_ell, (float)((lam - P.ell_lam0) * P.inv_ell_dlam));
                     const float Lf = ell * -logf(u32of(w1.w));
                     L = (double)Lf;
+                    const float rf = (n_si - 1.f) / (n_si + 1.f);
+                    r_back = (double)(rf * rf);
                 } else {
                     const double n_si = silicon_index(lam);
                     if (!refract(dl, Nx, Ny, Nz, n_cur / n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
                     const double ell = lerp_table(P.ell, P.n_ell, (lam - P.ell_lam0) * P.inv_ell_dlam);
                     L = ell * -log(u64of(w1.w));
+                    const double rf = (n_si - 1.0) / (n_si + 1.0);
+                    r_back = rf * rf;
                 }
-                const double depth = L * fabs(dl[2]);
-                if (!(depth <= P.t_si)) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
+                double depth = L * fabs(dl[2]);
+                if (!(depth <= P.t_si)) {
+                    // back-side reflection: the photon turns round at the back and converts on its way back
+                    bool back = false;
+                    if ((P.flags & PHOSIM_BACK_REFLECT) && u64of(w4.z) < r_back) {
+                        depth = 2.0 * P.t_si - depth;
+                        back = depth >= 0.0;
+                    }
+                    if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
+                }
+                // field-free dead layer at the entrance: the charge is not collected
+                if (depth < P.dead_layer) { R.flags = lost(PHOSIM_LOST_DEAD_LAYER, si); return; }
                 fx = fma(L, dl[0], fx);
                 fy = fma(L, dl[1], fy);
                 R.xc = fx; R.yc = fy;
@@ -332,6 +344,8 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         y = fma(-ny, l, y);
         z = P.h_top;
     }
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
     // frozen-flow layers top to bottom: propagate, refractive kick from the screen gradient (Sec. 2.3)
     if (P.flags & PHOSIM_ATMOSPHERE) {
         double kick;
@@ -367,7 +381,6 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         // second kick (Sec. 2.3.2): a draw from the long-exposure PSF of the screens above kappa_crit,
         // scaled like the refractive kick by (lambda / lambda_ref)^(-1/5)
         if (P.hf_K > 0) {
-            const uint4 w4 = philox(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
             const double scale = kick / P.kick0;
             if constexpr (MIXED) {
                 const float ang = lerp_table_f(P.hf32, P.hf_K, u32of(w4.x) * (float)P.hf_K - 0.5f) * (float)scale;
@@ -394,7 +407,7 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         z = P.z_ent;
     }
     double X[3] = {x, y, z}, D[3] = {nx, ny, nz};
-    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, R, fr);
+    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, w4, R, fr);
 }
 
 

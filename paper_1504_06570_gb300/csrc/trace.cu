@@ -65,7 +65,7 @@ __device__ __forceinline__ void consume(const TraceParams& P, const PhotonOut& R
     if (lane == 0) cnt[1] += __popc(dmask);
     const uint32_t reason = valid ? ((R.flags >> 8) & 0xffu) : 0u;
 #pragma unroll
-    for (int q = 1; q <= 7; ++q) {
+    for (int q = 1; q <= 8; ++q) {
         const unsigned b = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
         if (lane == 0) cnt[1 + q] += __popc(b);
     }
@@ -173,7 +173,7 @@ __global__ void chief_ray_kernel(const __grid_constant__ TraceParams P, DSource*
     PhotonOut R;
     R.flags = 0; R.pix = -1; R.x = R.y = 0.0;
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-    optics<false, false>(P, X, D, P.lam_ref, zero, zero, zero, R);
+    optics<false, false>(P, X, D, P.lam_ref, zero, zero, zero, zero, R);
     const bool ok = (R.flags & PHOSIM_F_DETECTED) != 0;
     S.ref_x = ok ? R.x : 0.0;
     S.ref_y = ok ? R.y : 0.0;

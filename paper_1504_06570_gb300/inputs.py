@@ -84,6 +84,7 @@ class Detector:
     ell_dlam: float = 1.0
     ell: np.ndarray = None
     sigma: np.ndarray = None     # diffusion sigma (mm) at depths uniformly spaced over [0, t_si]
+    dead_layer: float = 0.0      # field-free layer at the entrance (mm)
 
 
 @dataclass
@@ -143,6 +144,7 @@ class Scene:
     sensor: bool = True          # False: record the hit on the detector surface, no silicon
     z_entrance: float = None     # plane (mm) where the raytrace starts, below every layer, above every optic
     hf_kick: np.ndarray = None   # quantiles (rad at lambda_ref) of the high-frequency kick, or None
+    back_reflect: bool = False   # back-side reflection of photons that cross the silicon
 
     def __post_init__(self):
         if self.z_entrance is None:
@@ -606,3 +608,32 @@ def high_frequency_kick_table(r0_m=0.15, L0_m=20.0, lam_ref_nm=500.0, K=4096, cr
     u = (np.arange(K) + 0.5) / K
     q = np.where(u < core, 0.0, np.interp((u - core) / (1.0 - core), cdf_halo, th))
     return q, sigma2
+
+
+# ----------------------------------------------------------------------------------------------------------
+# charge diffusion from the silicon field model (Sec. 2.5)
+# ----------------------------------------------------------------------------------------------------------
+
+def diffusion_sigma_table(t_si_mm=0.1, v_over=20.0, T_K=173.0, n_bulk=1e12, n_b=0.0, s_b_mm=0.005, n_f=0.0,
+                          s_f_mm=0.005, n=65, n_fine=4001):
+    """Lateral diffusion sigma (mm) of charge converted at depths k t_si / (n - 1) below the entrance, from
+    the field model of Sec. 2.5.  With z measured from the collecting (front) surface, the doping is
+    n_d(z) = n_bulk + n_b exp(-(t - z) / s_b) + n_f exp(-z / s_f) (cm^-3) and the field magnitude
+    E(z) = V / t + q / (eps0 eps_Si) int_z^t n_d dz' (V/cm), largest at the front.  Diffusion over the drift
+    adds D dt = (mu k T / q) dz / (mu E): the mobility cancels (Einstein relation) and
+    sigma^2(z_c) = 2 (k T / q) int_0^z_c dz / E(z) for charge converted at z_c."""
+    q_over_eps = 1.602176634e-19 / (8.8541878128e-14 * 11.7)          # V cm
+    kT_q = 8.617333262e-5 * T_K                                       # V
+    t = t_si_mm * 0.1                                                  # cm
+    z = np.linspace(0.0, t, n_fine)
+    nd = n_bulk + n_b * np.exp(-(t - z) / (s_b_mm * 0.1)) + n_f * np.exp(-z / (s_f_mm * 0.1))
+    # int_z^t n_d dz' by the trapezoid rule from the back
+    seg = 0.5 * (nd[1:] + nd[:-1]) * np.diff(z)
+    tail = np.r_[np.cumsum(seg[::-1])[::-1], 0.0]
+    E = v_over / t + q_over_eps * tail
+    inv = 1.0 / E
+    cum = np.r_[0.0, np.cumsum(0.5 * (inv[1:] + inv[:-1]) * np.diff(z))]   # int_0^z dz / E
+    depth = np.linspace(0.0, t, n)                                     # below the entrance (the back)
+    zc = t - depth
+    sig_cm = np.sqrt(2.0 * kT_q * np.interp(zc, z, cum))
+    return sig_cm * 10.0                                               # mm

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libphosim.so")
 
 MAX_SURFACES, MAX_LAYERS, MAX_SCALES, MAX_ZERNIKE = 16, 8, 2, 28
 PLAIN_FP64, MIXED = 0, 1
-ATMOSPHERE, SENSOR, EARLY_REJECT, GRAPH = 1, 2, 4, 8
+ATMOSPHERE, SENSOR, EARLY_REJECT, GRAPH, BACK_REFLECT = 1, 2, 4, 8, 16
 MOMENT_WORDS = 8
 F_DETECTED = 1
 
@@ -38,7 +38,8 @@ class SceneDesc(C.Structure):
                 ("z_entrance", C.c_double), ("lambda_ref", C.c_double), ("nx", C.c_int32), ("ny", C.c_int32),
                 ("pixel", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("t_si", C.c_double),
                 ("ell_lam0", C.c_double), ("ell_dlam", C.c_double), ("n_ell", C.c_int32),
-                ("ell", C.POINTER(C.c_double)), ("n_sigma", C.c_int32), ("sigma", C.POINTER(C.c_double))]
+                ("ell", C.POINTER(C.c_double)), ("n_sigma", C.c_int32), ("sigma", C.POINTER(C.c_double)),
+                ("dead_layer", C.c_double)]
 
 
 class Surface(C.Structure):
@@ -166,12 +167,14 @@ class Scene:
         self._sig = np.ascontiguousarray(d.sigma, np.float64)
         desc = SceneDesc(seed=scene.seed, precision=precision,
                          flags=(ATMOSPHERE if scene.atmosphere else 0) | (SENSOR if scene.sensor else 0)
-                         | (EARLY_REJECT if early_reject else 0) | (GRAPH if graph else 0),
+                         | (EARLY_REJECT if early_reject else 0) | (GRAPH if graph else 0)
+                         | (BACK_REFLECT if getattr(scene, "back_reflect", False) else 0),
                          pupil_r_in=scene.pupil_r_in, pupil_r_out=scene.pupil_r_out, h_top=scene.h_top,
                          z_entrance=scene.z_entrance, lambda_ref=scene.lambda_ref, nx=d.nx, ny=d.ny, pixel=d.pixel,
                          x0=d.x0, y0=d.y0, t_si=d.t_si, ell_lam0=d.ell_lam0, ell_dlam=d.ell_dlam,
                          n_ell=len(self._ell), ell=self._ell.ctypes.data_as(C.POINTER(C.c_double)),
-                         n_sigma=len(self._sig), sigma=self._sig.ctypes.data_as(C.POINTER(C.c_double)))
+                         n_sigma=len(self._sig), sigma=self._sig.ctypes.data_as(C.POINTER(C.c_double)),
+                         dead_layer=float(getattr(d, "dead_layer", 0.0)))
         h = C.c_void_p()
         _check("phosim_create_scene", L.phosim_create_scene(C.byref(desc), C.byref(h)))
         self.h = h
@@ -295,8 +298,8 @@ class Scene:
         return t.value, k.value
 
     def counters(self):
-        out = (C.c_uint64 * 9)()
-        _check("phosim_get_counters", self.L.phosim_get_counters(self.h, out, 9))
+        out = (C.c_uint64 * 10)()
+        _check("phosim_get_counters", self.L.phosim_get_counters(self.h, out, 10))
         return np.array(out[:], np.uint64)
 
     def close(self):
@@ -309,6 +312,19 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+def bleed(image, full_well, stream=None):
+    """phosim_bleed on a device int32 image tensor (in place); returns the number of removed electrons."""
+    import torch
+    removed = torch.zeros(1, dtype=torch.int64, device=image.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    L = lib()
+    L.phosim_bleed.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_uint32, C.c_void_p, C.c_void_p]
+    _check("phosim_bleed", L.phosim_bleed(C.c_void_p(image.data_ptr()), image.shape[1], image.shape[0],
+                                          C.c_uint32(int(full_well)), C.c_void_p(removed.data_ptr()), C.c_void_p(stream)))
+    return removed
 
 
 def records_to_numpy(rec_tensor):

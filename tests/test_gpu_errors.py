@@ -1,0 +1,84 @@
+"""Error paths through the C ABI on a device: malformed descriptors return error codes and leave the scene
+usable; per-photon failures (a ray outside a surface's domain) are flags and counters, never faults."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_1504_06570_gb300 import inputs as I
+from paper_1504_06570_gb300 import phosim as P
+from tests import gpu_helpers as G
+from tests.helpers import bare_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+def test_load_errors_leave_the_scene_usable():
+    sc = I.paraboloid_scene(n_photons=2000, screen_n=128)
+    s = P.Scene(sc)
+    L = s.L
+    # detector not last
+    bad = [I.Surface(kind=I.DETECTOR, z=10000.0, material=1), I.Surface(kind=I.MIRROR, R=20000.0, kappa=-1.0)]
+    with pytest.raises(P.PhosimError) as e:
+        s.load_optics(bad, sc.materials, [])
+    assert e.value.code == -1
+    # too many surfaces
+    with pytest.raises(P.PhosimError) as e:
+        s.load_optics([I.Surface(kind=I.REFRACT, z=float(i)) for i in range(16)] + [I.Surface(kind=I.DETECTOR)],
+                      sc.materials, [])
+    assert e.value.code == -6
+    # layers not top to bottom
+    ph = np.zeros((8, 8))
+    with pytest.raises(P.PhosimError) as e:
+        s.load_screens([I.Layer(z=1e6, scales=[I.ScreenScale(10.0, ph)]), I.Layer(z=2e6, scales=[I.ScreenScale(10.0, ph)])])
+    assert e.value.code == -1
+    # negative flux
+    flux = -np.ones((1, 10))
+    assert L.phosim_load_seds(s.h, flux.ctypes.data_as(C.POINTER(C.c_double)), 1, 10, 400.0, 1.0) == -1
+    # gradient parameter field out of range
+    with pytest.raises(P.PhosimError) as e:
+        s.grad(np.zeros((1, 5)), [(0, 7)])
+    assert e.value.code == -1
+    # the scene still traces exactly as a fresh one
+    ref = G.run_gpu(sc, P.PLAIN_FP64, records=False)
+    img = torch.zeros((256, 256), dtype=torch.int32, device="cuda")
+    s.trace(img)
+    torch.cuda.synchronize()
+    assert np.array_equal(img.cpu().numpy().view(np.uint32), ref["image"])
+    s.close()
+
+
+def test_trace_before_loading_is_not_ready():
+    sc = I.paraboloid_scene(n_photons=10, screen_n=64)
+    d = sc.detector
+    ell, sig = np.ascontiguousarray(d.ell), np.ascontiguousarray(d.sigma)
+    desc = P.SceneDesc(seed=1, precision=0, flags=0, pupil_r_in=0.0, pupil_r_out=500.0, h_top=1e8, z_entrance=11000.0,
+                       lambda_ref=500.0, nx=16, ny=16, pixel=0.01, t_si=0.1, ell_lam0=d.ell_lam0, ell_dlam=1.0,
+                       n_ell=len(ell), ell=ell.ctypes.data_as(C.POINTER(C.c_double)), n_sigma=2,
+                       sigma=sig.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    L = P.lib()
+    assert L.phosim_create_scene(C.byref(desc), C.byref(h)) == 0
+    src = P.sources_struct(sc.sources)
+    cnt = np.array([10], np.uint64)
+    img = torch.zeros((16, 16), dtype=torch.int32, device="cuda")
+    rc = L.phosim_trace(h, src, 1, cnt.ctypes.data_as(C.POINTER(C.c_uint64)), None, C.c_void_p(img.data_ptr()),
+                        None, None, None)
+    assert rc == -5
+    L.phosim_destroy_scene(h)
+
+
+def test_rays_outside_a_surface_domain_are_flagged(oracle_mod):
+    """A sphere of radius 600 mm lit over 700 mm: rays beyond r = R have no intersection with its vertex
+    branch and are dropped as MISSED, identically in the oracle and the kernel."""
+    surfaces = [I.Surface(kind=I.MIRROR, R=600.0, kappa=0.0, z=0.0, r_out=700.0),
+                I.Surface(kind=I.DETECTOR, z=300.0, material=1)]
+    sc = bare_scene(surfaces, n_photons=20000, pupil=(0.0, 700.0), nx=2048, pixel=0.5)
+    gpu = G.run_gpu(sc, P.PLAIN_FP64)
+    ora = G.oracle_trace(oracle_mod, sc)
+    reason_g = (gpu["rec"]["flags"] >> 8) & 0xFF
+    reason_o = (ora["flags"] >> 8) & 0xFF
+    assert (reason_o == 2).sum() > 1000
+    assert np.array_equal(reason_g == 2, reason_o == 2)
+    assert gpu["counters"][1 + 2] == (reason_g == 2).sum()

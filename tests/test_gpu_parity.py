@@ -180,6 +180,42 @@ def test_graph_replay_matches_direct_launches():
     gr.close()
 
 
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED])
+def test_sensor_extensions(oracle_mod, precision):
+    """Dead layer, back-side reflection and a depth-dependent diffusion sigma from the field model."""
+    counts = [6000, 3000]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=12))
+    sc.detector.dead_layer = 0.0003
+    sc.detector.t_si = 0.01
+    sc.detector.sigma = I.diffusion_sigma_table(t_si_mm=0.01, v_over=5.0, n_bulk=5e11)
+    sc.back_reflect = True
+    gpu = G.run_gpu(sc, precision, early_reject=True)
+    ora = G.oracle_trace(oracle_mod, sc)
+    reasons = (ora["flags"] >> 8) & 0xFF
+    assert (reasons == 8).sum() > 50
+    if precision == P.PLAIN_FP64:
+        det_g, det_o = (gpu["rec"]["flags"] & 1) == 1, (ora["flags"] & 1) == 1
+        assert np.all((det_g == det_o) | G.boundary_mask(ora))
+        both = det_g & det_o
+        err = np.maximum(np.abs(gpu["rec"]["x"][both] - ora["x"][both]), np.abs(gpu["rec"]["y"][both] - ora["y"][both]))
+        assert err.max() / sc.detector.pixel < 1e-6
+    G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6 if precision == P.PLAIN_FP64 else 3e-3)
+
+
+def test_bleeding_matches_oracle(oracle_mod):
+    rng = np.random.default_rng(4)
+    img = rng.integers(0, 300, size=(64, 96)).astype(np.uint32)
+    for _ in range(12):
+        img[rng.integers(0, 64), rng.integers(0, 96)] += np.uint32(rng.integers(1000, 200000))
+    img[10, :] = 700
+    t = torch.as_tensor(img.view(np.int32).copy(), device="cuda")
+    removed = P.bleed(t, 1000)
+    torch.cuda.synchronize()
+    ref, ref_removed = oracle_mod.bleed(img, 1000)
+    assert np.array_equal(t.cpu().numpy().view(np.uint32), ref)
+    assert int(removed.item()) == ref_removed
+
+
 def test_invalid_sources_are_rejected():
     sc = I.paraboloid_scene(n_photons=10)
     s = P.Scene(sc)

@@ -521,3 +521,65 @@ def test_second_kick_distribution(oracle_mod):
     k = a1 > 1e-12
     assert stats.kstest((psi1[k] + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-3
     np.testing.assert_allclose(a1[k] / a2[k], (l1[k] / l2[k]) ** -0.2, rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------------------------- Sec. 2.4.2 / 2.5 sensor extensions
+def _mono_scene(lam, n, **kw):
+    return mirror_scene(20000.0, -1.0, 10000.0, sensor=True, lam_lo=lam, lam_hi=lam + 1.0, n_photons=n, **kw)
+
+
+def test_dead_layer_loss_fraction(oracle_mod):
+    """Sec. 2.4.2: charge converted in a field-free layer of thickness d at the entrance is lost; for
+    monochromatic light nearly normal to the chip that happens with probability 1 - exp(-d / ell)."""
+    lam, n, dead = 420.0, 40000, 0.0002
+    sc = _mono_scene(lam, n)
+    sc.detector.dead_layer = dead
+    rec = oracle_mod.Oracle(sc).trace()
+    ell = np.interp(rec["lam"], sc.detector.ell_lam0 + np.arange(len(sc.detector.ell)), sc.detector.ell)
+    p = np.mean(1 - np.exp(-dead / ell))
+    frac = np.mean(((rec["flags"] >> 8) & 0xFF) == 8)
+    assert abs(frac - p) < 4 * np.sqrt(p * (1 - p) / n) + 1e-3
+
+
+def test_back_side_reflection_conversion_fraction(oracle_mod):
+    """Sec. 2.4.2: a photon reaching the back of the silicon is reflected with the normal-incidence Fresnel
+    probability R = ((n - 1) / (n + 1))^2 and converts on the way back: converted fraction =
+    P(L <= t) + R P(t < L <= 2 t) for an exponential conversion length L (near-normal incidence)."""
+    lam, n = 1000.0, 40000
+    sc = _mono_scene(lam, n, t_si=0.1)
+    sc.back_reflect = True
+    o = oracle_mod.Oracle(sc)
+    rec = o.trace()
+    ell = np.interp(rec["lam"], sc.detector.ell_lam0 + np.arange(len(sc.detector.ell)), sc.detector.ell)
+    nsi = np.array([o.index(1, l) for l in rec["lam"][:200]]).mean()
+    R = ((nsi - 1) / (nsi + 1)) ** 2
+    t = 0.1
+    p = np.mean((1 - np.exp(-t / ell)) + R * (np.exp(-t / ell) - np.exp(-2 * t / ell)))
+    frac = np.mean((rec["flags"] & 1) == 1)
+    assert abs(frac - p) < 4 * np.sqrt(p * (1 - p) / n) + 2e-3, (frac, p)
+
+
+def test_diffusion_sigma_constant_field_closed_form():
+    """Sec. 2.5 field model: with no doping the field is V / t, and sigma^2 = 2 (kT/q) (drift length) t / V."""
+    t, V, T = 0.1, 20.0, 173.0
+    sig = I.diffusion_sigma_table(t_si_mm=t, v_over=V, T_K=T, n_bulk=0.0, n=11)
+    depth_cm = np.linspace(0.0, t * 0.1, 11)
+    expect = np.sqrt(2 * 8.617333262e-5 * T * (t * 0.1 - depth_cm) * (t * 0.1) / V) * 10.0
+    np.testing.assert_allclose(sig, expect, rtol=1e-6, atol=1e-12)
+    # doping raises the field towards the front, so diffusion shrinks
+    assert np.all(I.diffusion_sigma_table(n_bulk=2e12)[:-1] < I.diffusion_sigma_table(n_bulk=0.0)[:-1])
+
+
+def test_bleeding_conserves_charge_and_respects_the_implant(oracle_mod):
+    """Sec. 2.5 saturation: no pixel ends above the full well, charge moves only within its half-row (the
+    centre implant is not crossed), and what is not removed is conserved."""
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 500, size=(40, 64)).astype(np.uint32)
+    img[5, 10] = 30000; img[7, 33] = 5000; img[9, 31] = 40000; img[20, :] = 900
+    w = 1000
+    out, removed = oracle_mod.bleed(img, w)
+    assert out.max() <= w
+    assert int(out.sum()) + removed == int(img.sum())
+    for half in (slice(0, 32), slice(32, 64)):
+        before, after = img[:, half].sum(1).astype(np.int64), out[:, half].sum(1).astype(np.int64)
+        assert np.all(after <= before) and np.all((after == before) | (after == w * 32))
