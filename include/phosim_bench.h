@@ -19,6 +19,11 @@ extern "C" {
    Errors: INVALID_ARGUMENT (null output, iterations < 1), CUDA. */
 phosim_status phosim_fma_rate(int fp64, int iterations, int blocks_per_sm, void* stream, double* tflops);
 
+/* The device Philox4x32-10 the trace kernel draws from (Salmon et al., SC'11), applied to n counters with
+   one key, for known-answer checks.  ctr: host, 4 n words; key: host, 2 words; out: host, 4 n words.
+   Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);
+
 #ifdef __cplusplus
 }
 #endif

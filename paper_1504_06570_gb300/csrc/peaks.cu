@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include "phosim_bench.h"
+#include "phosim_device.cuh"
 
 namespace {
 
@@ -50,5 +51,33 @@ extern "C" phosim_status phosim_fma_rate(int fp64, int iterations, int blocks_pe
     cudaFree(sink);
     if (e != cudaSuccess || ms <= 0.f) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
     *tflops = 2.0 * 16.0 * (double)iterations * blocks * 256.0 / (ms * 1e-3) / 1e12;
+    return PHOSIM_OK;
+}
+
+namespace {
+__global__ void philox_kernel(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = phosim::philox(ctr[i], k0, k1);
+}
+}  // namespace
+
+extern "C" phosim_status phosim_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {
+    if (!ctr || !key || !out || n < 1) return PHOSIM_ERR_INVALID_ARGUMENT;
+    void *dc = nullptr, *dout = nullptr;
+    const size_t bytes = (size_t)n * sizeof(uint4);
+    if (cudaMalloc(&dc, bytes) != cudaSuccess || cudaMalloc(&dout, bytes) != cudaSuccess) {
+        cudaFree(dc);
+        (void)cudaGetLastError();
+        return PHOSIM_ERR_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaMemcpy(dc, ctr, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        philox_kernel<<<(n + 127) / 128, 128>>>((const uint4*)dc, key[0], key[1], (uint4*)dout, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dout);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
     return PHOSIM_OK;
 }

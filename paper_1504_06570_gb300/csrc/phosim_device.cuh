@@ -249,7 +249,9 @@ __device__ __forceinline__ uint32_t intersect(const DSurface& S, const double p[
         const double dF = d[2] - zx * d[0] - zy * d[1];
         if (dF == 0.0) return PHOSIM_LOST_NEWTON;
         // a single-precision reciprocal of the slope: the iteration still contracts by ~1e-7 per step
-        const double step = F * (double)__frcp_rn((float)dF);
+        // (outside the single-precision range the division stays exact)
+        const double adF = fabs(dF);
+        const double step = (adF > 1e-30 && adF < 1e30) ? F * (double)__frcp_rn((float)dF) : F / dF;
         l -= step;
         if (fabs(step) < 1e-8) {
             const double inv = rsqrt(fma(zx, zx, fma(zy, zy, 1.0)));

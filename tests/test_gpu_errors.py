@@ -82,3 +82,20 @@ def test_rays_outside_a_surface_domain_are_flagged(oracle_mod):
     assert (reason_o == 2).sum() > 1000
     assert np.array_equal(reason_g == 2, reason_o == 2)
     assert gpu["counters"][1 + 2] == (reason_g == 2).sum()
+
+
+def test_newton_iteration_cap_is_a_flag_not_a_fault():
+    """A flat plate carrying a steep 10th-order asphere (alpha_10 r^10 reaches kilometres at the rim) seen by
+    tilted rays: Newton's method from the plane's root cannot converge within the iteration cap for many rays.
+    They are dropped as NEWTON and counted; the launch completes and the context stays usable."""
+    surfaces = [I.Surface(kind=I.REFRACT, R=0.0, alpha=(0, 0, 0, 0, 0, 0, 0, 1e-20), z=0.0, r_out=500.0, material=0),
+                I.Surface(kind=I.DETECTOR, z=-1000.0, material=1)]
+    src = I.point_sources([0.3], [0.0], [5000])
+    sc = bare_scene(surfaces, n_photons=5000, pupil=(0.0, 500.0), nx=4096, pixel=1.0, sources=src)
+    sc.z_entrance = 2.0e7
+    gpu = G.run_gpu(sc, P.PLAIN_FP64)
+    reasons = (gpu["rec"]["flags"] >> 8) & 0xFF
+    assert (reasons == 3).sum() > 0
+    assert gpu["counters"][1 + 3] == (reasons == 3).sum()
+    again = G.run_gpu(I.paraboloid_scene(n_photons=1000, screen_n=64), P.PLAIN_FP64, records=False)
+    assert again["counters"][0] == 1000
