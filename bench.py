@@ -3,8 +3,10 @@
 Workload: 1000 stars, 1e8 source photons per step (300-1200 nm blackbodies) through seven frozen-flow von
 Karman layers (4096^2 at 1 cm + 1024^2 at 64 cm each), the synthetic 8.4 m three-mirror telescope with a
 three-lens camera and a 550-700 nm filter, and 100 um of silicon, onto one 4096 x 4096 chip.  A step is one
-phosim_trace call over all photons.  The headline is the mixed-precision path; the plain all-FP64 path is
-timed beside it, and the moments of both are compared with the CPU oracle on a photon sample.
+phosim_trace call over all photons.  The headline is the mixed-precision path with its FP64 parts in
+double-single arithmetic (--mode ds, the default) or in native FP64 (--mode mixed); the other mixed form and
+the plain all-FP64 path are timed beside it, and the moments of all three are compared with the CPU oracle on
+a photon sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -37,7 +39,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--photons", type=float, default=1e8, help="photons per step per GPU")
-    ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain FP64 path")
+    ap.add_argument("--mode", default="ds", choices=["ds", "mixed"], help="headline mixed-precision form")
+    ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain FP64 path and of the "
+                                                                  "other mixed form")
     ap.add_argument("--sample", type=int, default=8000, help="oracle photons per star for the CPU leg")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-split, batched and adjoint legs")
@@ -99,7 +103,8 @@ class ClockSampler:
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "launches_three_mirror_1e8.md")
 KERNEL_SOURCES = ("paper_1504_06570_gb300/csrc/photon.cuh", "paper_1504_06570_gb300/csrc/trace.cu",
-                  "paper_1504_06570_gb300/csrc/phosim_device.cuh")
+                  "paper_1504_06570_gb300/csrc/phosim_device.cuh", "paper_1504_06570_gb300/csrc/photon_ds.cuh",
+                  "paper_1504_06570_gb300/csrc/ds.cuh")
 
 
 def kernel_source_hash():
@@ -111,18 +116,25 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(photons):
-    """DRAM bytes per launch of the mixed trace kernel from the committed ncu summary, scaled to this launch's
-    photons, or None when the kernel sources changed since that capture."""
+def recorded_traffic(photons, kernel):
+    """DRAM bytes per launch of a trace kernel (trace_kernel<1> native-FP64 mixed, trace_kernel<2>
+    double-single) from the committed ncu summary, scaled to this launch's photons, or None when the kernel
+    sources changed since that capture."""
     import re
     try:
         text = open(TRAFFIC_PROFILE).read()
     except OSError:
         return None
-    m = re.search(r"traffic_record: bytes=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text)
-    if not m or m.group(3) != kernel_source_hash():
-        return None
-    return int(m.group(1)) * photons / int(m.group(2))
+    for m in re.finditer(r"traffic_record: kernel=(\S+) bytes=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text):
+        if m.group(1) == kernel and m.group(4) == kernel_source_hash():
+            return int(m.group(2)) * photons / int(m.group(3))
+    return None
+
+
+# FP32 instructions of each double-single primitive of ds.cuh (sum: TwoSum 6 + 2 + Fast2Sum 3; product:
+# 1 multiply + 3 FMAs + Fast2Sum 3; quotient: reciprocal estimate, product, ds x float product 6, ds sum 11,
+# correction and Fast2Sum; square root: reciprocal-root estimate, product, exact square, ds sum, correction)
+DS_INSTRUCTIONS = {"add": 11, "mul": 7, "div": 23, "sqrt": 20}
 
 
 def measured_peaks():
@@ -230,7 +242,7 @@ def precision_split(sc, mixed, plain, counts, dev):
     return out
 
 
-def batched_leg(sc2, args, dev, stream):
+def batched_leg(sc2, args, dev, stream, precision):
     """10^4 stars and Sersic galaxies with counts log-uniform 1e2-1e7 plus 1e9 sky photons on 15 arcsec
     Gaussian nodes, one persistent launch per step with the autotuned schedule (same optics and atmosphere)."""
     import torch
@@ -239,7 +251,7 @@ def batched_leg(sc2, args, dev, stream):
     t0 = time.perf_counter()
     sc = I.batched_scene(fine_n=16, coarse_n=16, photon_scale=args.batched_scale)
     sc.layers = sc2.layers
-    scn = P.Scene(sc, P.MIXED, early_reject=True)
+    scn = P.Scene(sc, precision, early_reject=True)
     threads, tile = scn.autotune(sample_photons=20_000_000)
     d = sc.detector
     img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
@@ -331,9 +343,11 @@ def main():
     from paper_1504_06570_gb300 import sharding
     first, counts = sharding.rank_photon_range(sc.sources.n_photons, rank, world)
     photons = int(counts.sum())
-    # both precisions with the paper's dynamic transmission (early coating rejection), which leaves the
-    # detected photons unchanged
-    mixed = P.Scene(sc, P.MIXED, early_reject=True, graph=True)
+    # every path with the paper's dynamic transmission (early coating rejection), which leaves the detected
+    # photons unchanged; the headline form as a CUDA graph
+    head_prec, other_prec = (P.MIXED_DS, P.MIXED) if args.mode == "ds" else (P.MIXED, P.MIXED_DS)
+    head = P.Scene(sc, head_prec, early_reject=True, graph=True)
+    other = P.Scene(sc, other_prec, early_reject=True, graph=True)
     plain = P.Scene(sc, P.PLAIN_FP64, early_reject=True)
     setup_s = time.perf_counter() - t_setup
     d = sc.detector
@@ -372,30 +386,32 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    per_mixed = timed(mixed, args.steps, args.warmup)
+    per_head = timed(head, args.steps, args.warmup)
     clock_rec = clocks.stop()
+    per_other = timed(other, args.plain_steps, 1)
     per_plain = timed(plain, args.plain_steps, 1)
 
     # e2e through the C ABI with host buffers: pinned host image in, result image out, every step
     himg = torch.zeros((d.ny, d.nx), dtype=torch.int32, pin_memory=True)
     for _ in range(1):
-        mixed.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+        head.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        mixed.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+        head.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
     img_bytes = d.nx * d.ny * 4
     src_bytes = n_src * (P.C.sizeof(P.Source) if hasattr(P, "C") else 80) + n_src * 16
 
-    ms_mixed = float(per_mixed.max()) if world == 1 else float(per_mixed.mean())
-    t_mixed = float(per_mixed.sum()) / 1e3
+    t_head = float(per_head.sum()) / 1e3
+    t_other = float(per_other.sum()) / 1e3
     t_plain = float(per_plain.sum()) / 1e3
-    t_mixed, t_plain, e2e_s = sharding.max_over_ranks([t_mixed, t_plain, e2e_s], device=dev)
-    value = photons * world * args.steps / t_mixed
+    t_head, t_other, t_plain, e2e_s = sharding.max_over_ranks([t_head, t_other, t_plain, e2e_s], device=dev)
+    value = photons * world * args.steps / t_head
+    other_value = photons * world * args.plain_steps / t_other
     plain_value = photons * world * args.plain_steps / t_plain
-    counters = mixed.counters()
+    counters = head.counters()
 
     if rank != 0:
         if world > 1:
@@ -403,16 +419,22 @@ def main():
             dist.destroy_process_group()
         return
 
-    peaks = measured_peaks()
+    names = {P.MIXED_DS: "mixed_ds", P.MIXED: "mixed_fp64_optics"}
+    descr = {P.MIXED_DS: "mixed, double-single (FP32-pair) positions/directions/transforms/intersections, FP32 "
+                         "deflections/SED blur/sensor",
+             P.MIXED: "mixed, FP64 positions/directions/transforms/intersections, FP32 deflections/SED blur/sensor"}
     line = {"metric": METRIC, "value": value, "unit": "photons/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": t_head / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f32" if head_prec == P.MIXED_DS else "f64+f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "photons_per_step_per_gpu": photons, "sources": n_src,
-                       "precision": "mixed (FP64 positions/intersections, FP32 deflections/SED blur/sensor)",
+                       "precision": descr[head_prec],
                        "l2": "inputs larger than L2 (gradient screens 2.8 GB, read in both precisions' forms)",
                        "setup_s": round(setup_s, 1)},
+            names[other_prec]: {"value": other_value, "unit": "photons/s",
+                                "ms_per_step": t_other / args.plain_steps * 1e3, "precision": descr[other_prec]},
             "plain_fp64": {"value": plain_value, "unit": "photons/s", "ms_per_step": t_plain / args.plain_steps * 1e3,
-                           "speedup_of_mixed": value / plain_value},
+                           "speedup_of_headline": value / plain_value},
             "detected_fraction": float(counters[1] / max(1, counters[0])),
             "e2e": {"value": photons * world / e2e_s, "unit": "photons/s", "h2d_bytes_per_step": img_bytes + src_bytes,
                     "d2h_bytes_per_step": img_bytes},
@@ -425,25 +447,43 @@ def main():
         ops = o.count_ops(count=np.minimum(counts, np.uint64(50)), early_reject=True)
         fl_pre = sum(v for k, v in ops["pre"].items() if k != "transcendental")
         fl_opt = sum(v for k, v in ops["optics"].items() if k != "transcendental")
-        kernel_s = float(np.mean(per_mixed)) / 1e3
-        achieved = fl_opt * photons / kernel_s / 1e12
-        peak = fp64_rate or FP64_NOMINAL_TFLOPS
-        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": recorded_traffic(photons),
-                            "traffic_unit": "DRAM bytes per launch (ncu, committed summary)",
-                            "algorithmic_gather_bytes": gather_bytes_per_launch(sc, ops, photons),
-                            "note": (f"FP64 optics flops {fl_opt:.0f} per sampled photon (oracle op count with the dynamic "
-                                     f"transmission rejection; +{fl_pre:.0f} sampling and atmosphere flops, mostly FP32 "
-                                     f"here) over the mixed step time; peak = "
-                                     + ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)"))}
+        per_mixed = per_head if head_prec == P.MIXED else per_other
+        per_ds = per_head if head_prec == P.MIXED_DS else per_other
+        peak64 = fp64_rate or FP64_NOMINAL_TFLOPS
+        # native-FP64 mixed kernel: the oracle's FP64 optics flops against the FP64 FMA rate
+        fp64_roof = {"bound": "alu", "achieved": fl_opt * photons / (float(np.mean(per_mixed)) / 1e3) / 1e12,
+                     "peak": peak64, "unit": "TFLOP/s", "traffic": recorded_traffic(photons, "trace_kernel<1>"),
+                     "note": (f"FP64 optics flops {fl_opt:.0f} per sampled photon (oracle op count with the dynamic "
+                              f"transmission rejection; +{fl_pre:.0f} sampling and atmosphere flops, mostly FP32 "
+                              f"here) over the step time; peak = "
+                              + ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)"))}
+        fp64_roof["frac"] = fp64_roof["achieved"] / peak64
+        # double-single kernel: the same optics operations as FP32 instructions of the double-single
+        # algorithms, against the FP32 instruction issue rate (FMA rate / 2)
+        ds_inst = sum(ops["optics"][k] * c for k, c in DS_INSTRUCTIONS.items())
+        peak32 = fp32_rate / 2 if fp32_rate else None
+        ds_roof = {"bound": "alu", "achieved": ds_inst * photons / (float(np.mean(per_ds)) / 1e3) / 1e12,
+                   "peak": peak32, "unit": "Tinst/s", "traffic": recorded_traffic(photons, "trace_kernel<2>"),
+                   "note": (f"the oracle's FP64 optics operations per sampled photon ({ops['optics']['add']:.0f} add, "
+                            f"{ops['optics']['mul']:.0f} mul, {ops['optics']['div']:.0f} div, "
+                            f"{ops['optics']['sqrt']:.0f} sqrt) costed as FP32 instructions of the double-single "
+                            f"primitives {DS_INSTRUCTIONS} = {ds_inst:.0f} per photon, over the step time; peak = "
+                            "measured FP32 FMA rate / 2 (one instruction per FMA); sampling, atmosphere and sensor "
+                            "instructions are not counted")}
+        ds_roof["frac"] = ds_roof["achieved"] / peak32 if peak32 else None
+        head_roof, other_roof = (ds_roof, fp64_roof) if head_prec == P.MIXED_DS else (fp64_roof, ds_roof)
+        head_roof["algorithmic_gather_bytes"] = gather_bytes_per_launch(sc, ops, photons)
+        head_roof["traffic_unit"] = "DRAM bytes per launch (ncu, committed summary)"
+        line["roofline"] = head_roof
+        line["roofline_" + names[other_prec]] = other_roof
         line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) * photons / (float(np.mean(per_plain)) / 1e3) / 1e12,
-                                       "peak": peak, "unit": "TFLOP/s"}
-        line["roofline_plain_fp64"]["frac"] = line["roofline_plain_fp64"]["achieved"] / peak
+                                       "peak": peak64, "unit": "TFLOP/s"}
+        line["roofline_plain_fp64"]["frac"] = line["roofline_plain_fp64"]["achieved"] / peak64
         if rank == 0:
             cpu, rec, cnt = cpu_leg(sc, args.sample)
             line["cpu_baseline"] = cpu
             errs = {}
-            for name, scn in (("mixed", mixed), ("plain_fp64", plain)):
+            for name, scn in ((names[head_prec], head), (names[other_prec], other), ("plain_fp64", plain)):
                 m2 = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
                 i2 = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
                 scn.trace(i2, None, m2, n_photons=cnt)
@@ -451,11 +491,13 @@ def main():
                 errs[name] = moment_errors(m2.cpu().numpy(), rec, n_src)
             line["moment_error_vs_oracle"] = errs
     if not args.no_extras and rank == 0:
-        line["precision_split"] = precision_split(sc, mixed, plain, counts, dev)
-        line["batched"] = batched_leg(sc, args, dev, stream)
+        line["precision_split"] = {names[head_prec]: precision_split(sc, head, plain, counts, dev),
+                                   names[other_prec]: precision_split(sc, other, plain, counts, dev)}
+        line["batched"] = batched_leg(sc, args, dev, stream, head_prec)
         line["adjoint"] = adjoint_leg(dev, stream)
     print(json.dumps(line))
-    mixed.close()
+    head.close()
+    other.close()
     plain.close()
     if world > 1:
         dist.barrier()

@@ -50,9 +50,16 @@ enum { PHOSIM_POINT = 0, PHOSIM_SERSIC = 1, PHOSIM_GAUSS = 2 };
 /* precision of the photon path */
 enum {
     PHOSIM_PLAIN_FP64 = 0,   /* every step in FP64 */
-    PHOSIM_MIXED = 1         /* FP64 for positions, surface transforms and intersections; FP32 for the
+    PHOSIM_MIXED = 1,        /* FP64 for positions, surface transforms and intersections; FP32 for the
                                 wavelength blur, screen-gradient deflections, source shapes, silicon
                                 conversion and diffusion; FP32 moment partials with compensated sums */
+    PHOSIM_MIXED_DS = 2      /* PHOSIM_MIXED with its FP64 parts (positions, directions, surface transforms,
+                                intersections, focal-plane position) in double-single arithmetic: pairs of
+                                FP32 numbers carrying about 48 significant bits, on the FP32 pipes, which
+                                issue about seventy times the FP64 rate on this GPU.  The pupil azimuth and
+                                the Sellmeier index are double-single too; coating decisions compare the
+                                integer draw with integer thresholds.  phosim_grad runs the FP64 path
+                                whatever the scene's precision. */
 };
 
 /* scene flags */
@@ -83,7 +90,7 @@ enum {
    absorption length; Sec. 2.5 diffusion).  Tables are host pointers, copied at creation. */
 typedef struct phosim_scene_desc {
     uint64_t seed;              /* Philox4x32-10 key */
-    int32_t precision;          /* PHOSIM_PLAIN_FP64 or PHOSIM_MIXED */
+    int32_t precision;          /* PHOSIM_PLAIN_FP64, PHOSIM_MIXED or PHOSIM_MIXED_DS */
     uint32_t flags;             /* PHOSIM_ATMOSPHERE | PHOSIM_SENSOR */
     double pupil_r_in, pupil_r_out;   /* annulus sampled on the first surface (Sec. 2.2), mm */
     double h_top;               /* top of the atmosphere, telescope-frame z, mm (100 km) */

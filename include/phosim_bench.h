@@ -1,8 +1,9 @@
 /*
- * phosim_bench.h — measurement helper of the phosim library (no counterpart in the paper).
+ * phosim_bench.h — measurement and check helpers of the phosim library (no counterpart in the paper).
  *
  * The photon path is bound by plain FP64/FP32 arithmetic, so its roofline needs the device's FMA issue
- * rate, which the vendor's published figures and the driver's copy/GEMM peaks do not give.
+ * rate, which the vendor's published figures and the copy/GEMM peaks do not give.  The other entries
+ * expose device building blocks (the random-number generator, the double-single arithmetic) to tests.
  */
 #ifndef PHOSIM_BENCH_H
 #define PHOSIM_BENCH_H
@@ -23,6 +24,15 @@ phosim_status phosim_fma_rate(int fp64, int iterations, int blocks_per_sm, void*
    one key, for known-answer checks.  ctr: host, 4 n words; key: host, 2 words; out: host, 4 n words.
    Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
 phosim_status phosim_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);
+
+/* The double-single primitives of the PHOSIM_MIXED_DS path applied element-wise, for accuracy checks
+   against FP64.  Each input double is first rounded to the nearest double-single pair; each result is
+   returned as the double hi + lo.  op: 0 a + b, 1 a - b, 2 a b, 3 a / b, 4 sqrt(a), 5 1 / sqrt(a),
+   6 a b + a, 7 (sin, cos) of 2 pi u with u = (a + 1/2) 2^-32 for the 32-bit integer a (2 n outputs),
+   8 u itself, 9 (floor(a), a - floor(a)) (2 n outputs).  a, b: host, n values (b unused by ops 4, 5, 7-9);
+   out: host, n or 2 n values.  Errors: INVALID_ARGUMENT (unknown op, null pointer, n < 1), OUT_OF_MEMORY,
+   CUDA. */
+phosim_status phosim_ds_eval(int op, const double* a, const double* b, double* out, int n);
 
 #ifdef __cplusplus
 }

@@ -1,8 +1,10 @@
-// FMA issue-rate probe: the denominator of the arithmetic roofline of the photon kernels.
+// FMA issue-rate probe (the denominator of the arithmetic roofline of the photon kernels) and the check
+// entries of phosim_bench.h: the device Philox and the double-single primitives.
 #include <cuda_runtime.h>
 
 #include "phosim_bench.h"
 #include "phosim_device.cuh"
+#include "photon_ds.cuh"
 
 namespace {
 
@@ -77,6 +79,67 @@ extern "C" phosim_status phosim_philox(const uint32_t* ctr, const uint32_t* key,
     }
     if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
     cudaFree(dc);
+    cudaFree(dout);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    return PHOSIM_OK;
+}
+
+namespace {
+__global__ void ds_eval_kernel(int op, const double* a, const double* b, double* out, int n) {
+    using namespace phosim;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ds x = ds_of(a[i]), y = ds_of(b[i]);
+    ds r = ds_f(0.f);
+    switch (op) {
+        case 0: r = x + y; break;
+        case 1: r = x - y; break;
+        case 2: r = x * y; break;
+        case 3: r = x / y; break;
+        case 4: r = ds_sqrt(x); break;
+        case 5: r = ds_rsqrt(x); break;
+        case 6: r = dfma(x, y, x); break;
+        case 7: {
+            ds s, c;
+            ds_sincos_2pi(ds_uniform((uint32_t)a[i]), s, c);
+            out[2 * i] = ds_value(s);
+            out[2 * i + 1] = ds_value(c);
+            return;
+        }
+        case 8: r = ds_uniform((uint32_t)a[i]); break;
+        case 9: {
+            const float f = ds_floor(x);
+            out[2 * i] = (double)f;
+            out[2 * i + 1] = (double)ds_frac(x, f);
+            return;
+        }
+        default: break;
+    }
+    out[i] = ds_value(r);
+}
+}  // namespace
+
+extern "C" phosim_status phosim_ds_eval(int op, const double* a, const double* b, double* out, int n) {
+    if (op < 0 || op > 9 || !a || !b || !out || n < 1) return PHOSIM_ERR_INVALID_ARGUMENT;
+    const size_t in_bytes = (size_t)n * sizeof(double);
+    const size_t out_bytes = (op == 7 || op == 9 ? 2 : 1) * in_bytes;
+    double *da = nullptr, *db = nullptr, *dout = nullptr;
+    if (cudaMalloc(&da, in_bytes) != cudaSuccess || cudaMalloc(&db, in_bytes) != cudaSuccess ||
+        cudaMalloc(&dout, out_bytes) != cudaSuccess) {
+        cudaFree(da);
+        cudaFree(db);
+        (void)cudaGetLastError();
+        return PHOSIM_ERR_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaMemcpy(da, a, in_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(db, b, in_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        ds_eval_kernel<<<(n + 127) / 128, 128>>>(op, da, db, dout, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, out_bytes, cudaMemcpyDeviceToHost);
+    cudaFree(da);
+    cudaFree(db);
     cudaFree(dout);
     if (e != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
     return PHOSIM_OK;

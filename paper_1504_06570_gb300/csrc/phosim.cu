@@ -176,6 +176,44 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
     return PHOSIM_OK;
 }
 
+// a double-single pair, with magnitudes beyond the single-precision range (an unlimited aperture) clamped
+ds ds_clamped(double v) {
+    if (v > 1e37) return ds{1e37f, 0.f};
+    if (v < -1e37) return ds{-1e37f, 0.f};
+    return ds_of(v);
+}
+
+// the double-single copy of a surface (DSurfaceS): asphere coefficients rescaled to rho = r / rn
+void build_surface_s(const phosim_surface& s, const DSurface& d, DSurfaceS& e) {
+    std::memset(&e, 0, sizeof(e));
+    e.c = ds_of(d.c);
+    e.k1c2 = ds_of(d.k1c2);
+    e.kc = ds_of(d.kc);
+    const double rn = (s.r_out > 0.0 && s.r_out < 1e6) ? s.r_out : 1000.0;
+    for (int k = 0; k < 4; ++k) {
+        const double ae = d.ae[k] * std::pow(rn, 2 * k + 4), ao = d.ao[k] * std::pow(rn, 2 * k + 3);
+        e.ae[k] = ds_clamped(ae);
+        e.aed[k] = ds_clamped((2 * k + 4) * ae);
+        e.ao[k] = ds_clamped(ao);
+        e.aod[k] = ds_clamped((2 * k + 3) * ao);
+    }
+    for (int i = 0; i < 9; ++i) e.M[i] = ds_of(d.M[i]);
+    for (int i = 0; i < 3; ++i) e.o[i] = ds_of(d.o[i]);
+    e.r_in2 = ds_clamped(d.r_in2);
+    e.r_out2 = ds_clamped(d.r_out2);
+    e.inv_rn = ds_of(1.0 / rn);
+    e.inv_rn2 = ds_of(1.0 / (rn * rn));
+    e.zinv = (float)d.zinv;
+    for (int i = 0; i < kZPoly; ++i) e.zp[i] = (float)d.zp[i];
+}
+
+// integer accept thresholds of a transmission: the draw (w + 1/2) 2^-32 < T exactly when w < ceil(T 2^32 - 1/2)
+unsigned long long accept_threshold(double T) {
+    if (!(T > 0.0)) return 0ull;
+    if (T >= 1.0) return 1ull << 32;
+    return (unsigned long long)std::ceil(std::ldexp(T, 32) - 0.5);
+}
+
 // ----------------------------------------------------------------------------------------- device kernels
 // central-difference gradient of a periodic phase screen, rad per mm (Sec. 2.3.2), stored per node as the
 // 2 x 2 block of gradients the bilinear interpolation reads (see DScale)
@@ -231,14 +269,14 @@ void destroy_graph(TraceGraph& g) {
 
 // The chief-ray and trace launches as one CUDA graph: captured once per precision on a private stream,
 // then replayed on the caller's stream with this call's kernel parameters and launch shapes.
-phosim_status launch_trace_graph(phosim_scene* sc, TraceParams& P, bool mixed, int blocks, int n_src, double* moments,
+phosim_status launch_trace_graph(phosim_scene* sc, TraceParams& P, int mode, int blocks, int n_src, double* moments,
                                  cudaStream_t st) {
-    TraceGraph& g = sc->graphs[mixed ? 1 : 0];
+    TraceGraph& g = sc->graphs[mode];
     if (!g.exec) {
         if (!sc->capture_stream) CU(cudaStreamCreateWithFlags(&sc->capture_stream, cudaStreamNonBlocking));
         CU(cudaStreamBeginCapture(sc->capture_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e1 = launch_chief_rays(P, sc->d_src, n_src, moments, sc->capture_stream);
-        cudaError_t e2 = launch_trace(P, mixed, blocks, sc->threads, sc->capture_stream);
+        cudaError_t e2 = launch_trace(P, mode, blocks, sc->threads, sc->capture_stream);
         cudaGraph_t graph = nullptr;
         cudaError_t e3 = cudaStreamEndCapture(sc->capture_stream, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !graph) {
@@ -257,7 +295,7 @@ phosim_status launch_trace_graph(phosim_scene* sc, TraceParams& P, bool mixed, i
             if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
             cudaKernelNodeParams kp;
             if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) continue;
-            if (kp.func == trace_kernel_ptr(mixed)) g.trace = node;
+            if (kp.func == trace_kernel_ptr(mode)) g.trace = node;
             else if (kp.func == chief_kernel_ptr()) g.chief = node;
         }
         if (!g.trace || !g.chief) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
@@ -273,7 +311,7 @@ phosim_status launch_trace_graph(phosim_scene* sc, TraceParams& P, bool mixed, i
     kc.kernelParams = chief_args;
     void* trace_args[1] = {&P};
     cudaKernelNodeParams kt = {};
-    kt.func = (void*)trace_kernel_ptr(mixed);
+    kt.func = (void*)trace_kernel_ptr(mode);
     kt.gridDim = dim3((unsigned)blocks);
     kt.blockDim = dim3((unsigned)sc->threads);
     kt.kernelParams = trace_args;
@@ -304,7 +342,8 @@ const char* phosim_status_string(phosim_status s) {
 phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out) {
     if (!d || !out) return PHOSIM_ERR_INVALID_ARGUMENT;
     *out = nullptr;
-    if (d->precision != PHOSIM_PLAIN_FP64 && d->precision != PHOSIM_MIXED) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (d->precision != PHOSIM_PLAIN_FP64 && d->precision != PHOSIM_MIXED && d->precision != PHOSIM_MIXED_DS)
+        return PHOSIM_ERR_INVALID_ARGUMENT;
     if (d->nx <= 0 || d->ny <= 0 || (int64_t)d->nx * d->ny > (int64_t)1 << 31) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->pixel > 0.0) || !(d->t_si > 0.0) || !(d->lambda_ref > 0.0) || !(d->ell_dlam > 0.0))
         return PHOSIM_ERR_INVALID_ARGUMENT;
@@ -336,6 +375,13 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
     P.n_ell = d->n_ell; P.n_sig = d->n_sigma;
     P.sig_scale = (d->n_sigma - 1) / d->t_si;
     P.dead_layer = d->dead_layer;
+    P.pr_in2_s = ds_of(P.pr_in2); P.pr_dr2_s = ds_of(P.pr_dr2);
+    P.h_top_s = ds_of(P.h_top); P.z_ent_s = ds_of(P.z_ent);
+    P.xlo_s = ds_of(P.xlo); P.ylo_s = ds_of(P.ylo); P.inv_pixel_s = ds_of(P.inv_pixel);
+    P.chip_w_s = ds_of(P.nx * P.pixel); P.chip_h_s = ds_of(P.ny * P.pixel);
+    P.kick0f = (float)P.kick0; P.inv_lam_ref_f = (float)(1.0 / P.lam_ref);
+    P.t_sif = (float)P.t_si; P.dead_layerf = (float)P.dead_layer;
+    P.ell_lam0f = (float)P.ell_lam0; P.inv_ell_dlamf = (float)P.inv_ell_dlam; P.sig_scalef = (float)P.sig_scale;
     sc->precision = d->precision;
     std::vector<float> f(d->ell, d->ell + d->n_ell), g(d->sigma, d->sigma + d->n_sigma);
     double* pd;
@@ -384,8 +430,7 @@ void phosim_destroy_scene(phosim_scene* sc) {
     cudaFree(sc->d_stage);
     cudaFree(sc->d_grad_scratch);
     cudaFree(sc->d_mom_scratch);
-    destroy_graph(sc->graphs[0]);
-    destroy_graph(sc->graphs[1]);
+    for (TraceGraph& g : sc->graphs) destroy_graph(g);
     if (sc->capture_stream) cudaStreamDestroy(sc->capture_stream);
     (void)cudaGetLastError();
     delete sc;
@@ -417,6 +462,7 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
     int coated = 0;
     for (int i = 0; i < n_surf; ++i) {
         build_surface(surf[i], P.surf[i]);
+        build_surface_s(surf[i], P.surf[i], P.surf_s[i]);
         if (surf[i].coating >= 0 && surf[i].kind != PHOSIM_DETECTOR) {
             if (coated >= PHOSIM_MAX_COATED) return PHOSIM_ERR_LIMIT;
             P.coated_surface[coated] = i;
@@ -427,26 +473,40 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
     P.pupil_surf.flags &= ~SF_ZERN;
     if (!(P.pupil_surf.flags & (SF_CONIC | SF_EVEN | SF_ODD))) P.pupil_surf.flags |= SF_FLAT_ONLY;
     P.pupil_z = surf[0].z;
+    P.pupil_s = P.surf_s[0];
+    P.pupil_z_s = ds_of(P.pupil_z);
     P.n_surf = n_surf;
     P.n_coated = coated;
     P.n_mat = n_mat;
     for (int k = 0; k < n_mat; ++k) {
         P.mat[k].kind = mats[k].kind;
-        for (int q = 0; q < 3; ++q) { P.mat[k].B[q] = mats[k].B[q]; P.mat[k].C[q] = mats[k].C[q]; }
+        for (int q = 0; q < 3; ++q) {
+            P.mat[k].B[q] = mats[k].B[q]; P.mat[k].C[q] = mats[k].C[q];
+            P.mat[k].Bs[q] = ds_of(mats[k].B[q]); P.mat[k].Cs[q] = ds_of(mats[k].C[q]);
+        }
     }
     std::vector<void*> mem;
     for (int k = 0; k < n_coat; ++k) {
         double *d, *dmax;
+        unsigned long long *dthr, *dmax_thr;
         const int nl = coats[k].n_lambda, nt = coats[k].n_theta;
         std::vector<double> tmax((size_t)nl, 0.0);
+        std::vector<unsigned long long> thr((size_t)nl * nt), tmax_thr((size_t)nl);
         for (int il = 0; il < nl; ++il)
             for (int it = 0; it < nt; ++it) tmax[il] = std::max(tmax[il], coats[k].table[(size_t)il * nt + it]);
+        for (size_t i = 0; i < thr.size(); ++i) thr[i] = accept_threshold(coats[k].table[i]);
+        for (int il = 0; il < nl; ++il) tmax_thr[il] = accept_threshold(tmax[il]);
         phosim_status st = upload(mem, coats[k].table, (size_t)nl * nt, &d);
         if (st == PHOSIM_OK) st = upload(mem, tmax.data(), tmax.size(), &dmax);
+        if (st == PHOSIM_OK) st = upload(mem, thr.data(), thr.size(), &dthr);
+        if (st == PHOSIM_OK) st = upload(mem, tmax_thr.data(), tmax_thr.size(), &dmax_thr);
         if (st != PHOSIM_OK) { free_all(mem); return st; }
         DCoating& C = P.coat[k];
         C.lam0 = coats[k].lam0; C.inv_dlam = 1.0 / coats[k].dlam;
         C.th0 = coats[k].theta0; C.inv_dth = 1.0 / coats[k].dtheta;
+        C.lam0f = (float)C.lam0; C.inv_dlamf = (float)C.inv_dlam; C.th0f = (float)C.th0; C.inv_dthf = (float)C.inv_dth;
+        C.T_thr = dthr;
+        C.Tmax_thr = dmax_thr;
         C.nl = coats[k].n_lambda; C.nt = coats[k].n_theta;
         C.T = d;
         C.Tmax = dmax;
@@ -491,6 +551,7 @@ phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, 
         const phosim_layer& L = layers[k];
         DLayer& D = P.layer[k];
         D.z = L.z; D.vx = L.vx; D.vy = L.vy; D.n_scales = L.n_scales;
+        D.zs = ds_of(L.z); D.vxs = ds_of(L.vx); D.vys = ds_of(L.vy);
         for (int q = 0; q < L.n_scales; ++q) {
             const phosim_screen_scale& S = L.scales[q];
             const size_t nn = (size_t)S.n * S.n;
@@ -513,6 +574,7 @@ phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, 
             }
             D.s[q].n = S.n;
             D.s[q].inv_pix = 1.0 / S.pixel;
+            D.s[q].inv_pix_s = ds_of(1.0 / S.pixel);
             D.s[q].g64 = (const double2*)g64;
             D.s[q].g32 = (const float4*)g32;
         }
@@ -563,6 +625,8 @@ phosim_status phosim_load_seds(phosim_scene* sc, const double* flux, int n_sed, 
     sc->base.n_bins = n_bins;
     sc->base.sed_lam0 = lam0;
     sc->base.sed_dlam = dlam;
+    sc->base.sed_lam0f = (float)lam0;
+    sc->base.sed_dlamf = (float)dlam;
     sc->n_sed = n_sed;
     sc->seds_loaded = true;
     return PHOSIM_OK;
@@ -693,10 +757,10 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     if (!sc || n_src < 0 || (n_src > 0 && (!src || !n_photons)) || !image) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool mixed = sc->precision == PHOSIM_MIXED;
+    const int mode = sc->precision;
     // launch shape
     int per_sm = 0;
-    CU(trace_occupancy(mixed, sc->threads, &per_sm));
+    CU(trace_occupancy(mode, sc->threads, &per_sm));
     if (per_sm < 1) per_sm = 1;
     const int blocks = sc->sm_count * per_sm;
     const uint64_t warps = (uint64_t)blocks * (sc->threads / 32);
@@ -774,11 +838,11 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     P.moments = moments;
     P.records = records;
     if (P.flags & PHOSIM_GRAPH) {
-        phosim_status gs = launch_trace_graph(sc, P, mixed, blocks, n_src, moments, st);
+        phosim_status gs = launch_trace_graph(sc, P, mode, blocks, n_src, moments, st);
         if (gs != PHOSIM_OK) return gs;
     } else {
         CU(launch_chief_rays(P, sc->d_src, n_src, moments, st));
-        CU(launch_trace(P, mixed, blocks, sc->threads, st));
+        CU(launch_trace(P, mode, blocks, sc->threads, st));
     }
     sc->last_stream = st;
     if (host_image) {

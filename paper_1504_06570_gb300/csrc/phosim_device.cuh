@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "phosim.h"
+#include "ds.cuh"
 
 namespace phosim {
 
@@ -32,16 +33,35 @@ struct DSurface {
     double zp[kZPoly];                        // sum_j c_j Z_j as monomials of (x zinv, y zinv), row b = y power
 };
 
+// The shape and placement of a surface as double-single pairs, for the FP32-pipe optics.  The asphere
+// polynomials are rescaled to the normalised radius rho = r / rn (rn the clear radius), so that their
+// coefficients stay far from the single-precision underflow that alpha_10 ~ 1e-30 mm^-9 would reach:
+// even part  z = sum_k ae[k] u^(k+2),  u = rho^2;   (1/r) dz/dr = inv_rn2 u sum_k aed[k] u^k
+// odd part   z = rho^3 sum_k ao[k] u^k;             (1/r) dz/dr = inv_rn2 rho sum_k aod[k] u^k
+struct DSurfaceS {
+    ds c, k1c2, kc;
+    ds ae[4], aed[4], ao[4], aod[4];
+    ds M[9], o[3];
+    ds r_in2, r_out2;
+    ds inv_rn, inv_rn2;
+    float zinv, pad;
+    float zp[kZPoly];
+};
+
 struct DMaterial {
     int kind, pad;
     double B[3], C[3];
+    ds Bs[3], Cs[3];
 };
 
 struct DCoating {
     double lam0, inv_dlam, th0, inv_dth;
+    float lam0f, inv_dlamf, th0f, inv_dthf;
     int nl, nt, pad0, pad1;
     const double* T;                          // nl x nt
     const double* Tmax;                       // nl: the largest transmission over angles at each wavelength
+    const unsigned long long* T_thr;          // the same as integer thresholds ceil(T 2^32 - 1/2) on the draw
+    const unsigned long long* Tmax_thr;
 };
 
 // A screen scale's central-difference gradient (rad / mm), stored per node (i, j) as the 2 x 2 block of
@@ -50,12 +70,14 @@ struct DCoating {
 struct DScale {
     int n, pad;
     double inv_pix;
+    ds inv_pix_s;
     const double2* g64;                       // 4 double2 per node, n x n nodes
     const float4* g32;                        // 2 float4 per node: (g00, g10), (g01, g11)
 };
 
 struct DLayer {
     double z, vx, vy;
+    ds zs, vxs, vys;
     int n_scales, pad;
     DScale s[PHOSIM_MAX_SCALES];
 };
@@ -85,6 +107,11 @@ struct TraceParams {
     DMaterial mat[kMaxMaterials];
     DCoating coat[kMaxCoatings];
     DLayer layer[PHOSIM_MAX_LAYERS];
+    // the same scene in double-single / single precision for the FP32-pipe path
+    DSurfaceS surf_s[PHOSIM_MAX_SURFACES];
+    DSurfaceS pupil_s;
+    ds pr_in2_s, pr_dr2_s, h_top_s, z_ent_s, pupil_z_s, xlo_s, ylo_s, inv_pixel_s, chip_w_s, chip_h_s;
+    float kick0f, inv_lam_ref_f, sed_lam0f, sed_dlamf, t_sif, dead_layerf, ell_lam0f, inv_ell_dlamf, sig_scalef;
     // sensor / detector
     int nx, ny, n_ell, n_sig;
     double pixel, inv_pixel, xlo, ylo, t_si, ell_lam0, inv_ell_dlam, sig_scale, dead_layer;

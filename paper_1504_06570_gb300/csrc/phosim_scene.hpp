@@ -46,15 +46,16 @@ struct phosim_scene {
     double* d_mom_scratch = nullptr;
     size_t cap_mom = 0;
     // CUDA graphs of the trace launch (PHOSIM_GRAPH), one per precision, captured on a private stream
-    TraceGraph graphs[2];
+    TraceGraph graphs[3];
     cudaStream_t capture_stream = nullptr;
 };
 
 namespace phosim {
-cudaError_t launch_trace(const TraceParams& P, bool mixed, int blocks, int threads, cudaStream_t st);
+// mode: the scene's precision (PHOSIM_PLAIN_FP64, PHOSIM_MIXED, PHOSIM_MIXED_DS)
+cudaError_t launch_trace(const TraceParams& P, int mode, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_chief_rays(const TraceParams& P, DSource* sources, int n_src, double* moments, cudaStream_t st);
-cudaError_t trace_occupancy(bool mixed, int threads, int* blocks_per_sm);
-const void* trace_kernel_ptr(bool mixed);
+cudaError_t trace_occupancy(int mode, int threads, int* blocks_per_sm);
+const void* trace_kernel_ptr(int mode);
 const void* chief_kernel_ptr();
 void free_all(std::vector<void*>& v);
 }  // namespace phosim

@@ -1,0 +1,509 @@
+// The photon path of Peterson et al. (2015), Sec. 2.2-2.5, with double-single arithmetic on the FP32 pipes
+// (precision PHOSIM_MIXED_DS).
+//
+// The steps, their order and the random-number slots are those of trace_photon in photon.cuh; what
+// changes is the number type.  Positions, directions, the surface transforms, the intersections and the
+// final focal-plane position, which the FP64 paths keep in double precision, are double-single pairs
+// (ds.cuh, about 48 significant bits); the deflections, the wavelength, the sensor draws and the moment
+// partials are single precision as in the mixed path.  Accept decisions on coatings compare the integer
+// random word with integer thresholds, so for a given table bin they are those of the FP64 paths exactly.
+#pragma once
+
+#include "photon.cuh"
+
+namespace phosim {
+
+struct PhotonOutS {
+    ds x, y, xc, yc;
+    float lam;
+    uint32_t flags;
+    int pix;
+};
+
+// the per-source constants of a tile, converted once per tile
+struct SourceS {
+    ds xi, eta, t0, t_exp, ref_x, ref_y;
+    float zfac, a, b, cpa, spa;
+    int kind, sed, table;
+};
+
+__device__ __forceinline__ SourceS source_s(const DSource& s) {
+    SourceS r;
+    r.xi = ds_of(s.xi); r.eta = ds_of(s.eta); r.t0 = ds_of(s.t0); r.t_exp = ds_of(s.t_exp);
+    r.ref_x = ds_of(s.ref_x); r.ref_y = ds_of(s.ref_y);
+    r.zfac = (float)s.zfac; r.a = (float)s.a; r.b = (float)s.b; r.cpa = (float)s.cpa; r.spa = (float)s.spa;
+    r.kind = s.kind; r.sed = s.sed; r.table = s.table;
+    return r;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// sin and cos of 2 pi u for an exact uniform u: quadrant from v = 4u, phi = (v - k) pi / 2 in
+// [-pi/4, pi/4], then the Taylor series of sin and cos in x = phi^2 to x^7 (truncation below 1e-15), the
+// terms above x^4 in single precision and the rest as double-single.
+// ------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ds_sincos_2pi(ds u, ds& s, ds& c) {
+    const ds v = {u.hi * 4.f, u.lo * 4.f};
+    const float k = rintf(v.hi);
+    const ds f = v - k;
+    const ds phi = f * ds{1.5707963705062866f, -4.371138828673793e-08f};
+    const ds x = phi * phi;
+    const float xf = x.hi;
+    // sin(phi) / phi
+    const float ts = fmaf(xf, fmaf(xf, -7.647163609812713e-13f, 1.6059044372074283e-10f), -2.5052107943679403e-08f);
+    ds ps = dfma(x, ts, ds{2.7557318844628753e-06f, 3.793571224297229e-14f});
+    ps = dfma(x, ps, ds{-0.00019841270113829523f, 2.725596874933456e-12f});
+    ps = dfma(x, ps, ds{0.008333333767950535f, -4.34617203337595e-10f});
+    ps = dfma(x, ps, ds{-0.1666666716337204f, 4.967053879312289e-09f});
+    ps = dfma(x, ps, ds_f(1.f));
+    const ds sn = phi * ps;
+    // cos(phi)
+    const float tc = fmaf(xf, fmaf(xf, -1.147074536050896e-11f, 2.0876755879584152e-09f), -2.755731998149713e-07f);
+    ds pc = dfma(x, tc, ds{2.4801587642286904e-05f, -3.40699609366682e-13f});
+    pc = dfma(x, pc, ds{-0.0013888889225199819f, 3.3631094437103215e-11f});
+    pc = dfma(x, pc, ds{0.0416666679084301f, -1.2417634698280722e-09f});
+    pc = dfma(x, pc, ds_f(-0.5f));
+    const ds cs = dfma(x, pc, ds_f(1.f));
+    const int q = ((int)k) & 3;
+    if (q == 0) { s = sn; c = cs; }
+    else if (q == 1) { s = cs; c = -sn; }
+    else if (q == 2) { s = -sn; c = -cs; }
+    else { s = -cs; c = sn; }
+}
+
+// Sellmeier index (Sec. 2.4.1) of the single-precision wavelength, in double-single
+__device__ __forceinline__ ds sellmeier_ds(const DMaterial& m, float lam_nm) {
+    const ds lu = ds_f(lam_nm) * ds{0.0010000000474974513f, -4.7497450417210985e-11f};   // micrometres
+    const ds l2 = lu * lu;
+    ds n2 = ds_f(1.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n2 = n2 + m.Bs[i] * l2 / (l2 - m.Cs[i]);
+    return ds_sqrt(n2);
+}
+
+__device__ __forceinline__ void zern_eval_f(const float* __restrict__ zp, float u, float v, float& z, float& zu,
+                                            float& zv) {
+    float q[7], dq[7];
+    int off = 0;
+#pragma unroll
+    for (int b = 0; b <= 6; ++b) {
+        const int deg = 6 - b;
+        float acc = zp[off + deg], dacc = 0.f;
+#pragma unroll
+        for (int a = deg - 1; a >= 0; --a) {
+            dacc = fmaf(dacc, u, acc);
+            acc = fmaf(acc, u, zp[off + a]);
+        }
+        q[b] = acc;
+        dq[b] = dacc;
+        off += deg + 1;
+    }
+    float zz = q[6], zzu = dq[6], zzv = 0.f;
+#pragma unroll
+    for (int b = 5; b >= 0; --b) {
+        zzv = fmaf(zzv, v, zz);
+        zz = fmaf(zz, v, q[b]);
+        zzu = fmaf(zzu, v, dq[b]);
+    }
+    z = zz; zu = zzu; zv = zzv;
+}
+
+// Sag and slopes (Sec. 2.4.1).  The Zernike figure (tens of nanometres) is evaluated in single precision:
+// its absolute error is far below the 1e-8 mm the intersection resolves.
+__device__ __forceinline__ bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy) {
+    const ds r2 = dfma(x, x, y * y);
+    ds g = ds_f(0.f);
+    z = ds_f(0.f);
+    if (flags & SF_CONIC) {
+        const ds arg = ds_f(1.f) - E.k1c2 * r2;
+        if (arg.hi < 0.f) return false;
+        const ds rs = ds_rsqrt(arg);
+        z = E.c * r2 / dfma(arg, rs, ds_f(1.f));
+        g = E.c * rs;
+    }
+    if (flags & SF_EVEN) {
+        const ds u = r2 * E.inv_rn2;
+        const ds pe = dfma(dfma(dfma(E.ae[3], u, E.ae[2]), u, E.ae[1]), u, E.ae[0]);
+        z = dfma(u * u, pe, z);
+        const ds pd = dfma(dfma(dfma(E.aed[3], u, E.aed[2]), u, E.aed[1]), u, E.aed[0]);
+        g = dfma(u * E.inv_rn2, pd, g);
+    }
+    if (flags & SF_ODD) {
+        const ds rho = ds_sqrt(r2) * E.inv_rn;
+        const ds u = rho * rho;
+        const ds po = dfma(dfma(dfma(E.ao[3], u, E.ao[2]), u, E.ao[1]), u, E.ao[0]);
+        z = dfma(u * rho, po, z);
+        const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
+        g = dfma(rho * E.inv_rn2, pd, g);
+    }
+    zx = x * g;
+    zy = y * g;
+    if (flags & SF_ZERN) {
+        float zz, zu, zv;
+        zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
+        z = z + zz;
+        zx = zx + zu * E.zinv;
+        zy = zy + zv * E.zinv;
+    }
+    return true;
+}
+
+// Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
+// vertex branch, then Newton's method for the aspheric and Zernike terms until the step is below 1e-8 mm.
+// The Newton slope F'(l) only scales the step, so it is taken in single precision.
+__device__ __forceinline__ uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
+                                                 ds N[3]) {
+    if (flags & SF_FLAT_ONLY) {
+        if (d[2].hi == 0.f) return PHOSIM_LOST_MISSED;
+        l = -(p[2] / d[2]);
+        N[0] = ds_f(0.f); N[1] = ds_f(0.f); N[2] = ds_f(1.f);
+        return 0;
+    }
+    const ds A = dfma(E.kc * d[2], d[2], E.c * dfma(d[0], d[0], d[1] * d[1]));
+    const ds b = dfma(E.kc * p[2], d[2], E.c * dfma(p[0], d[0], p[1] * d[1])) - d[2];
+    const ds C = dfma(E.kc * p[2], p[2], E.c * dfma(p[0], p[0], p[1] * p[1])) - p[2] * 2.f;
+    const ds disc = dfma(b, b, -(A * C));
+    if (disc.hi < 0.f) return PHOSIM_LOST_MISSED;
+    const ds sq = ds_sqrt(disc);
+    const ds q = b.hi >= 0.f ? -(b + sq) : sq - b;
+    if (q.hi == 0.f) return PHOSIM_LOST_MISSED;
+    l = C / q;
+    if (A.hi != 0.f && (ds_f(1.f) - E.kc * dfma(l, d[2], p[2])).hi < 0.f) l = q / A;
+    if (!(flags & (SF_EVEN | SF_ODD | SF_ZERN))) {
+        const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]), z = dfma(l, d[2], p[2]);
+        const ds vx = -(E.c * x), vy = -(E.c * y), vz = ds_f(1.f) - E.kc * z;
+        const ds inv = ds_rsqrt(dfma(vx, vx, dfma(vy, vy, vz * vz)));
+        N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
+        return 0;
+    }
+    ds zx = ds_f(0.f), zy = ds_f(0.f);
+#pragma unroll 1
+    for (int it = 0; it < 20; ++it) {
+        const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]);
+        ds zs;
+        if (!sag_ds(E, flags, x, y, zs, zx, zy)) return PHOSIM_LOST_MISSED;
+        const ds F = dfma(l, d[2], p[2]) - zs;
+        const float dF = d[2].hi - zx.hi * d[0].hi - zy.hi * d[1].hi;
+        if (dF == 0.f) return PHOSIM_LOST_NEWTON;
+        const float step = F.hi * __fdividef(1.f, dF);
+        l = l - step;
+        if (fabsf(step) < 1e-8f) {
+            const ds inv = ds_rsqrt(dfma(zx, zx, dfma(zy, zy, ds_f(1.f))));
+            N[0] = -(zx * inv); N[1] = -(zy * inv); N[2] = inv;
+            return 0;
+        }
+    }
+    return PHOSIM_LOST_NEWTON;
+}
+
+__device__ __forceinline__ ds dot3(const ds a[3], const ds b[3]) { return dfma(a[0], b[0], dfma(a[1], b[1], a[2] * b[2])); }
+
+// Snell's law in vector form (Sec. 2.4.2), mu = n1 / n2; false on total internal reflection
+__device__ __forceinline__ bool refract_ds(ds d[3], ds N[3], ds mu) {
+    ds cosi = -dot3(d, N);
+    ds n0 = N[0], n1 = N[1], n2 = N[2];
+    if (cosi.hi < 0.f) { n0 = -n0; n1 = -n1; n2 = -n2; cosi = -cosi; }
+    const ds k = ds_f(1.f) - mu * mu * (ds_f(1.f) - cosi * cosi);
+    if (k.hi < 0.f) return false;
+    const ds a = mu * cosi - ds_sqrt(k);
+    d[0] = dfma(mu, d[0], a * n0);
+    d[1] = dfma(mu, d[1], a * n1);
+    d[2] = dfma(mu, d[2], a * n2);
+    return true;
+}
+
+__device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, const ds x[3], const ds d[3], ds p[3],
+                                              ds dl[3]) {
+    const ds rx = x[0] - E.o[0], ry = x[1] - E.o[1], rz = x[2] - E.o[2];
+    if (!(flags & SF_ROTATED)) {
+        p[0] = rx; p[1] = ry; p[2] = rz;
+        dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p[i] = dfma(E.M[3 * i], rx, dfma(E.M[3 * i + 1], ry, E.M[3 * i + 2] * rz));
+        dl[i] = dfma(E.M[3 * i], d[0], dfma(E.M[3 * i + 1], d[1], E.M[3 * i + 2] * d[2]));
+    }
+}
+
+__device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, const ds p[3], const ds dl[3], ds x[3],
+                                                ds d[3]) {
+    if (!(flags & SF_ROTATED)) {
+        x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1]; x[2] = p[2] + E.o[2];
+        d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        x[i] = dfma(E.M[i], p[0], dfma(E.M[3 + i], p[1], dfma(E.M[6 + i], p[2], E.o[i])));
+        d[i] = dfma(E.M[i], dl[0], dfma(E.M[3 + i], dl[1], E.M[6 + i] * dl[2]));
+    }
+}
+
+// the coating accept-reject: the draw (w + 1/2) 2^-32 < T exactly when w < ceil(T 2^32 - 1/2)
+__device__ __forceinline__ int coat_lambda_bin(const DCoating& C, float lam) {
+    int il = (int)floorf((lam - C.lam0f) * C.inv_dlamf);
+    return il < 0 ? 0 : (il > C.nl - 1 ? C.nl - 1 : il);
+}
+
+__device__ __forceinline__ float sample_wavelength_f(const TraceParams& P, const SourceS& s, const uint4& w0) {
+    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.n_bins - 1, w0.z);
+    const float lo = fmaf((float)bin, P.sed_dlamf, P.sed_lam0f);
+    return fmaf(u32of(w0.w), P.sed_dlamf, lo) * s.zfac;
+}
+
+// dynamic transmission (Sec. 3.2) on the single-precision wavelength, as early_coating_reject
+__device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, float lam, const uint4& w2, const uint4& w3) {
+#pragma unroll 1
+    for (int k = 0; k < P.n_coated; ++k) {
+        const int si = P.coated_surface[k];
+        const DCoating& C = P.coat[P.surf[si].coating];
+        const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
+        if (!((unsigned long long)w < __ldg(C.Tmax_thr + coat_lambda_bin(C, lam)))) return si;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int early_reject_surface_f(const TraceParams& P, const SourceS& s, int src, uint64_t i,
+                                                      float& lam) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+    lam = sample_wavelength_f(P, s, w0);
+    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    return early_coating_reject_f(P, lam, w2, w3);
+}
+
+// Surfaces in order (Sec. 2.4.2): the steps of optics<MIXED = true, FULL = true> in photon.cuh.
+__device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3], float lam, uint4 w1, uint4 w2,
+                                          uint4 w3, uint4 w4, PhotonOutS& R) {
+    ds n_cur = ds_f(1.f);
+    int glass_mat = -1;
+    ds glass_n = ds_f(1.f), glass_inv = ds_f(1.f);
+#pragma unroll 1
+    for (int si = 0; si < P.n_surf; ++si) {
+        const DSurface& S = P.surf[si];
+        const DSurfaceS& E = P.surf_s[si];
+        const int flags = S.flags;
+        ds p[3], dl[3];
+        to_surface_ds(E, flags, X, D, p, dl);
+        ds l, Nv[3];
+        const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
+        if (why) { R.flags = lost(why, si); return; }
+        p[0] = dfma(l, dl[0], p[0]);
+        p[1] = dfma(l, dl[1], p[1]);
+        p[2] = dfma(l, dl[2], p[2]);
+        if (S.kind == PHOSIM_DETECTOR) {
+            const ds hx = p[0] - P.xlo_s, hy = p[1] - P.ylo_s;
+            if (!(hx.hi >= 0.f && hy.hi >= 0.f && ds_lt(hx, P.chip_w_s) && ds_lt(hy, P.chip_h_s))) {
+                R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
+                return;
+            }
+            ds fx = p[0], fy = p[1];
+            R.xc = fx; R.yc = fy;
+            if (P.flags & PHOSIM_SENSOR) {
+                // refraction into the silicon, exponential conversion length (Sec. 2.4.2)
+                const float n_si = silicon_index_f(lam);
+                if (!refract_ds(dl, Nv, n_cur / ds_f(n_si))) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+                const float ell = lerp_table_f(P.ell32, P.n_ell, (lam - P.ell_lam0f) * P.inv_ell_dlamf);
+                const float L = ell * -logf(u32of(w1.w));
+                const float rf = (n_si - 1.f) / (n_si + 1.f);
+                float depth = L * fabsf(dl[2].hi);
+                if (!(depth <= P.t_sif)) {
+                    // back-side reflection: the photon turns round at the back and converts on its way back
+                    bool back = false;
+                    if ((P.flags & PHOSIM_BACK_REFLECT) && u32of(w4.z) < rf * rf) {
+                        depth = 2.f * P.t_sif - depth;
+                        back = depth >= 0.f;
+                    }
+                    if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
+                }
+                if (depth < P.dead_layerf) { R.flags = lost(PHOSIM_LOST_DEAD_LAYER, si); return; }
+                fx = dfma(dl[0], L, fx);
+                fy = dfma(dl[1], L, fy);
+                R.xc = fx; R.yc = fy;
+                // lateral Gaussian diffusion (Sec. 2.5)
+                const float sg = lerp_table_f(P.sig32, P.n_sig, depth * P.sig_scalef);
+                const float g = sqrtf(-2.f * logf(u32of(w2.x)));
+                float sn, cs;
+                sincospif(2.f * u32of(w2.y), &sn, &cs);
+                fx = fx + sg * g * cs;
+                fy = fy + sg * g * sn;
+            }
+            R.x = fx; R.y = fy;
+            const float px = ds_floor((fx - P.xlo_s) * P.inv_pixel_s), py = ds_floor((fy - P.ylo_s) * P.inv_pixel_s);
+            if (!(px >= 0.f && py >= 0.f && px < (float)P.nx && py < (float)P.ny)) {
+                R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
+                return;
+            }
+            R.pix = (int)py * P.nx + (int)px;
+            R.flags = PHOSIM_F_DETECTED;
+            return;
+        }
+        // clear aperture
+        const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
+        if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return; }
+        // coating accept-reject at the incidence angle and wavelength
+        if (S.coat_slot >= 0) {
+            const DCoating& C = P.coat[S.coating];
+            int it = 0;
+            if (C.nt > 1) {
+                const float cosi = fabsf(dl[0].hi * Nv[0].hi + dl[1].hi * Nv[1].hi + dl[2].hi * Nv[2].hi);
+                const float th = acosf(fminf(1.f, cosi));
+                it = (int)floorf((th - C.th0f) * C.inv_dthf);
+                it = it < 0 ? 0 : (it > C.nt - 1 ? C.nt - 1 : it);
+            }
+            const int k = S.coat_slot;
+            const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
+            if (!((unsigned long long)w < __ldg(C.T_thr + (size_t)coat_lambda_bin(C, lam) * C.nt + it))) {
+                R.flags = lost(PHOSIM_LOST_COATING, si);
+                return;
+            }
+        }
+        if (S.kind == PHOSIM_MIRROR) {
+            const ds dn2 = dot3(dl, Nv) * -2.f;
+            dl[0] = dfma(dn2, Nv[0], dl[0]);
+            dl[1] = dfma(dn2, Nv[1], dl[1]);
+            dl[2] = dfma(dn2, Nv[2], dl[2]);
+        } else {
+            const DMaterial& m = P.mat[S.material];
+            ds n_next = ds_f(1.f), inv_next = ds_f(1.f);
+            if (m.kind == PHOSIM_SELLMEIER) {
+                if (glass_mat != S.material) {
+                    glass_n = sellmeier_ds(m, lam);
+                    glass_inv = ds_rcp(glass_n);
+                    glass_mat = S.material;
+                }
+                n_next = glass_n;
+                inv_next = glass_inv;
+            } else if (m.kind == PHOSIM_SILICON) {
+                n_next = ds_f(silicon_index_f(lam));
+                inv_next = ds_rcp(n_next);
+            }
+            if (!refract_ds(dl, Nv, n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+            n_cur = n_next;
+        }
+        from_surface_ds(E, flags, p, dl, X, D);
+    }
+    R.flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
+}
+
+// Bilinear screen gradient (Sec. 2.3.2) at a double-single screen position; single-precision weights
+__device__ __forceinline__ void screen_gradient_ds(const DScale& S, ds sx, ds sy, float& gx, float& gy) {
+    const ds fx = sx * S.inv_pix_s, fy = sy * S.inv_pix_s;
+    const float flx = ds_floor(fx), fly = ds_floor(fy);
+    const int n = S.n;
+    const int ix = (int)flx, iy = (int)fly;
+    int i0, j0;
+    if ((n & (n - 1)) == 0) {
+        i0 = ix & (n - 1);
+        j0 = iy & (n - 1);
+    } else {
+        i0 = ix % n; i0 += i0 < 0 ? n : 0;
+        j0 = iy % n; j0 += j0 < 0 ? n : 0;
+    }
+    const size_t node = (size_t)j0 * n + i0;
+    const float tx = ds_frac(fx, flx), ty = ds_frac(fy, fly);
+    const float4 A = __ldg(S.g32 + 2 * node), B = __ldg(S.g32 + 2 * node + 1);
+    const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
+    gx += w00 * A.x + w10 * A.z + w01 * B.x + w11 * B.z;
+    gy += w00 * A.y + w10 * A.w + w01 * B.y + w11 * B.w;
+}
+
+// One photon from the top of the atmosphere to the pixel: the steps of trace_photon<MIXED = true>.
+__device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
+                                                PhotonOutS& R) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+    const uint4 w1 = philox(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
+    R.flags = 0; R.pix = -1;
+    R.x = R.y = R.xc = R.yc = ds_f(0.f);
+    // time stamp, wavelength (Sec. 2.2)
+    const ds t = dfma(s.t_exp, ds_uniform(w1.x), s.t0);
+    const float lam = sample_wavelength_f(P, s, w0);
+    R.lam = lam;
+    // direction with the paraxial shape offset (Sec. 2.2, 2.2.1)
+    ds nx = s.xi, ny = s.eta;
+    if (s.kind == PHOSIM_SERSIC) {
+        const float r = lerp_table_f(P.sersic32 + (size_t)s.table * P.sersic_K, P.sersic_K,
+                                     u32of(w1.y) * (float)P.sersic_K - 0.5f);
+        float sp, cp;
+        sincospif(2.f * u32of(w1.z), &sp, &cp);
+        const float dx = s.a * r * cp, dy = s.b * r * sp;
+        nx = nx + (dx * s.cpa - dy * s.spa);
+        ny = ny + (dx * s.spa + dy * s.cpa);
+    } else if (s.kind == PHOSIM_GAUSS) {
+        const float g = sqrtf(-2.f * logf(u32of(w1.y)));
+        float sp, cp;
+        sincospif(2.f * u32of(w1.z), &sp, &cp);
+        nx = nx + s.a * g * cp;
+        ny = ny + s.a * g * sp;
+    }
+    ds w = ds_f(1.f) - dfma(nx, nx, ny * ny);
+    ds rinv = ds_rsqrt(w);
+    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    if (P.flags & PHOSIM_EARLY_REJECT) {
+        const int si = early_coating_reject_f(P, lam, w2, w3);
+        if (si >= 0) { R.flags = lost(PHOSIM_LOST_COATING, si); return; }
+    }
+    // pupil point on the annulus, on the nominal first surface, moved back to the top of the atmosphere
+    const ds r = ds_sqrt(dfma(ds_uniform(w0.x), P.pr_dr2_s, P.pr_in2_s));
+    ds sp, cp;
+    ds_sincos_2pi(ds_uniform(w0.y), sp, cp);
+    ds x = r * cp, y = r * sp;
+    ds zs = ds_f(0.f), zx, zy;
+    sag_ds(P.pupil_s, P.pupil_surf.flags, x, y, zs, zx, zy);
+    ds z = P.pupil_z_s + zs;
+    {
+        const ds l = (P.h_top_s - z) * rinv;
+        x = x - nx * l;
+        y = y - ny * l;
+        z = P.h_top_s;
+    }
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
+    // frozen-flow layers top to bottom (Sec. 2.3)
+    if (P.flags & PHOSIM_ATMOSPHERE) {
+        const float kick = P.kick0f * exp2f(-0.2f * log2f(lam * P.inv_lam_ref_f));
+#pragma unroll 1
+        for (int k = 0; k < P.n_layers; ++k) {
+            const DLayer& L = P.layer[k];
+            const ds ll = (z - L.zs) * rinv;
+            x = dfma(nx, ll, x);
+            y = dfma(ny, ll, y);
+            z = L.zs;
+            const ds sx = x - L.vxs * t, sy = y - L.vys * t;
+            float gx = 0.f, gy = 0.f;
+#pragma unroll 1
+            for (int q = 0; q < L.n_scales; ++q) screen_gradient_ds(L.s[q], sx, sy, gx, gy);
+            nx = nx + kick * gx;
+            ny = ny + kick * gy;
+            w = ds_f(1.f) - dfma(nx, nx, ny * ny);
+            rinv = ds_rsqrt(w);
+        }
+        // second kick (Sec. 2.3.2) from the long-exposure PSF of the screens above kappa_crit
+        if (P.hf_K > 0) {
+            const float ang = lerp_table_f(P.hf32, P.hf_K, u32of(w4.x) * (float)P.hf_K - 0.5f) * (kick / P.kick0f);
+            float sa, ca;
+            sincospif(2.f * u32of(w4.y), &sa, &ca);
+            nx = nx + ang * ca;
+            ny = ny + ang * sa;
+            w = ds_f(1.f) - dfma(nx, nx, ny * ny);
+            rinv = ds_rsqrt(w);
+        }
+    }
+    const ds nz = -(w * rinv);
+    {
+        const ds l = (z - P.z_ent_s) * rinv;
+        x = dfma(nx, l, x);
+        y = dfma(ny, l, y);
+        z = P.z_ent_s;
+    }
+    ds X[3] = {x, y, z}, D[3] = {nx, ny, nz};
+    optics_ds(P, X, D, lam, w1, w2, w3, w4, R);
+}
+
+}  // namespace phosim

@@ -6,10 +6,12 @@
 // without imbalance; per-source moment sums are reduced over the tile in registers before one set of
 // atomics, and pixel increments are aggregated across the warp's lanes that hit the same pixel.
 #include <cstdio>
+#include <type_traits>
 
 #include "phosim_device.cuh"
 #include "phosim_scene.hpp"
 #include "photon.cuh"
+#include "photon_ds.cuh"
 
 namespace phosim {
 
@@ -33,14 +35,21 @@ struct TileAcc {
     float f1, f2, f3, f4, f5, c1, c2, c3, c4, c5;
 };
 
-// Account for one batch of up to 32 photons that went through trace_photon: record, image, moments and
-// the detected / dropped counters.  Every lane of the warp calls it.
-template <bool MIXED>
-__device__ __forceinline__ void consume(const TraceParams& P, const PhotonOut& R, bool valid, uint64_t rec_index,
-                                        double rx, double ry, int lane, TileAcc& A, unsigned long long* cnt) {
+// Account for one batch of up to 32 photons that went through a photon path: record, image, moments and
+// the detected / dropped counters.  Every lane of the warp calls it.  Out is PhotonOut (FP64 positions)
+// or PhotonOutS (double-single positions); ref is the source's chief-ray position in the same type.
+template <bool MIXED, class Out, class Ref>
+__device__ __forceinline__ void consume(const TraceParams& P, const Out& R, bool valid, uint64_t rec_index,
+                                        Ref rx, Ref ry, int lane, TileAcc& A, unsigned long long* cnt) {
+    constexpr bool DS = std::is_same<Out, PhotonOutS>::value;
     if (valid && P.records) {
         phosim_photon_record rec;
-        rec.x = R.x; rec.y = R.y; rec.xc = R.xc; rec.yc = R.yc; rec.lambda = R.lam;
+        if constexpr (DS) {
+            rec.x = ds_value(R.x); rec.y = ds_value(R.y); rec.xc = ds_value(R.xc); rec.yc = ds_value(R.yc);
+            rec.lambda = (double)R.lam;
+        } else {
+            rec.x = R.x; rec.y = R.y; rec.xc = R.xc; rec.yc = R.yc; rec.lambda = R.lam;
+        }
         rec.flags = R.flags; rec.pix = R.pix;
         P.records[rec_index] = rec;
     }
@@ -49,9 +58,15 @@ __device__ __forceinline__ void consume(const TraceParams& P, const PhotonOut& R
     if (det) {
         const unsigned same = __match_any_sync(dmask, R.pix);
         if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
-        const double dx = R.x - rx, dy = R.y - ry;
         if constexpr (MIXED) {
-            const float fx = (float)dx, fy = (float)dy;
+            float fx, fy;
+            if constexpr (DS) {
+                fx = (R.x - rx).hi;
+                fy = (R.y - ry).hi;
+            } else {
+                fx = (float)(R.x - rx);
+                fy = (float)(R.y - ry);
+            }
             kahan_add(A.f1, A.c1, fx);
             kahan_add(A.f2, A.c2, fy);
             kahan_add(A.f3, A.c3, fx * fx);
@@ -59,6 +74,7 @@ __device__ __forceinline__ void consume(const TraceParams& P, const PhotonOut& R
             kahan_add(A.f5, A.c5, fy * fy);
             A.m0 += 1.0;
         } else {
+            const double dx = R.x - rx, dy = R.y - ry;
             A.m0 += 1.0; A.m1 += dx; A.m2 += dy; A.m3 += dx * dx; A.m4 += dx * dy; A.m5 += dy * dy;
         }
     }
@@ -73,8 +89,15 @@ __device__ __forceinline__ void consume(const TraceParams& P, const PhotonOut& R
 
 constexpr int kWarpsPerBlock = 8;
 
-template <bool MIXED>
+// MODE: kPlain (every step FP64), kMixed (FP64 optics, FP32 sampling / deflections / sensor), kDS (the
+// mixed path with the FP64 parts in double-single arithmetic on the FP32 pipes)
+constexpr int kPlain = 0, kMixed = 1, kDS = 2;
+
+template <int MODE>
 __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ TraceParams P) {
+    constexpr bool MIXED = MODE != kPlain;
+    constexpr bool DS = MODE == kDS;
+    using Out = typename std::conditional<DS, PhotonOutS, PhotonOut>::type;
     // With early rejection most photons stop after their wavelength is drawn.  Survivors are queued per
     // warp (photon offsets within the tile, in shared memory) and propagated 32 at a time, so the expensive
     // part runs with full warps instead of the few lanes that survived in each batch.
@@ -97,7 +120,10 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ T
         const uint64_t off = j * P.tile_photons;
         const uint32_t count = (uint32_t)min((uint64_t)P.tile_photons, s.count - off);
         const uint64_t first = s.first + off, rec_base = s.rec_off + off;
-        const double rx = s.ref_x, ry = s.ref_y;
+        SourceS ss;
+        if constexpr (DS) ss = source_s(s);
+        const auto rx = [&] { if constexpr (DS) return ss.ref_x; else return s.ref_x; }();
+        const auto ry = [&] { if constexpr (DS) return ss.ref_y; else return s.ref_y; }();
         TileAcc A = {};
         int queued = 0;
         uint32_t base = 0;
@@ -110,12 +136,22 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ T
                 bool go_on = valid;
                 if (early) {
                     // stage 1: the early coating decision alone
-                    double lam = 0.0;
-                    const int rej = valid ? early_reject_surface<MIXED>(P, s, src, first + k, lam) : -1;
+                    Out R;
+                    int rej = -1;
+                    if constexpr (DS) {
+                        float lam = 0.f;
+                        if (valid) rej = early_reject_surface_f(P, ss, src, first + k, lam);
+                        R.x = R.y = R.xc = R.yc = ds_f(0.f);
+                        R.lam = lam;
+                    } else {
+                        double lam = 0.0;
+                        if (valid) rej = early_reject_surface<MIXED>(P, s, src, first + k, lam);
+                        R.x = R.y = R.xc = R.yc = 0.0;
+                        R.lam = lam;
+                    }
                     go_on = valid && rej < 0;
-                    PhotonOut R;
                     R.flags = valid ? lost(PHOSIM_LOST_COATING, rej) : 0u;
-                    R.pix = -1; R.x = R.y = R.xc = R.yc = 0.0; R.lam = lam;
+                    R.pix = -1;
                     consume<MIXED>(P, R, valid && !go_on, rec_base + k, rx, ry, lane, A, cnt);
                 }
                 // queue the photons that go on
@@ -133,9 +169,12 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ T
                 const bool v = lane < take;
                 const uint32_t kk = v ? queue[queued + lane] : 0u;
                 __syncwarp();
-                PhotonOut Q;
+                Out Q;
                 Q.flags = 0; Q.pix = -1;
-                if (v) trace_photon<MIXED>(P, s, src, first + kk, Q);
+                if (v) {
+                    if constexpr (DS) trace_photon_ds(P, ss, src, first + kk, Q);
+                    else trace_photon<MIXED>(P, s, src, first + kk, Q);
+                }
                 consume<MIXED>(P, Q, v, rec_base + kk, rx, ry, lane, A, cnt);
             }
             if (drained && queued == 0) break;
@@ -189,20 +228,21 @@ cudaError_t launch_chief_rays(const TraceParams& P, DSource* sources, int n_src,
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const TraceParams& P, bool mixed, int blocks, int threads, cudaStream_t st) {
-    if (mixed) trace_kernel<true><<<blocks, threads, 0, st>>>(P);
-    else trace_kernel<false><<<blocks, threads, 0, st>>>(P);
+cudaError_t launch_trace(const TraceParams& P, int mode, int blocks, int threads, cudaStream_t st) {
+    if (mode == kDS) trace_kernel<kDS><<<blocks, threads, 0, st>>>(P);
+    else if (mode == kMixed) trace_kernel<kMixed><<<blocks, threads, 0, st>>>(P);
+    else trace_kernel<kPlain><<<blocks, threads, 0, st>>>(P);
     return cudaGetLastError();
 }
 
-const void* trace_kernel_ptr(bool mixed) {
-    return mixed ? (const void*)trace_kernel<true> : (const void*)trace_kernel<false>;
+const void* trace_kernel_ptr(int mode) {
+    if (mode == kDS) return (const void*)trace_kernel<kDS>;
+    return mode == kMixed ? (const void*)trace_kernel<kMixed> : (const void*)trace_kernel<kPlain>;
 }
 const void* chief_kernel_ptr() { return (const void*)chief_ray_kernel; }
 
-cudaError_t trace_occupancy(bool mixed, int threads, int* blocks_per_sm) {
-    if (mixed) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<true>, threads, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<false>, threads, 0);
+cudaError_t trace_occupancy(int mode, int threads, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel_ptr(mode), threads, 0);
 }
 
 }  // namespace phosim

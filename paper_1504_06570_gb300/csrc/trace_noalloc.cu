@@ -64,9 +64,9 @@ extern "C" phosim_status phosim_trace_noalloc(phosim_scene* sc, const phosim_sou
     phosim_status st = scratch_address(&base);
     if (st != PHOSIM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool mixed = sc->precision == PHOSIM_MIXED;
+    const int mode = sc->precision;
     int per_sm = 0;
-    if (trace_occupancy(mixed, sc->threads, &per_sm) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    if (trace_occupancy(mode, sc->threads, &per_sm) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
     per_sm = std::max(per_sm, 1);
     const int blocks = sc->sm_count * per_sm;
     const uint64_t warps = (uint64_t)blocks * (sc->threads / 32);
@@ -123,7 +123,7 @@ extern "C" phosim_status phosim_trace_noalloc(phosim_scene* sc, const phosim_sou
     P.moments = moments;
     P.records = records;
     if (launch_chief_rays(P, d_src, n_src, moments, s) != cudaSuccess ||
-        launch_trace(P, mixed, blocks, sc->threads, s) != cudaSuccess) {
+        launch_trace(P, mode, blocks, sc->threads, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return PHOSIM_ERR_CUDA;
     }

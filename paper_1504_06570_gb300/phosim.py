@@ -17,7 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_lib", "libphosim.so")
 
 MAX_SURFACES, MAX_LAYERS, MAX_SCALES, MAX_ZERNIKE = 16, 8, 2, 28
-PLAIN_FP64, MIXED = 0, 1
+PLAIN_FP64, MIXED, MIXED_DS = 0, 1, 2
 ATMOSPHERE, SENSOR, EARLY_REJECT, GRAPH, BACK_REFLECT = 1, 2, 4, 8, 16
 MOMENT_WORDS = 8
 F_DETECTED = 1

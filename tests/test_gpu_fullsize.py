@@ -18,12 +18,12 @@ def scene():
     return I.three_mirror_scene()
 
 
-@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED])
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED, P.MIXED_DS])
 def test_full_size_sampled_parity(oracle_mod, scene, precision):
     sc = scene
     counts = sc.sources.n_photons
     n = int(counts.sum())
-    s = P.Scene(sc, precision, early_reject=True, graph=(precision == P.MIXED))
+    s = P.Scene(sc, precision, early_reject=True, graph=(precision != P.PLAIN_FP64))
     d = sc.detector
     img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
     rec = torch.zeros(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
