@@ -13,6 +13,12 @@
 
 #include <cuda_runtime.h>
 
+// attributes of the larger primitives (quotient, roots): out of line keeps the photon kernel's code within
+// the instruction cache
+#ifndef PHOSIM_DS_HEAVY
+#define PHOSIM_DS_HEAVY __noinline__
+#endif
+
 namespace phosim {
 
 struct ds {
@@ -95,13 +101,13 @@ __device__ __forceinline__ ds dfma(ds a, float b, ds c) {
 
 // Quotient: a single-precision reciprocal estimate r, q1 = a r, then one correction from the remainder
 // a - q1 b evaluated in double-single; relative error about 2^-45.
-__device__ __forceinline__ ds operator/(ds a, ds b) {
+static __device__ PHOSIM_DS_HEAVY ds operator/(ds a, ds b) {
     const float r = __fdividef(1.f, b.hi);
     const float q1 = __fmul_rn(a.hi, r);
     const ds rem = a - b * q1;
     return fast_two_sum(q1, __fmul_rn(rem.hi, r));
 }
-__device__ __forceinline__ ds ds_rcp(ds b) {
+static __device__ PHOSIM_DS_HEAVY ds ds_rcp(ds b) {
     const float r = __fdividef(1.f, b.hi);
     const ds rem = ds_f(1.f) - b * r;         // 1 - b r, small
     return fast_two_sum(r, __fmul_rn(rem.hi, r));
@@ -109,7 +115,7 @@ __device__ __forceinline__ ds ds_rcp(ds b) {
 
 // Square root: y = a rsqrt(a) in single precision, then the Newton correction (a - y^2) / (2 y) with the
 // residual exact (two_prod); relative error about 2^-44.  Non-positive arguments give 0.
-__device__ __forceinline__ ds ds_sqrt(ds a) {
+static __device__ PHOSIM_DS_HEAVY ds ds_sqrt(ds a) {
     if (!(a.hi > 0.f)) return {0.f, 0.f};
     const float r = rsqrtf(a.hi);
     const float y = __fmul_rn(a.hi, r);
@@ -119,7 +125,7 @@ __device__ __forceinline__ ds ds_sqrt(ds a) {
 
 // Reciprocal square root: r0 = rsqrt(a.hi), e = 1 - a r0^2 evaluated in double-single, then the second-
 // order Taylor correction r0 (1 + e / 2 + 3 e^2 / 8); relative error at the double-single rounding level.
-__device__ __forceinline__ ds ds_rsqrt(ds a) {
+static __device__ PHOSIM_DS_HEAVY ds ds_rsqrt(ds a) {
     const float r = rsqrtf(a.hi);
     const ds ar2 = a * two_prod(r, r);
     const float e = __fsub_rn(__fsub_rn(1.f, ar2.hi), ar2.lo);

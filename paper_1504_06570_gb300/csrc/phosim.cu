@@ -261,6 +261,22 @@ __global__ void sed_threshold_kernel(const double* __restrict__ flux, int n_sed,
     }
 }
 
+// guide table of each SED's thresholds: guide[j] = the number of thresholds <= j 2^24, j = 0..kSedGuide
+__global__ void sed_guide_kernel(const unsigned long long* __restrict__ thr, int n_sed, int n, int* guide) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (j > kSedGuide || s >= n_sed) return;
+    const unsigned long long* t = thr + (size_t)s * n;
+    const unsigned long long v = (unsigned long long)j << 24;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v < t[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    guide[(size_t)s * (kSedGuide + 1) + j] = lo;
+}
+
 void destroy_graph(TraceGraph& g) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
@@ -611,17 +627,26 @@ phosim_status phosim_load_seds(phosim_scene* sc, const double* flux, int n_sed, 
         sed_threshold_kernel<<<(n_sed + 127) / 128, 128>>>(d_flux, n_sed, n_bins, lam0, dlam, d_cum, d_thr);
         e = cudaGetLastError();
     }
+    int* d_guide = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_guide, (size_t)n_sed * (kSedGuide + 1) * sizeof(int));
+    if (e == cudaSuccess) {
+        sed_guide_kernel<<<dim3((kSedGuide + 1 + 127) / 128, n_sed), 128>>>(d_thr, n_sed, n_bins - 1, d_guide);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_flux);
     cudaFree(d_cum);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         cudaFree(d_thr);
+        cudaFree(d_guide);
         return e == cudaErrorMemoryAllocation ? PHOSIM_ERR_OUT_OF_MEMORY : PHOSIM_ERR_CUDA;
     }
     free_all(sc->sed_mem);
     sc->sed_mem.push_back(d_thr);
+    sc->sed_mem.push_back(d_guide);
     sc->base.thr = d_thr;
+    sc->base.sed_guide = d_guide;
     sc->base.n_bins = n_bins;
     sc->base.sed_lam0 = lam0;
     sc->base.sed_dlam = dlam;

@@ -17,6 +17,7 @@ namespace phosim {
 constexpr int kMaxMaterials = 8;
 constexpr int kMaxCoatings = 8;
 constexpr int kZPoly = 28;                 // monomials x^a y^b, a + b <= 6
+constexpr int kSedGuide = 256;             // guide-table buckets of the wavelength-bin draw (its top 8 bits)
 
 enum SurfFlags : int { SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FLAT_ONLY = 16, SF_ROTATED = 32 };
 
@@ -123,6 +124,7 @@ struct TraceParams {
     int n_bins, sersic_K;
     double sed_lam0, sed_dlam;
     const unsigned long long* thr;            // n_sed x (n_bins - 1) integer thresholds on the bin draw
+    const int* sed_guide;                     // n_sed x (kSedGuide + 1): first threshold above j 2^24
     const double* sersic;
     const float* sersic32;
     int hf_K;                                 // quantiles of the high-frequency kick (0 = none)

@@ -23,9 +23,13 @@ __device__ __forceinline__ uint32_t word(const uint4& w, int k) {
 }
 
 // Wavelength bin (Sec. 2.2): the first bin whose cumulative photon probability exceeds the draw, decided
-// on the integer draw against thresholds precomputed from the FP64 cumulative table.
-__device__ __forceinline__ int sed_bin(const unsigned long long* __restrict__ thr, int n, uint32_t w) {
-    int lo = 0, hi = n;   // thresholds thr[0..n-1]; answer in [0, n]
+// on the integer draw against thresholds precomputed from the FP64 cumulative table.  A guide table (Chen and
+// Asau's indexed search) narrows the search to the thresholds between guide[j] and guide[j + 1] for the draw's
+// top byte j: every threshold below guide[j] is at most j 2^24 <= w, and the one at guide[j + 1] exceeds
+// (j + 1) 2^24 > w, so the answer lies in that range and is the plain search's answer.
+__device__ __forceinline__ int sed_bin(const unsigned long long* __restrict__ thr, const int* __restrict__ guide, uint32_t w) {
+    const int j = (int)(w >> 24);
+    int lo = __ldg(guide + j), hi = __ldg(guide + j + 1);
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if ((unsigned long long)w < __ldg(thr + mid)) hi = mid;
@@ -236,7 +240,7 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
 // Wavelength (Sec. 2.2): cumulative photon-number table, blur within the bin, redshift.
 template <bool MIXED>
 __device__ __forceinline__ double sample_wavelength(const TraceParams& P, const DSource& s, const uint4& w0) {
-    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.n_bins - 1, w0.z);
+    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.sed_guide + (size_t)s.sed * (kSedGuide + 1), w0.z);
     if constexpr (MIXED) {
         const float lo = (float)(P.sed_lam0 + bin * P.sed_dlam);
         return (double)(fmaf(u32of(w0.w), (float)P.sed_dlam, lo) * (float)s.zfac);

@@ -11,7 +11,20 @@
 
 #include "photon.cuh"
 
+#ifndef PHOSIM_DS_SAG
+#define PHOSIM_DS_SAG __noinline__
+#endif
+#ifndef PHOSIM_DS_PHILOX
+#define PHOSIM_DS_PHILOX __noinline__
+#endif
+#ifndef PHOSIM_DS_STEP
+#define PHOSIM_DS_STEP __noinline__
+#endif
+
 namespace phosim {
+
+// one out-of-line copy of the generator for the double-single path (the FP64 kernels inline it)
+static __device__ PHOSIM_DS_PHILOX uint4 philox_ds(uint4 c, uint32_t k0, uint32_t k1) { return philox(c, k0, k1); }
 
 struct PhotonOutS {
     ds x, y, xc, yc;
@@ -41,7 +54,7 @@ __device__ __forceinline__ SourceS source_s(const DSource& s) {
 // [-pi/4, pi/4], then the Taylor series of sin and cos in x = phi^2 to x^7 (truncation below 1e-15), the
 // terms above x^4 in single precision and the rest as double-single.
 // ------------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void ds_sincos_2pi(ds u, ds& s, ds& c) {
+static __device__ PHOSIM_DS_STEP void ds_sincos_2pi(ds u, ds& s, ds& c) {
     const ds v = {u.hi * 4.f, u.lo * 4.f};
     const float k = rintf(v.hi);
     const ds f = v - k;
@@ -71,7 +84,7 @@ __device__ __forceinline__ void ds_sincos_2pi(ds u, ds& s, ds& c) {
 }
 
 // Sellmeier index (Sec. 2.4.1) of the single-precision wavelength, in double-single
-__device__ __forceinline__ ds sellmeier_ds(const DMaterial& m, float lam_nm) {
+static __device__ PHOSIM_DS_STEP ds sellmeier_ds(const DMaterial& m, float lam_nm) {
     const ds lu = ds_f(lam_nm) * ds{0.0010000000474974513f, -4.7497450417210985e-11f};   // micrometres
     const ds l2 = lu * lu;
     ds n2 = ds_f(1.f);
@@ -109,7 +122,7 @@ __device__ __forceinline__ void zern_eval_f(const float* __restrict__ zp, float 
 
 // Sag and slopes (Sec. 2.4.1).  The Zernike figure (tens of nanometres) is evaluated in single precision:
 // its absolute error is far below the 1e-8 mm the intersection resolves.
-__device__ __forceinline__ bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy) {
+static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy) {
     const ds r2 = dfma(x, x, y * y);
     ds g = ds_f(0.f);
     z = ds_f(0.f);
@@ -150,7 +163,7 @@ __device__ __forceinline__ bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y
 // Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
 // vertex branch, then Newton's method for the aspheric and Zernike terms until the step is below 1e-8 mm.
 // The Newton slope F'(l) only scales the step, so it is taken in single precision.
-__device__ __forceinline__ uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
+static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
                                                  ds N[3]) {
     if (flags & SF_FLAT_ONLY) {
         if (d[2].hi == 0.f) return PHOSIM_LOST_MISSED;
@@ -198,7 +211,7 @@ __device__ __forceinline__ uint32_t intersect_ds(const DSurfaceS& E, int flags, 
 __device__ __forceinline__ ds dot3(const ds a[3], const ds b[3]) { return dfma(a[0], b[0], dfma(a[1], b[1], a[2] * b[2])); }
 
 // Snell's law in vector form (Sec. 2.4.2), mu = n1 / n2; false on total internal reflection
-__device__ __forceinline__ bool refract_ds(ds d[3], ds N[3], ds mu) {
+static __device__ PHOSIM_DS_STEP bool refract_ds(ds d[3], ds N[3], ds mu) {
     ds cosi = -dot3(d, N);
     ds n0 = N[0], n1 = N[1], n2 = N[2];
     if (cosi.hi < 0.f) { n0 = -n0; n1 = -n1; n2 = -n2; cosi = -cosi; }
@@ -247,7 +260,7 @@ __device__ __forceinline__ int coat_lambda_bin(const DCoating& C, float lam) {
 }
 
 __device__ __forceinline__ float sample_wavelength_f(const TraceParams& P, const SourceS& s, const uint4& w0) {
-    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.n_bins - 1, w0.z);
+    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.sed_guide + (size_t)s.sed * (kSedGuide + 1), w0.z);
     const float lo = fmaf((float)bin, P.sed_dlamf, P.sed_lam0f);
     return fmaf(u32of(w0.w), P.sed_dlamf, lo) * s.zfac;
 }
@@ -267,11 +280,11 @@ __device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, floa
 __device__ __forceinline__ int early_reject_surface_f(const TraceParams& P, const SourceS& s, int src, uint64_t i,
                                                       float& lam) {
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
-    const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+    const uint4 w0 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
     lam = sample_wavelength_f(P, s, w0);
-    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    const uint4 w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
     uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
     return early_coating_reject_f(P, lam, w2, w3);
 }
 
@@ -415,8 +428,8 @@ __device__ __forceinline__ void screen_gradient_ds(const DScale& S, ds sx, ds sy
 __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
                                                 PhotonOutS& R) {
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
-    const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
-    const uint4 w1 = philox(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
+    const uint4 w0 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+    const uint4 w1 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
     R.flags = 0; R.pix = -1;
     R.x = R.y = R.xc = R.yc = ds_f(0.f);
     // time stamp, wavelength (Sec. 2.2)
@@ -442,9 +455,9 @@ __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const Sour
     }
     ds w = ds_f(1.f) - dfma(nx, nx, ny * ny);
     ds rinv = ds_rsqrt(w);
-    const uint4 w2 = philox(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    const uint4 w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
     uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.n_coated > 2) w3 = philox(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
     if (P.flags & PHOSIM_EARLY_REJECT) {
         const int si = early_coating_reject_f(P, lam, w2, w3);
         if (si >= 0) { R.flags = lost(PHOSIM_LOST_COATING, si); return; }
@@ -464,7 +477,7 @@ __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const Sour
         z = P.h_top_s;
     }
     uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
+    if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
     // frozen-flow layers top to bottom (Sec. 2.3)
     if (P.flags & PHOSIM_ATMOSPHERE) {
         const float kick = P.kick0f * exp2f(-0.2f * log2f(lam * P.inv_lam_ref_f));

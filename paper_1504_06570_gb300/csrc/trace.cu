@@ -28,19 +28,36 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Per-warp accumulation state of one tile: moment partials (FP64 in the plain path; FP32 with Kahan
-// compensation in the mixed path) and, in lane 0, the launch counters.
-struct TileAcc {
-    double m0, m1, m2, m3, m4, m5;
-    float f1, f2, f3, f4, f5, c1, c2, c3, c4, c5;
+// Per-lane accumulation state of one tile: the count of detected photons and the moment partials about the
+// source's chief-ray position (FP64 in the plain path; FP32 with Kahan compensation in the mixed paths).
+template <bool MIXED> struct TileAcc {
+    uint32_t n;
+    double m[5];
+};
+template <> struct TileAcc<true> {
+    uint32_t n;
+    float f[5], c[5];
 };
 
+#ifndef PHOSIM_CONSUME
+#define PHOSIM_CONSUME __forceinline__
+#endif
+// resident blocks of 256 threads per SM the register allocation is sized for: the FP64 kernels are bound by
+// the FP64 pipe, the double-single kernel by latency (more resident warps hide its dependent FP32 chains)
+#ifndef PHOSIM_TRACE_MIN_BLOCKS
+#define PHOSIM_TRACE_MIN_BLOCKS 2
+#endif
+#ifndef PHOSIM_TRACE_MIN_BLOCKS_DS
+#define PHOSIM_TRACE_MIN_BLOCKS_DS 8
+#endif
+
 // Account for one batch of up to 32 photons that went through a photon path: record, image, moments and
-// the detected / dropped counters.  Every lane of the warp calls it.  Out is PhotonOut (FP64 positions)
-// or PhotonOutS (double-single positions); ref is the source's chief-ray position in the same type.
+// the detected / dropped counters (cnt: the warp's counters in shared memory, updated by lane 0).  Every
+// lane of the warp calls it.  Out is PhotonOut (FP64 positions) or PhotonOutS (double-single positions);
+// rx, ry are the source's chief-ray position in the same type.
 template <bool MIXED, class Out, class Ref>
-__device__ __forceinline__ void consume(const TraceParams& P, const Out& R, bool valid, uint64_t rec_index,
-                                        Ref rx, Ref ry, int lane, TileAcc& A, unsigned long long* cnt) {
+__device__ PHOSIM_CONSUME void consume(const TraceParams& P, const Out& R, bool valid, uint64_t rec_index,
+                                        Ref rx, Ref ry, int lane, TileAcc<MIXED>& A, unsigned long long* cnt) {
     constexpr bool DS = std::is_same<Out, PhotonOutS>::value;
     if (valid && P.records) {
         phosim_photon_record rec;
@@ -58,6 +75,7 @@ __device__ __forceinline__ void consume(const TraceParams& P, const Out& R, bool
     if (det) {
         const unsigned same = __match_any_sync(dmask, R.pix);
         if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
+        A.n += 1;
         if constexpr (MIXED) {
             float fx, fy;
             if constexpr (DS) {
@@ -67,15 +85,14 @@ __device__ __forceinline__ void consume(const TraceParams& P, const Out& R, bool
                 fx = (float)(R.x - rx);
                 fy = (float)(R.y - ry);
             }
-            kahan_add(A.f1, A.c1, fx);
-            kahan_add(A.f2, A.c2, fy);
-            kahan_add(A.f3, A.c3, fx * fx);
-            kahan_add(A.f4, A.c4, fx * fy);
-            kahan_add(A.f5, A.c5, fy * fy);
-            A.m0 += 1.0;
+            kahan_add(A.f[0], A.c[0], fx);
+            kahan_add(A.f[1], A.c[1], fy);
+            kahan_add(A.f[2], A.c[2], fx * fx);
+            kahan_add(A.f[3], A.c[3], fx * fy);
+            kahan_add(A.f[4], A.c[4], fy * fy);
         } else {
             const double dx = R.x - rx, dy = R.y - ry;
-            A.m0 += 1.0; A.m1 += dx; A.m2 += dy; A.m3 += dx * dx; A.m4 += dx * dy; A.m5 += dy * dy;
+            A.m[0] += dx; A.m[1] += dy; A.m[2] += dx * dx; A.m[3] += dx * dy; A.m[4] += dy * dy;
         }
     }
     if (lane == 0) cnt[1] += __popc(dmask);
@@ -92,23 +109,28 @@ constexpr int kWarpsPerBlock = 8;
 // MODE: kPlain (every step FP64), kMixed (FP64 optics, FP32 sampling / deflections / sensor), kDS (the
 // mixed path with the FP64 parts in double-single arithmetic on the FP32 pipes)
 constexpr int kPlain = 0, kMixed = 1, kDS = 2;
+constexpr int min_blocks(int mode) { return mode == kDS ? PHOSIM_TRACE_MIN_BLOCKS_DS : PHOSIM_TRACE_MIN_BLOCKS; }
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ TraceParams P) {
+__global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __grid_constant__ TraceParams P) {
     constexpr bool MIXED = MODE != kPlain;
     constexpr bool DS = MODE == kDS;
     using Out = typename std::conditional<DS, PhotonOutS, PhotonOut>::type;
     // With early rejection most photons stop after their wavelength is drawn.  Survivors are queued per
     // warp (photon offsets within the tile, in shared memory) and propagated 32 at a time, so the expensive
-    // part runs with full warps instead of the few lanes that survived in each batch.
+    // part runs with full warps instead of the few lanes that survived in each batch.  Lane-uniform state
+    // (the launch counters, the double-single source constants) also lives in shared memory, which leaves
+    // the registers to the photon path.
     __shared__ uint32_t queue_mem[kWarpsPerBlock][64];
-    const int lane = threadIdx.x & 31;
-    uint32_t* queue = queue_mem[threadIdx.x >> 5];
+    __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
+    __shared__ SourceS src_mem[DS ? kWarpsPerBlock : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* queue = queue_mem[warp];
+    unsigned long long* cnt = cnt_mem[warp];
     const unsigned lanes_below = (1u << lane) - 1u;
     const bool early = (P.flags & PHOSIM_EARLY_REJECT) != 0;
-    unsigned long long cnt[kNumCounters];
-#pragma unroll
-    for (int k = 0; k < kNumCounters; ++k) cnt[k] = 0;
+    if (lane < kNumCounters) cnt[lane] = 0;
+    __syncwarp();
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(P.tile_counter, 1ull);
@@ -120,11 +142,12 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ T
         const uint64_t off = j * P.tile_photons;
         const uint32_t count = (uint32_t)min((uint64_t)P.tile_photons, s.count - off);
         const uint64_t first = s.first + off, rec_base = s.rec_off + off;
-        SourceS ss;
-        if constexpr (DS) ss = source_s(s);
-        const auto rx = [&] { if constexpr (DS) return ss.ref_x; else return s.ref_x; }();
-        const auto ry = [&] { if constexpr (DS) return ss.ref_y; else return s.ref_y; }();
-        TileAcc A = {};
+        if constexpr (DS) {
+            if (lane == 0) src_mem[warp] = source_s(s);
+            __syncwarp();
+        }
+        const SourceS& ss = src_mem[DS ? warp : 0];
+        TileAcc<MIXED> A = {};
         int queued = 0;
         uint32_t base = 0;
         for (;;) {
@@ -152,7 +175,8 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ T
                     go_on = valid && rej < 0;
                     R.flags = valid ? lost(PHOSIM_LOST_COATING, rej) : 0u;
                     R.pix = -1;
-                    consume<MIXED>(P, R, valid && !go_on, rec_base + k, rx, ry, lane, A, cnt);
+                    if constexpr (DS) consume<MIXED>(P, R, valid && !go_on, rec_base + k, ss.ref_x, ss.ref_y, lane, A, cnt);
+                    else consume<MIXED>(P, R, valid && !go_on, rec_base + k, s.ref_x, s.ref_y, lane, A, cnt);
                 }
                 // queue the photons that go on
                 const unsigned gmask = __ballot_sync(0xffffffffu, go_on);
@@ -171,33 +195,36 @@ __global__ void __launch_bounds__(256, 2) trace_kernel(const __grid_constant__ T
                 __syncwarp();
                 Out Q;
                 Q.flags = 0; Q.pix = -1;
-                if (v) {
-                    if constexpr (DS) trace_photon_ds(P, ss, src, first + kk, Q);
-                    else trace_photon<MIXED>(P, s, src, first + kk, Q);
+                if constexpr (DS) {
+                    if (v) trace_photon_ds(P, ss, src, first + kk, Q);
+                    consume<MIXED>(P, Q, v, rec_base + kk, ss.ref_x, ss.ref_y, lane, A, cnt);
+                } else {
+                    if (v) trace_photon<MIXED>(P, s, src, first + kk, Q);
+                    consume<MIXED>(P, Q, v, rec_base + kk, s.ref_x, s.ref_y, lane, A, cnt);
                 }
-                consume<MIXED>(P, Q, v, rec_base + kk, rx, ry, lane, A, cnt);
             }
             if (drained && queued == 0) break;
         }
-        if constexpr (MIXED) {
-            A.m1 = (double)A.f1 - (double)A.c1; A.m2 = (double)A.f2 - (double)A.c2; A.m3 = (double)A.f3 - (double)A.c3;
-            A.m4 = (double)A.f4 - (double)A.c4; A.m5 = (double)A.f5 - (double)A.c5;
-        }
         if (P.moments) {
-            const double m0 = warp_sum(A.m0), m1 = warp_sum(A.m1), m2 = warp_sum(A.m2);
-            const double m3 = warp_sum(A.m3), m4 = warp_sum(A.m4), m5 = warp_sum(A.m5);
+            double m[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if constexpr (MIXED) m[q] = (double)A.f[q] - (double)A.c[q];
+                else m[q] = A.m[q];
+                m[q] = warp_sum(m[q]);
+            }
+            const double m0 = warp_sum((double)A.n);
             if (lane == 0 && m0 > 0.0) {
                 double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
-                atomicAdd(M + 0, m0); atomicAdd(M + 1, m1); atomicAdd(M + 2, m2);
-                atomicAdd(M + 3, m3); atomicAdd(M + 4, m4); atomicAdd(M + 5, m5);
+                atomicAdd(M + 0, m0);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) atomicAdd(M + 1 + q, m[q]);
             }
         }
+        __syncwarp();
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < kNumCounters; ++k)
-            if (cnt[k]) atomicAdd(P.counters + k, cnt[k]);
-    }
+    __syncwarp();
+    if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
 }
 
 // Chief ray of each source (pupil centre, source centre direction, lambda_ref, no apertures): the
