@@ -41,6 +41,7 @@ typedef int phosim_status;
 #define PHOSIM_MAX_SCALES 2
 #define PHOSIM_MAX_ZERNIKE 28        /* Noll j <= 28: radial order <= 6 */
 #define PHOSIM_MAX_COATED 6          /* coated surfaces with an accept-reject draw */
+#define PHOSIM_MAX_BUNDLE 4096       /* photons per ray of a background bundle */
 
 /* surface kinds, materials, source kinds (Sec. 2.4.1, 2.2) */
 enum { PHOSIM_MIRROR = 0, PHOSIM_REFRACT = 1, PHOSIM_DETECTOR = 2 };
@@ -159,12 +160,17 @@ typedef struct phosim_source {
     int32_t kind;               /* PHOSIM_POINT, PHOSIM_SERSIC, PHOSIM_GAUSS */
     int32_t sed;                /* index of the SED table */
     int32_t table;              /* Sersic radial table index */
-    int32_t pad;
+    int32_t bundle;             /* photons per ray, the background optimisation of Sec. 3.2 (0 or 1: one photon
+                                   per ray, <= PHOSIM_MAX_BUNDLE): photon i follows ray i / bundle through the
+                                   atmosphere and the optics to the detector surface, then lands at a Gaussian
+                                   offset of sigma bundle_sigma from the ray's hit and goes through the sensor
+                                   with its own draws (Philox blocks 5 and 6 of its own counter) */
     double xi, eta;             /* n_x, n_y of the undisturbed photon */
     double redshift;
     double t0, t_exp;
     double a, b, pa;            /* Sersic semi-axes at the half-light radius and position angle (rad);
                                    PHOSIM_GAUSS: a = sigma (rad) */
+    double bundle_sigma;        /* mm on the detector surface, >= 0 (used when bundle > 1) */
 } phosim_source;
 
 /* Per-photon record, written only when a record buffer is given (debugging / parity). */

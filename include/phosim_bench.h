@@ -34,6 +34,16 @@ phosim_status phosim_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* 
    CUDA. */
 phosim_status phosim_ds_eval(int op, const double* a, const double* b, double* out, int n);
 
+/* Per-kernel timing of phosim_trace.  While on, each phosim_trace call on the scene launches its kernels
+   one by one (no CUDA graph) with a CUDA event recorded on the call's stream before and after each launch.
+   phosim_stage_times waits for the events of the scene's last phosim_trace call and returns the summed
+   milliseconds of each kernel: ms[0] chief rays, ms[1] the one-kernel trace (PHOSIM_PLAIN_FP64,
+   PHOSIM_MIXED), ms[2] the entry stage and ms[3] the optics stage of the two-kernel double-single path
+   (PHOSIM_MIXED_DS); kernels the call did not launch read 0.  n >= 4.
+   Errors: INVALID_ARGUMENT (null scene or output, n < 4), CUDA. */
+phosim_status phosim_set_stage_timing(phosim_scene* scene, int on);
+phosim_status phosim_stage_times(phosim_scene* scene, double* ms, int n);
+
 #ifdef __cplusplus
 }
 #endif

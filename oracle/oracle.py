@@ -142,6 +142,11 @@ class Oracle:
         img = np.zeros((det.ny, det.nx), np.uint32) if image else None
         u64p = C.POINTER(C.c_uint64)
         dp = C.POINTER(C.c_double)
+        bn = _arr(getattr(src, "bundle", None) if getattr(src, "bundle", None) is not None else np.ones(n), np.int32)
+        bs = _arr(getattr(src, "bundle_sigma", None) if getattr(src, "bundle_sigma", None) is not None else np.zeros(n),
+                  np.float64)
+        self._keep_b = (bn, bs)
+        self.L.oracle_set_bundles(self.h, C.c_int(n), bn.ctypes.data_as(C.POINTER(C.c_int)), _dp(bs))
         rc = self.L.oracle_trace(self.h, C.c_int(n), *self._src_args(src), first.ctypes.data_as(u64p),
                                  count.ctypes.data_as(u64p), *(rec[k].ctypes.data_as(dp) for k in ("x", "y", "xc", "yc", "lam")),
                                  rec["flags"].ctypes.data_as(C.POINTER(C.c_uint32)),

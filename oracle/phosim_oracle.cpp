@@ -171,6 +171,17 @@ struct Scene {
     int sersic_K = 0;
     std::vector<std::vector<double>> sersic;
     std::vector<double> hf;      // quantiles of the high-frequency kick angle at lam_ref, u = (k + 1/2) / K
+    // background bundles (Sec. 3.2): per source, photons per ray (<= 1: one photon per ray) and the sigma (mm)
+    // of the Gaussian spread of a ray's photons on the detector surface
+    std::vector<int> bundle_n;
+    std::vector<double> bundle_sigma;
+};
+
+// A photon of a bundle: its own Gaussian offset on the detector surface and its own sensor draws, from
+// blocks 5 and 6 of its counter (the ray's path uses the draws of the ray's counter).
+struct Member {
+    double sx, sy;
+    uint32_t conv, diff_a, diff_b, back;
 };
 
 struct Source {
@@ -435,6 +446,28 @@ Draws draw_photon(const Scene& sc, int src_id, uint64_t i) {
     return D;
 }
 
+// Photon i of a bundle of n photons per ray (Sec. 3.2): the ray is i / n; the photon's offset on the
+// detector surface is a Gaussian of the given sigma drawn from block 5 of its own counter (Box-Muller), its
+// sensor draws are the rest of blocks 5 and 6.
+Member member_draws(const Scene& sc, int src_id, uint64_t i, double sigma) {
+    uint32_t w[8];
+    for (uint32_t blk = 5; blk < 7; ++blk) {
+        uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(i >> 32), (uint32_t)src_id, blk};
+        philox4x32_10(ctr, (uint32_t)sc.seed, (uint32_t)(sc.seed >> 32), &w[4 * (blk - 5)]);
+    }
+    Member m;
+    const double g = std::sqrt(-2.0 * std::log(uniform01(w[0])));
+    const double ph = 2.0 * M_PI * uniform01(w[1]);
+    m.sx = sigma * g * std::cos(ph);
+    m.sy = sigma * g * std::sin(ph);
+    m.conv = w[2]; m.diff_a = w[3]; m.diff_b = w[4]; m.back = w[5];
+    return m;
+}
+
+inline int bundle_of(const Scene& sc, int s) {
+    return (s < (int)sc.bundle_n.size() && sc.bundle_n[s] > 1) ? sc.bundle_n[s] : 1;
+}
+
 inline void min_margin(double& m, double v) { v = std::fabs(v); if (v < m) m = v; }
 
 struct Pre {     // photon state entering the optics (after the atmosphere)
@@ -566,7 +599,7 @@ struct OpticsOut {
 // Sec. 2.4.2 + 2.5: surfaces in order, then the silicon sensor and the pixel
 template <class T>
 void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const Pre& P, const Draws* D,
-                       OpticsOut<T>& out) {
+                       OpticsOut<T>& out, const Member* M = nullptr) {
     T x[3] = {T(P.x[0]), T(P.x[1]), T(P.x[2])};
     T d[3] = {T(P.d[0]), T(P.d[1]), T(P.d[2])};
     const double lam = P.lam;
@@ -593,6 +626,15 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
         T nn = sqrt(T(1.0) + zx * zx + zy * zy);
         T N[3] = {-zx / nn, -zy / nn, T(1.0) / nn};
         if (s.kind == K_DETECTOR) {
+            if (M) {   // a bundle's photon: its Gaussian offset from the ray's hit on the detector surface
+                p[0] = p[0] + T(M->sx);
+                p[1] = p[1] + T(M->sy);
+            }
+            // the sensor's draws (none for the deterministic rays of the surface-only traces, D = null)
+            const uint32_t w_conv = M ? M->conv : (D ? D->w[S_CONV] : 0u);
+            const uint32_t w_back = M ? M->back : (D ? D->w[S_BACK] : 0u);
+            const uint32_t w_diff_a = M ? M->diff_a : (D ? D->w[S_DIFF_A] : 0u);
+            const uint32_t w_diff_b = M ? M->diff_b : (D ? D->w[S_DIFF_B] : 0u);
             double hx = val(p[0]) - (sc.x0 - 0.5 * sc.nx * sc.pixel);
             double hy = val(p[1]) - (sc.y0 - 0.5 * sc.ny * sc.pixel);
             min_margin(out.margin_mm, hx); min_margin(out.margin_mm, hx - sc.nx * sc.pixel);
@@ -615,7 +657,7 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
                 if (val(t) < 0.0) t = T(0.0);
                 if (val(t) > 1.0) t = T(1.0);
                 T ell = T(sc.ell[k]) * (T(1.0) - t) + T(sc.ell[k + 1]) * t;
-                T Lt = ell * (-log(T(uniform01(D->w[S_CONV]))));
+                T Lt = ell * (-log(T(uniform01(w_conv))));
                 T dz = dl[2];
                 T deptht = Lt * (val(dz) < 0.0 ? -dz : dz);
                 double depth = val(deptht), L = val(Lt);
@@ -627,7 +669,7 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
                     if (sc.back_reflect) {
                         T rf = (n_si - T(1.0)) / (n_si + T(1.0));
                         double r_back = val(rf * rf);
-                        double u = uniform01(D->w[S_BACK]);
+                        double u = uniform01(w_back);
                         if (std::fabs(u - r_back) < 1e-12) out.margin_mm = 0.0;
                         if (u < r_back) {
                             deptht = T(2.0 * sc.t_si) - deptht;
@@ -651,8 +693,8 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
                 if (val(ts) < 0.0) ts = T(0.0);
                 if (val(ts) > 1.0) ts = T(1.0);
                 T sigma = T(sc.sig[ks]) * (T(1.0) - ts) + T(sc.sig[ks + 1]) * ts;
-                T g = sqrt(T(-2.0) * log(T(uniform01(D->w[S_DIFF_A]))));
-                T ph = T(2.0 * M_PI) * T(uniform01(D->w[S_DIFF_B]));
+                T g = sqrt(T(-2.0) * log(T(uniform01(w_diff_a))));
+                T ph = T(2.0 * M_PI) * T(uniform01(w_diff_b));
                 fx = fx + T(val(sigma * g * cos(ph)));
                 fy = fy + T(val(sigma * g * sin(ph)));
             }
@@ -853,6 +895,13 @@ uint64_t oracle_bleed(uint32_t* img, int nx, int ny, uint32_t w) {
     return removed;
 }
 
+// Background bundles (Sec. 3.2): n[s] photons per ray of source s (<= 1: one), spread with sigma[s] mm.
+void oracle_set_bundles(void* p, int n_src, const int* n, const double* sigma) {
+    Scene* s = (Scene*)p;
+    s->bundle_n.assign(n, n + n_src);
+    s->bundle_sigma.assign(sigma, sigma + n_src);
+}
+
 void oracle_set_hf_kick(void* p, int K, const double* q) {
     Scene* sc = (Scene*)p;
     sc->hf.assign(q, q + K);
@@ -886,11 +935,18 @@ int oracle_trace(void* p, int n_src, const int* kind, const int* sed, const int*
 #pragma omp parallel for schedule(static)
         for (long long k = 0; k < n; ++k) {
             uint64_t i = first[s] + (uint64_t)k;
-            Draws D = draw_photon(*sc, s, i);
+            const int nb = bundle_of(*sc, s);
+            // a bundle's photon follows its ray (index i / nb) to the detector surface
+            Draws D = draw_photon(*sc, s, nb > 1 ? i / (uint64_t)nb : i);
             Pre P;
             sample_and_atmosphere(*sc, src, D, P);
             OpticsOut<double> o;
-            optics_and_sensor(*sc, ST, P, &D, o);
+            if (nb > 1) {
+                const Member M = member_draws(*sc, s, i, sc->bundle_sigma[s]);
+                optics_and_sensor(*sc, ST, P, &D, o, &M);
+            } else {
+                optics_and_sensor(*sc, ST, P, &D, o);
+            }
             size_t r = off[s] + (size_t)k;
             if (rx) { rx[r] = o.x; ry[r] = o.y; rxc[r] = o.xc; ryc[r] = o.yc; rlam[r] = P.lam; rflags[r] = o.flags;
                       rpix[r] = o.pix; rmargin_mm[r] = o.margin_mm; rmargin_nm[r] = o.margin_nm; }

@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "phosim_bench.h"
 #include "phosim_device.cuh"
 #include "phosim_scene.hpp"
 #include "grad.hpp"
@@ -45,6 +46,13 @@ phosim_status upload(std::vector<void*>& owner, const T* host, size_t n, T** out
 }
 
 bool is_finite(double v) { return std::isfinite(v); }
+
+// device counter words of a scene: [0] tile counter, [1 .. kNumCounters] launch counters, then the state
+// count of the two-kernel double-single path
+constexpr int kStateCountWord = 1 + kNumCounters;
+constexpr int kCounterWords = kStateCountWord + 1;
+// photons per chunk of the two-kernel path: its state buffer holds one chunk (64 bytes a photon, 8.6 GB)
+constexpr uint64_t kStateChunk = 1ull << 27;
 
 // ----------------------------------------------------------------------------------------- Zernike figure
 // Noll index -> radial order n, |m| and whether the term is the cosine one (even j) or the sine one.
@@ -283,56 +291,73 @@ void destroy_graph(TraceGraph& g) {
     g = TraceGraph();
 }
 
-// The chief-ray and trace launches as one CUDA graph: captured once per precision on a private stream,
-// then replayed on the caller's stream with this call's kernel parameters and launch shapes.
-phosim_status launch_trace_graph(phosim_scene* sc, TraceParams& P, int mode, int blocks, int n_src, double* moments,
-                                 cudaStream_t st) {
-    TraceGraph& g = sc->graphs[mode];
+// Event pair number k of the scene's timing pool (grown on demand), tagged with a kernel kind.
+phosim_status timing_pair(phosim_scene* sc, int kind, cudaEvent_t* a, cudaEvent_t* b) {
+    const size_t k = (size_t)sc->timing_used;
+    while (sc->timing_events.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        sc->timing_events.push_back(e);
+    }
+    if (sc->timing_kind.size() < k + 1) sc->timing_kind.resize(k + 1);
+    sc->timing_kind[k] = kind;
+    *a = sc->timing_events[2 * k];
+    *b = sc->timing_events[2 * k + 1];
+    sc->timing_used++;
+    return PHOSIM_OK;
+}
+
+// one kernel launch of a captured sequence
+struct KernelLaunch {
+    const void* func;
+    dim3 grid, block;
+    void** args;
+};
+
+// Launch a fixed sequence of kernels as one CUDA graph: captured once per slot on a private stream, then
+// replayed on the caller's stream with this call's kernel parameters and launch shapes.
+phosim_status launch_graph(phosim_scene* sc, int slot, const KernelLaunch* L, int n, cudaStream_t st) {
+    TraceGraph& g = sc->graphs[slot];
+    if (g.exec && g.n != n) destroy_graph(g);
     if (!g.exec) {
         if (!sc->capture_stream) CU(cudaStreamCreateWithFlags(&sc->capture_stream, cudaStreamNonBlocking));
         CU(cudaStreamBeginCapture(sc->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = launch_chief_rays(P, sc->d_src, n_src, moments, sc->capture_stream);
-        cudaError_t e2 = launch_trace(P, mode, blocks, sc->threads, sc->capture_stream);
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            e = cudaLaunchKernel(L[i].func, L[i].grid, L[i].block, L[i].args, 0, sc->capture_stream);
         cudaGraph_t graph = nullptr;
-        cudaError_t e3 = cudaStreamEndCapture(sc->capture_stream, &graph);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !graph) {
+        cudaError_t e2 = cudaStreamEndCapture(sc->capture_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
             if (graph) cudaGraphDestroy(graph);
             (void)cudaGetLastError();
             return PHOSIM_ERR_CUDA;
         }
         g.graph = graph;
+        g.n = n;
         if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
-        size_t n = 0;
-        cudaGraphGetNodes(g.graph, nullptr, &n);
-        std::vector<cudaGraphNode_t> nodes(n);
-        cudaGraphGetNodes(g.graph, nodes.data(), &n);
+        size_t cnt = 0;
+        cudaGraphGetNodes(g.graph, nullptr, &cnt);
+        std::vector<cudaGraphNode_t> nodes(cnt);
+        cudaGraphGetNodes(g.graph, nodes.data(), &cnt);
         for (cudaGraphNode_t node : nodes) {
             cudaGraphNodeType t;
             if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
             cudaKernelNodeParams kp;
             if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) continue;
-            if (kp.func == trace_kernel_ptr(mode)) g.trace = node;
-            else if (kp.func == chief_kernel_ptr()) g.chief = node;
+            for (int i = 0; i < n; ++i)
+                if (kp.func == L[i].func) g.node[i] = node;
         }
-        if (!g.trace || !g.chief) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+        for (int i = 0; i < n; ++i)
+            if (!g.node[i]) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
     }
-    DSource* src_ptr = sc->d_src;
-    int n = n_src;
-    double* mom = moments;
-    void* chief_args[4] = {&P, &src_ptr, &n, &mom};
-    cudaKernelNodeParams kc = {};
-    kc.func = (void*)chief_kernel_ptr();
-    kc.gridDim = dim3((unsigned)((n_src + 127) / 128));
-    kc.blockDim = dim3(128);
-    kc.kernelParams = chief_args;
-    void* trace_args[1] = {&P};
-    cudaKernelNodeParams kt = {};
-    kt.func = (void*)trace_kernel_ptr(mode);
-    kt.gridDim = dim3((unsigned)blocks);
-    kt.blockDim = dim3((unsigned)sc->threads);
-    kt.kernelParams = trace_args;
-    CU(cudaGraphExecKernelNodeSetParams(g.exec, g.chief, &kc));
-    CU(cudaGraphExecKernelNodeSetParams(g.exec, g.trace, &kt));
+    for (int i = 0; i < n; ++i) {
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)L[i].func;
+        kp.gridDim = L[i].grid;
+        kp.blockDim = L[i].block;
+        kp.kernelParams = L[i].args;
+        CU(cudaGraphExecKernelNodeSetParams(g.exec, g.node[i], &kp));
+    }
     CU(cudaGraphLaunch(g.exec, st));
     return PHOSIM_OK;
 }
@@ -444,9 +469,11 @@ void phosim_destroy_scene(phosim_scene* sc) {
     cudaFree(sc->d_prefix);
     cudaFree(sc->d_counters);
     cudaFree(sc->d_stage);
+    cudaFree(sc->d_state);
     cudaFree(sc->d_grad_scratch);
     cudaFree(sc->d_mom_scratch);
     for (TraceGraph& g : sc->graphs) destroy_graph(g);
+    for (cudaEvent_t e : sc->timing_events) cudaEventDestroy(e);
     if (sc->capture_stream) cudaStreamDestroy(sc->capture_stream);
     (void)cudaGetLastError();
     delete sc;
@@ -767,6 +794,24 @@ phosim_status phosim_autotune(phosim_scene* sc, const phosim_source* src, int n_
     return rs;
 }
 
+phosim_status phosim_set_stage_timing(phosim_scene* sc, int on) {
+    if (!sc) return PHOSIM_ERR_INVALID_ARGUMENT;
+    sc->stage_timing = on != 0;
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_stage_times(phosim_scene* sc, double* ms, int n) {
+    if (!sc || !ms || n < 4) return PHOSIM_ERR_INVALID_ARGUMENT;
+    for (int k = 0; k < n; ++k) ms[k] = 0.0;
+    for (int k = 0; k < sc->timing_used; ++k) {
+        CU(cudaEventSynchronize(sc->timing_events[2 * k + 1]));
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, sc->timing_events[2 * k], sc->timing_events[2 * k + 1]));
+        ms[sc->timing_kind[k]] += t;
+    }
+    return PHOSIM_OK;
+}
+
 phosim_status phosim_get_counters(phosim_scene* sc, uint64_t* out, int n) {
     if (!sc || !out || n < kNumCounters) return PHOSIM_ERR_INVALID_ARGUMENT;
     unsigned long long h[kNumCounters];
@@ -783,11 +828,14 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
     const int mode = sc->precision;
+    const bool staged = mode == PHOSIM_MIXED_DS;        // the two-kernel double-single path
     // launch shape
-    int per_sm = 0;
-    CU(trace_occupancy(mode, sc->threads, &per_sm));
-    if (per_sm < 1) per_sm = 1;
-    const int blocks = sc->sm_count * per_sm;
+    int per_sm = 0, per_sm_optics = 0;
+    if (staged) CU(ds_stage_occupancy(sc->threads, &per_sm, &per_sm_optics));
+    else CU(trace_occupancy(mode, sc->threads, &per_sm));
+    per_sm = std::max(per_sm, 1);
+    per_sm_optics = std::max(per_sm_optics, 1);
+    const int blocks = sc->sm_count * per_sm, blocks_optics = sc->sm_count * per_sm_optics;
     const uint64_t warps = (uint64_t)blocks * (sc->threads / 32);
     uint64_t total = 0;
     for (int s = 0; s < n_src; ++s) total += n_photons[s];
@@ -807,16 +855,28 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         if (q.kind == PHOSIM_SERSIC && (q.table < 0 || q.table >= sc->sersic_tables)) return PHOSIM_ERR_INVALID_ARGUMENT;
         if (!is_finite(q.xi) || !is_finite(q.eta) || q.xi * q.xi + q.eta * q.eta >= 1.0 || !(q.redshift > -1.0))
             return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (q.bundle < 0 || (q.bundle > 1 && !(q.bundle_sigma >= 0.0 && is_finite(q.bundle_sigma))))
+            return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (q.bundle > PHOSIM_MAX_BUNDLE) return PHOSIM_ERR_LIMIT;
         DSource& d = hs[s];
         std::memset(&d, 0, sizeof(d));
         d.kind = q.kind; d.sed = q.sed; d.table = q.table;
         d.xi = q.xi; d.eta = q.eta; d.zfac = 1.0 + q.redshift; d.t0 = q.t0; d.t_exp = q.t_exp;
         d.a = q.a; d.b = q.b; d.cpa = std::cos(q.pa); d.spa = std::sin(q.pa);
+        d.bundle = q.bundle > 1 ? (uint32_t)q.bundle : 1u;
+        d.bsig = q.bundle > 1 ? q.bundle_sigma : 0.0;
         d.first = first ? first[s] : 0;
         d.count = n_photons[s];
         d.rec_off = rec;
         rec += n_photons[s];
-        prefix[s + 1] = prefix[s] + (n_photons[s] + T - 1) / T;
+        // work units: photons, or in the two-kernel path the rays of a bundle that have photons in the range
+        d.ufirst = d.first;
+        d.ucount = d.count;
+        if (staged && d.bundle > 1 && d.count > 0) {
+            d.ufirst = d.first / d.bundle;
+            d.ucount = (d.first + d.count + d.bundle - 1) / d.bundle - d.ufirst;
+        }
+        prefix[s + 1] = prefix[s] + (d.ucount + T - 1) / T;
     }
     if (n_src == 0 || total == 0) return PHOSIM_OK;
     if (sc->cap_src < (size_t)n_src) {
@@ -850,7 +910,19 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     }
     CU(cudaMemcpyAsync(sc->d_src, hs.data(), hs.size() * sizeof(DSource), cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(sc->d_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
-    CU(cudaMemsetAsync(sc->d_counters, 0, (1 + kNumCounters) * sizeof(unsigned long long), st));
+    // two-kernel path: the entrance-plane states of one chunk of tiles at most (kStateChunk photons)
+    const uint64_t n_tiles = prefix[n_src];
+    const uint64_t chunk_tiles = staged ? std::max<uint64_t>(1, kStateChunk / T) : n_tiles;
+    if (staged) {
+        const size_t need = (size_t)std::min<uint64_t>(total, chunk_tiles * T);
+        if (sc->cap_state < need) {
+            cudaFree(sc->d_state);
+            sc->d_state = nullptr; sc->cap_state = 0;
+            CU(cudaMalloc(&sc->d_state, need * sizeof(DSState)));
+            sc->cap_state = need;
+        }
+    }
+    CU(cudaMemsetAsync(sc->d_counters, 0, kCounterWords * sizeof(unsigned long long), st));
     TraceParams P = sc->base;
     P.sources = sc->d_src;
     P.tile_prefix = sc->d_prefix;
@@ -862,12 +934,65 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     P.image = d_image;
     P.moments = moments;
     P.records = records;
-    if (P.flags & PHOSIM_GRAPH) {
-        phosim_status gs = launch_trace_graph(sc, P, mode, blocks, n_src, moments, st);
-        if (gs != PHOSIM_OK) return gs;
+    DSource* src_ptr = sc->d_src;
+    int n_src_arg = n_src;
+    double* mom_arg = moments;
+    void* chief_args[4] = {&P, &src_ptr, &n_src_arg, &mom_arg};
+    const dim3 chief_grid((unsigned)((n_src + 127) / 128)), chief_block(128);
+    sc->timing_used = 0;
+    // a launch between events of the scene's timing pool when per-kernel timing is on
+    auto timed = [&](int kind, auto&& launch) -> phosim_status {
+        if (!sc->stage_timing) { CU(launch()); return PHOSIM_OK; }
+        cudaEvent_t a, b;
+        phosim_status ts = timing_pair(sc, kind, &a, &b);
+        if (ts != PHOSIM_OK) return ts;
+        CU(cudaEventRecord(a, st));
+        CU(launch());
+        CU(cudaEventRecord(b, st));
+        return PHOSIM_OK;
+    };
+    const bool use_graph = (P.flags & PHOSIM_GRAPH) && !sc->stage_timing;
+    if (!staged) {
+        void* trace_args[1] = {&P};
+        if (use_graph) {
+            const KernelLaunch L[2] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
+                                       {trace_kernel_ptr(mode), dim3((unsigned)blocks), dim3((unsigned)sc->threads), trace_args}};
+            phosim_status gs = launch_graph(sc, mode, L, 2, st);
+            if (gs != PHOSIM_OK) return gs;
+        } else {
+            phosim_status ls = timed(0, [&] { return launch_chief_rays(P, sc->d_src, n_src, moments, st); });
+            if (ls == PHOSIM_OK) ls = timed(1, [&] { return launch_trace(P, mode, blocks, sc->threads, st); });
+            if (ls != PHOSIM_OK) return ls;
+        }
     } else {
-        CU(launch_chief_rays(P, sc->d_src, n_src, moments, st));
-        CU(launch_trace(P, mode, blocks, sc->threads, st));
+        DSStage S;
+        S.state = sc->d_state;
+        S.n_state = sc->d_counters + kStateCountWord;
+        S.tile_begin = 0;
+        S.tile_end = std::min(n_tiles, chunk_tiles);
+        void* stage_args[2] = {&P, &S};
+        const dim3 block((unsigned)sc->threads);
+        if (use_graph && chunk_tiles >= n_tiles) {
+            const KernelLaunch L[3] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
+                                       {ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, stage_args},
+                                       {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics), block, stage_args}};
+            phosim_status gs = launch_graph(sc, mode, L, 3, st);
+            if (gs != PHOSIM_OK) return gs;
+        } else {
+            phosim_status ls = timed(0, [&] { return launch_chief_rays(P, sc->d_src, n_src, moments, st); });
+            if (ls != PHOSIM_OK) return ls;
+            for (uint64_t t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
+                S.tile_begin = t0;
+                S.tile_end = std::min(n_tiles, t0 + chunk_tiles);
+                if (t0 > 0) {
+                    CU(cudaMemsetAsync(sc->d_counters, 0, sizeof(unsigned long long), st));
+                    CU(cudaMemsetAsync(sc->d_counters + kStateCountWord, 0, sizeof(unsigned long long), st));
+                }
+                ls = timed(2, [&] { return launch_ds_entry(P, S, blocks, sc->threads, st); });
+                if (ls == PHOSIM_OK) ls = timed(3, [&] { return launch_ds_optics(P, S, blocks_optics, sc->threads, st); });
+                if (ls != PHOSIM_OK) return ls;
+            }
+        }
     }
     sc->last_stream = st;
     if (host_image) {

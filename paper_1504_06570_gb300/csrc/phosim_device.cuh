@@ -84,10 +84,13 @@ struct DLayer {
 };
 
 struct DSource {
-    int kind, sed, table, pad;
+    int kind, sed, table;
+    uint32_t bundle;                          // photons per ray (Sec. 3.2 background optimisation), >= 1
     double xi, eta, zfac, t0, t_exp, a, b, cpa, spa;
+    double bsig;                              // sigma of the spread of a ray's photons on the detector, mm
     double ref_x, ref_y;
     uint64_t first, count, rec_off;           // photons [first, first + count); record index of the first
+    uint64_t ufirst, ucount;                  // work units of the two-kernel path: rays of a bundle, else photons
 };
 
 // counters: [0] traced, [1] detected, [1 + r] dropped for reason r
@@ -165,6 +168,8 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 //   block 2: diffusion a, diffusion b, coated surface 0, coated surface 1
 //   block 3: coated surfaces 2..5
 //   block 4: high-frequency kick magnitude, direction, back-side reflection
+//   blocks 5, 6 (photons of a bundle, counter of the photon; the ray uses blocks 0-4 of the ray's counter):
+//            spread a, spread b, conversion, diffusion a; diffusion b, back-side reflection
 __device__ __forceinline__ double u64of(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
 __device__ __forceinline__ float u32of(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
 

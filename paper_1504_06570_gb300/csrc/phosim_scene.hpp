@@ -4,12 +4,17 @@
 #include <vector>
 
 #include "phosim_device.cuh"
+#include "photon_ds.cuh"
 
 // One captured [chief rays, trace] launch pair, replayed with updated kernel parameters.
+// One captured sequence of kernel launches ([chief rays, trace] or [chief rays, entry, optics]), replayed
+// with each call's kernel parameters and launch shapes.
+constexpr int kMaxGraphNodes = 3;
 struct TraceGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t chief = nullptr, trace = nullptr;
+    int n = 0;
+    cudaGraphNode_t node[kMaxGraphNodes] = {};
 };
 
 struct phosim_scene {
@@ -37,6 +42,8 @@ struct phosim_scene {
     size_t cap_prefix = 0;
     unsigned long long* d_counters = nullptr;   // [0] tile counter, [1..9] counters
     uint32_t* d_stage = nullptr;                // staging image for host image pointers
+    phosim::DSState* d_state = nullptr;         // entrance-plane states of the two-kernel double-single path
+    size_t cap_state = 0;
     size_t cap_stage = 0;
     cudaStream_t last_stream = nullptr;
     // adjoint: Zernike monomial table (owned with the optics) and per-call scratch
@@ -48,6 +55,12 @@ struct phosim_scene {
     // CUDA graphs of the trace launch (PHOSIM_GRAPH), one per precision, captured on a private stream
     TraceGraph graphs[3];
     cudaStream_t capture_stream = nullptr;
+    // per-kernel timing (phosim_set_stage_timing): an event pair per launch of the last call, with the
+    // kernel kind (0 chief, 1 one-kernel trace, 2 entry stage, 3 optics stage)
+    bool stage_timing = false;
+    std::vector<cudaEvent_t> timing_events;
+    std::vector<int> timing_kind;
+    int timing_used = 0;
 };
 
 namespace phosim {
@@ -57,5 +70,11 @@ cudaError_t launch_chief_rays(const TraceParams& P, DSource* sources, int n_src,
 cudaError_t trace_occupancy(int mode, int threads, int* blocks_per_sm);
 const void* trace_kernel_ptr(int mode);
 const void* chief_kernel_ptr();
+// the two-kernel double-single path (PHOSIM_MIXED_DS in phosim_trace)
+cudaError_t launch_ds_entry(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_ds_optics(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);
+cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm);
+const void* ds_entry_kernel_ptr();
+const void* ds_optics_kernel_ptr();
 void free_all(std::vector<void*>& v);
 }  // namespace phosim

@@ -92,9 +92,44 @@ struct ForwardRecord {
     double L, ox, oy;
 };
 
+// A photon of a bundle (Sec. 3.2 background optimisation): it follows its ray (the photon index divided by
+// the bundle size) to the detector surface, lands at a Gaussian offset of the source's spread sigma from the
+// ray's hit and takes its own sensor draws, all from blocks 5 and 6 of its own counter.
+struct MemberDraw {
+    double sx, sy;
+    uint32_t conv, diff_a, diff_b, back;
+};
+
+template <bool MIXED>
+__device__ __forceinline__ MemberDraw member_draw(const TraceParams& P, double bsig, int src, uint64_t i) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    const uint4 m5 = philox(make_uint4(clo, chi, (uint32_t)src, 5u), P.k0, P.k1);
+    const uint4 m6 = philox(make_uint4(clo, chi, (uint32_t)src, 6u), P.k0, P.k1);
+    MemberDraw m;
+    if constexpr (MIXED) {
+        const float g = sqrtf(-2.f * logf(u32of(m5.x)));
+        float sn, cs;
+        sincospif(2.f * u32of(m5.y), &sn, &cs);
+        m.sx = (double)((float)bsig * g * cs);
+        m.sy = (double)((float)bsig * g * sn);
+    } else {
+        const double g = sqrt(-2.0 * log(u64of(m5.x)));
+        double sn, cs;
+        sincospi(2.0 * u64of(m5.y), &sn, &cs);
+        m.sx = bsig * g * cs;
+        m.sy = bsig * g * sn;
+    }
+    m.conv = m5.z; m.diff_a = m5.w; m.diff_b = m6.x; m.back = m6.y;
+    return m;
+}
+
+// the ray a photon follows: itself, or for a bundle of n photons per ray, photon index / n
+__device__ __forceinline__ uint64_t ray_of(uint32_t bundle, uint64_t i) { return bundle > 1 ? i / bundle : i; }
+
 template <bool MIXED, bool FULL, bool RECORD = false>
 __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double D[3], double lam, uint4 w1, uint4 w2,
-                                       uint4 w3, uint4 w4, PhotonOut& R, ForwardRecord* fr = nullptr) {
+                                       uint4 w3, uint4 w4, PhotonOut& R, ForwardRecord* fr = nullptr,
+                                       const MemberDraw* mb = nullptr) {
     double n_cur = 1.0;
     int glass_mat = -1;
     double glass_n = 1.0, glass_inv = 1.0;
@@ -115,6 +150,12 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
         p[2] = fma(l, dl[2], p[2]);
         const double Nx = Nv[0], Ny = Nv[1], Nz = Nv[2];
         if (S.kind == PHOSIM_DETECTOR) {
+            uint32_t w_conv = w1.w, w_diff_a = w2.x, w_diff_b = w2.y, w_back = w4.z;
+            if (mb) {   // a bundle's photon: its offset from the ray's hit and its own sensor draws
+                p[0] += mb->sx;
+                p[1] += mb->sy;
+                w_conv = mb->conv; w_diff_a = mb->diff_a; w_diff_b = mb->diff_b; w_back = mb->back;
+            }
             const double hx = p[0] - P.xlo, hy = p[1] - P.ylo;
             if (FULL && !(hx >= 0.0 && hy >= 0.0 && hx < P.nx * P.pixel && hy < P.ny * P.pixel)) {
                 R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
@@ -129,7 +170,7 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                     const float n_si = silicon_index_f((float)lam);
                     if (!refract(dl, Nx, Ny, Nz, n_cur / (double)n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
                     const float ell = lerp_table_f(P.ell32, P.n_ell, (float)((lam - P.ell_lam0) * P.inv_ell_dlam));
-                    const float Lf = ell * -logf(u32of(w1.w));
+                    const float Lf = ell * -logf(u32of(w_conv));
                     L = (double)Lf;
                     const float rf = (n_si - 1.f) / (n_si + 1.f);
                     r_back = (double)(rf * rf);
@@ -137,7 +178,7 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                     const double n_si = silicon_index(lam);
                     if (!refract(dl, Nx, Ny, Nz, n_cur / n_si)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
                     const double ell = lerp_table(P.ell, P.n_ell, (lam - P.ell_lam0) * P.inv_ell_dlam);
-                    L = ell * -log(u64of(w1.w));
+                    L = ell * -log(u64of(w_conv));
                     const double rf = (n_si - 1.0) / (n_si + 1.0);
                     r_back = rf * rf;
                 }
@@ -145,7 +186,7 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                 if (!(depth <= P.t_si)) {
                     // back-side reflection: the photon turns round at the back and converts on its way back
                     bool back = false;
-                    if ((P.flags & PHOSIM_BACK_REFLECT) && u64of(w4.z) < r_back) {
+                    if ((P.flags & PHOSIM_BACK_REFLECT) && u64of(w_back) < r_back) {
                         depth = 2.0 * P.t_si - depth;
                         back = depth >= 0.0;
                     }
@@ -159,15 +200,15 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                 // lateral Gaussian diffusion (Sec. 2.5)
                 if constexpr (MIXED) {
                     const float sg = lerp_table_f(P.sig32, P.n_sig, (float)(depth * P.sig_scale));
-                    const float g = sqrtf(-2.f * logf(u32of(w2.x)));
+                    const float g = sqrtf(-2.f * logf(u32of(w_diff_a)));
                     float sn, cs;
-                    sincospif(2.f * u32of(w2.y), &sn, &cs);
+                    sincospif(2.f * u32of(w_diff_b), &sn, &cs);
                     sigma = 1.0; gxd = (double)(sg * g * cs); gyd = (double)(sg * g * sn);
                 } else {
                     sigma = lerp_table(P.sig, P.n_sig, depth * P.sig_scale);
-                    const double g = sqrt(-2.0 * log(u64of(w2.x)));
+                    const double g = sqrt(-2.0 * log(u64of(w_diff_a)));
                     double sn, cs;
-                    sincospi(2.0 * u64of(w2.y), &sn, &cs);
+                    sincospi(2.0 * u64of(w_diff_b), &sn, &cs);
                     gxd = g * cs; gyd = g * sn;
                 }
                 fx = fma(sigma, gxd, fx);
@@ -269,6 +310,7 @@ __device__ __forceinline__ int early_coating_reject(const TraceParams& P, double
 template <bool MIXED>
 __device__ __forceinline__ int early_reject_surface(const TraceParams& P, const DSource& s, int src, uint64_t i,
                                                     double& lam) {
+    i = ray_of(s.bundle, i);
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
     const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
     lam = sample_wavelength<MIXED>(P, s, w0);
@@ -279,8 +321,9 @@ __device__ __forceinline__ int early_reject_surface(const TraceParams& P, const 
 }
 
 template <bool MIXED, bool RECORD = false>
-__device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource& s, int src, uint64_t i, PhotonOut& R,
-                                             ForwardRecord* fr = nullptr) {
+__device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource& s, int src, uint64_t photon,
+                                             PhotonOut& R, ForwardRecord* fr = nullptr) {
+    const uint64_t i = ray_of(s.bundle, photon);
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
     const uint4 w0 = philox(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
     const uint4 w1 = philox(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
@@ -411,7 +454,10 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
         z = P.z_ent;
     }
     double X[3] = {x, y, z}, D[3] = {nx, ny, nz};
-    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, w4, R, fr);
+    MemberDraw mb;
+    const bool bundled = s.bundle > 1;
+    if (bundled) mb = member_draw<MIXED>(P, s.bsig, src, photon);
+    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, w4, R, fr, bundled ? &mb : nullptr);
 }
 
 

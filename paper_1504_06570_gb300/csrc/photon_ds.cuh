@@ -11,14 +11,21 @@
 
 #include "photon.cuh"
 
+// inlining of the larger steps (sag, intersection, refraction, Sellmeier index, pupil azimuth): inline is
+// faster (no call boundaries inside the surface loop); the quotient, roots and the generator stay out of line
 #ifndef PHOSIM_DS_SAG
-#define PHOSIM_DS_SAG __noinline__
+#define PHOSIM_DS_SAG __forceinline__
 #endif
 #ifndef PHOSIM_DS_PHILOX
 #define PHOSIM_DS_PHILOX __noinline__
 #endif
 #ifndef PHOSIM_DS_STEP
-#define PHOSIM_DS_STEP __noinline__
+#define PHOSIM_DS_STEP __forceinline__
+#endif
+// code for rare surface features (odd asphere terms, Zernike figure, tilts): inline (measured faster than
+// out of line)
+#ifndef PHOSIM_DS_RARE
+#define PHOSIM_DS_RARE __forceinline__
 #endif
 
 namespace phosim {
@@ -33,11 +40,28 @@ struct PhotonOutS {
     int pix;
 };
 
+// A photon's state on the entrance plane of the telescope, passed from the entry stage to the optics stage
+// of the two-kernel double-single path (64 bytes)
+struct __align__(16) DSState {
+    ds x, y, z, nx, ny, nz;
+    float lam;
+    int src;
+    unsigned long long idx;       // photon index within its source's stream
+};
+
+// one chunk of the two-kernel path: tiles [tile_begin, tile_end) of the launch, their states, the count
+struct DSStage {
+    DSState* state;
+    unsigned long long* n_state;
+    uint64_t tile_begin, tile_end;
+};
+
 // the per-source constants of a tile, converted once per tile
 struct SourceS {
     ds xi, eta, t0, t_exp, ref_x, ref_y;
-    float zfac, a, b, cpa, spa;
+    float zfac, a, b, cpa, spa, bsig;
     int kind, sed, table;
+    uint32_t bundle;
 };
 
 __device__ __forceinline__ SourceS source_s(const DSource& s) {
@@ -46,6 +70,7 @@ __device__ __forceinline__ SourceS source_s(const DSource& s) {
     r.ref_x = ds_of(s.ref_x); r.ref_y = ds_of(s.ref_y);
     r.zfac = (float)s.zfac; r.a = (float)s.a; r.b = (float)s.b; r.cpa = (float)s.cpa; r.spa = (float)s.spa;
     r.kind = s.kind; r.sed = s.sed; r.table = s.table;
+    r.bundle = s.bundle; r.bsig = (float)s.bsig;
     return r;
 }
 
@@ -120,8 +145,28 @@ __device__ __forceinline__ void zern_eval_f(const float* __restrict__ zp, float 
     z = zz; zu = zzu; zv = zzv;
 }
 
-// Sag and slopes (Sec. 2.4.1).  The Zernike figure (tens of nanometres) is evaluated in single precision:
-// its absolute error is far below the 1e-8 mm the intersection resolves.
+// The odd asphere terms and the Zernike figure of a sag, out of line: surfaces without them (the common
+// case) keep the surface loop's code compact in the instruction cache.
+static __device__ PHOSIM_DS_RARE void sag_odd_ds(const DSurfaceS& E, ds r2, ds& z, ds& g) {
+    const ds rho = ds_sqrt(r2) * E.inv_rn;
+    const ds u = rho * rho;
+    const ds po = dfma(dfma(dfma(E.ao[3], u, E.ao[2]), u, E.ao[1]), u, E.ao[0]);
+    z = dfma(u * rho, po, z);
+    const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
+    g = dfma(rho * E.inv_rn2, pd, g);
+}
+
+// The Zernike figure (tens of nanometres) is evaluated in single precision: its absolute error is far below
+// the 1e-8 mm the intersection resolves.
+static __device__ PHOSIM_DS_RARE void sag_zern_ds(const DSurfaceS& E, ds x, ds y, ds& z, ds& zx, ds& zy) {
+    float zz, zu, zv;
+    zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
+    z = z + zz;
+    zx = zx + zu * E.zinv;
+    zy = zy + zv * E.zinv;
+}
+
+// Sag and slopes (Sec. 2.4.1).
 static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy) {
     const ds r2 = dfma(x, x, y * y);
     ds g = ds_f(0.f);
@@ -140,23 +185,10 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
         const ds pd = dfma(dfma(dfma(E.aed[3], u, E.aed[2]), u, E.aed[1]), u, E.aed[0]);
         g = dfma(u * E.inv_rn2, pd, g);
     }
-    if (flags & SF_ODD) {
-        const ds rho = ds_sqrt(r2) * E.inv_rn;
-        const ds u = rho * rho;
-        const ds po = dfma(dfma(dfma(E.ao[3], u, E.ao[2]), u, E.ao[1]), u, E.ao[0]);
-        z = dfma(u * rho, po, z);
-        const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
-        g = dfma(rho * E.inv_rn2, pd, g);
-    }
+    if (flags & SF_ODD) sag_odd_ds(E, r2, z, g);
     zx = x * g;
     zy = y * g;
-    if (flags & SF_ZERN) {
-        float zz, zu, zv;
-        zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
-        z = z + zz;
-        zx = zx + zu * E.zinv;
-        zy = zy + zv * E.zinv;
-    }
+    if (flags & SF_ZERN) sag_zern_ds(E, x, y, z, zx, zy);
     return true;
 }
 
@@ -224,33 +256,42 @@ static __device__ PHOSIM_DS_STEP bool refract_ds(ds d[3], ds N[3], ds mu) {
     return true;
 }
 
-__device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, const ds x[3], const ds d[3], ds p[3],
-                                              ds dl[3]) {
-    const ds rx = x[0] - E.o[0], ry = x[1] - E.o[1], rz = x[2] - E.o[2];
-    if (!(flags & SF_ROTATED)) {
-        p[0] = rx; p[1] = ry; p[2] = rz;
-        dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
-        return;
-    }
+// rotations into and out of a tilted surface's frame, out of line (aligned surfaces only translate)
+static __device__ PHOSIM_DS_RARE void rotate_in_ds(const DSurfaceS& E, ds rx, ds ry, ds rz, const ds d[3], ds p[3],
+                                                ds dl[3]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         p[i] = dfma(E.M[3 * i], rx, dfma(E.M[3 * i + 1], ry, E.M[3 * i + 2] * rz));
         dl[i] = dfma(E.M[3 * i], d[0], dfma(E.M[3 * i + 1], d[1], E.M[3 * i + 2] * d[2]));
     }
 }
-
-__device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, const ds p[3], const ds dl[3], ds x[3],
-                                                ds d[3]) {
-    if (!(flags & SF_ROTATED)) {
-        x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1]; x[2] = p[2] + E.o[2];
-        d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
-        return;
-    }
+static __device__ PHOSIM_DS_RARE void rotate_out_ds(const DSurfaceS& E, const ds p[3], const ds dl[3], ds x[3], ds d[3]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         x[i] = dfma(E.M[i], p[0], dfma(E.M[3 + i], p[1], dfma(E.M[6 + i], p[2], E.o[i])));
         d[i] = dfma(E.M[i], dl[0], dfma(E.M[3 + i], dl[1], E.M[6 + i] * dl[2]));
     }
+}
+
+__device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, const ds x[3], const ds d[3], ds p[3],
+                                              ds dl[3]) {
+    const ds rx = x[0] - E.o[0], ry = x[1] - E.o[1], rz = x[2] - E.o[2];
+    if (flags & SF_ROTATED) {
+        rotate_in_ds(E, rx, ry, rz, d, p, dl);
+        return;
+    }
+    p[0] = rx; p[1] = ry; p[2] = rz;
+    dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
+}
+
+__device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, const ds p[3], const ds dl[3], ds x[3],
+                                                ds d[3]) {
+    if (flags & SF_ROTATED) {
+        rotate_out_ds(E, p, dl, x, d);
+        return;
+    }
+    x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1]; x[2] = p[2] + E.o[2];
+    d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
 }
 
 // the coating accept-reject: the draw (w + 1/2) 2^-32 < T exactly when w < ceil(T 2^32 - 1/2)
@@ -277,6 +318,7 @@ __device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, floa
     return -1;
 }
 
+// i is the photon, or for a bundle the ray
 __device__ __forceinline__ int early_reject_surface_f(const TraceParams& P, const SourceS& s, int src, uint64_t i,
                                                       float& lam) {
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
@@ -288,9 +330,38 @@ __device__ __forceinline__ int early_reject_surface_f(const TraceParams& P, cons
     return early_coating_reject_f(P, lam, w2, w3);
 }
 
-// Surfaces in order (Sec. 2.4.2): the steps of optics<MIXED = true, FULL = true> in photon.cuh.
-__device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3], float lam, uint4 w1, uint4 w2,
-                                          uint4 w3, uint4 w4, PhotonOutS& R) {
+// A bundle's photon (member_draw in photon.cuh) with a single-precision spread
+struct MemberDrawS {
+    float sx, sy;
+    uint32_t conv, diff_a, diff_b, back;
+};
+
+__device__ __forceinline__ MemberDrawS member_draw_s(const TraceParams& P, float bsig, int src, uint64_t i) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    const uint4 m5 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 5u), P.k0, P.k1);
+    const uint4 m6 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 6u), P.k0, P.k1);
+    MemberDrawS m;
+    const float g = sqrtf(-2.f * logf(u32of(m5.x)));
+    float sn, cs;
+    sincospif(2.f * u32of(m5.y), &sn, &cs);
+    m.sx = bsig * g * cs;
+    m.sy = bsig * g * sn;
+    m.conv = m5.z; m.diff_a = m5.w; m.diff_b = m6.x; m.back = m6.y;
+    return m;
+}
+
+// A ray on the detector surface (detector frame): hit point, direction, normal, index of the medium in front.
+struct DetectorHit {
+    ds px, py;
+    ds dl[3], N[3];
+    ds n_cur;
+    int si;
+};
+
+// Surfaces in order up to the detector surface (Sec. 2.4.2): the steps of optics<MIXED = true, FULL = true>
+// in photon.cuh before the sensor.  False when the ray is lost on the way (R.flags says where and why).
+__device__ __forceinline__ bool optics_to_detector_ds(const TraceParams& P, ds X[3], ds D[3], float lam, uint4 w2,
+                                                      uint4 w3, uint32_t& lost_flags, DetectorHit& H) {
     ds n_cur = ds_f(1.f);
     int glass_mat = -1;
     ds glass_n = ds_f(1.f), glass_inv = ds_f(1.f);
@@ -303,60 +374,22 @@ __device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3]
         to_surface_ds(E, flags, X, D, p, dl);
         ds l, Nv[3];
         const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
-        if (why) { R.flags = lost(why, si); return; }
+        if (why) { lost_flags = lost(why, si); return false; }
         p[0] = dfma(l, dl[0], p[0]);
         p[1] = dfma(l, dl[1], p[1]);
         p[2] = dfma(l, dl[2], p[2]);
         if (S.kind == PHOSIM_DETECTOR) {
-            const ds hx = p[0] - P.xlo_s, hy = p[1] - P.ylo_s;
-            if (!(hx.hi >= 0.f && hy.hi >= 0.f && ds_lt(hx, P.chip_w_s) && ds_lt(hy, P.chip_h_s))) {
-                R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
-                return;
-            }
-            ds fx = p[0], fy = p[1];
-            R.xc = fx; R.yc = fy;
-            if (P.flags & PHOSIM_SENSOR) {
-                // refraction into the silicon, exponential conversion length (Sec. 2.4.2)
-                const float n_si = silicon_index_f(lam);
-                if (!refract_ds(dl, Nv, n_cur / ds_f(n_si))) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
-                const float ell = lerp_table_f(P.ell32, P.n_ell, (lam - P.ell_lam0f) * P.inv_ell_dlamf);
-                const float L = ell * -logf(u32of(w1.w));
-                const float rf = (n_si - 1.f) / (n_si + 1.f);
-                float depth = L * fabsf(dl[2].hi);
-                if (!(depth <= P.t_sif)) {
-                    // back-side reflection: the photon turns round at the back and converts on its way back
-                    bool back = false;
-                    if ((P.flags & PHOSIM_BACK_REFLECT) && u32of(w4.z) < rf * rf) {
-                        depth = 2.f * P.t_sif - depth;
-                        back = depth >= 0.f;
-                    }
-                    if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
-                }
-                if (depth < P.dead_layerf) { R.flags = lost(PHOSIM_LOST_DEAD_LAYER, si); return; }
-                fx = dfma(dl[0], L, fx);
-                fy = dfma(dl[1], L, fy);
-                R.xc = fx; R.yc = fy;
-                // lateral Gaussian diffusion (Sec. 2.5)
-                const float sg = lerp_table_f(P.sig32, P.n_sig, depth * P.sig_scalef);
-                const float g = sqrtf(-2.f * logf(u32of(w2.x)));
-                float sn, cs;
-                sincospif(2.f * u32of(w2.y), &sn, &cs);
-                fx = fx + sg * g * cs;
-                fy = fy + sg * g * sn;
-            }
-            R.x = fx; R.y = fy;
-            const float px = ds_floor((fx - P.xlo_s) * P.inv_pixel_s), py = ds_floor((fy - P.ylo_s) * P.inv_pixel_s);
-            if (!(px >= 0.f && py >= 0.f && px < (float)P.nx && py < (float)P.ny)) {
-                R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
-                return;
-            }
-            R.pix = (int)py * P.nx + (int)px;
-            R.flags = PHOSIM_F_DETECTED;
-            return;
+            // the hit on the detector surface, its direction and the medium in front of it
+            H.px = p[0]; H.py = p[1];
+            H.dl[0] = dl[0]; H.dl[1] = dl[1]; H.dl[2] = dl[2];
+            H.N[0] = Nv[0]; H.N[1] = Nv[1]; H.N[2] = Nv[2];
+            H.n_cur = n_cur;
+            H.si = si;
+            return true;
         }
         // clear aperture
         const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
-        if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return; }
+        if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { lost_flags = lost(PHOSIM_LOST_VIGNETTED, si); return false; }
         // coating accept-reject at the incidence angle and wavelength
         if (S.coat_slot >= 0) {
             const DCoating& C = P.coat[S.coating];
@@ -370,8 +403,8 @@ __device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3]
             const int k = S.coat_slot;
             const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
             if (!((unsigned long long)w < __ldg(C.T_thr + (size_t)coat_lambda_bin(C, lam) * C.nt + it))) {
-                R.flags = lost(PHOSIM_LOST_COATING, si);
-                return;
+                lost_flags = lost(PHOSIM_LOST_COATING, si);
+                return false;
             }
         }
         if (S.kind == PHOSIM_MIRROR) {
@@ -394,12 +427,81 @@ __device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3]
                 n_next = ds_f(silicon_index_f(lam));
                 inv_next = ds_rcp(n_next);
             }
-            if (!refract_ds(dl, Nv, n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+            if (!refract_ds(dl, Nv, n_cur * inv_next)) { lost_flags = lost(PHOSIM_LOST_TIR, si); return false; }
             n_cur = n_next;
         }
         from_surface_ds(E, flags, p, dl, X, D);
     }
-    R.flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
+    lost_flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
+    return false;
+}
+
+// The sensor and the pixel for a ray's hit on the detector surface (Sec. 2.4.2, 2.5): the detector steps of
+// optics<MIXED = true, FULL = true>, with a bundle photon's offset and draws when mb is given.
+__device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHit& H, float lam, uint4 w1, uint4 w2,
+                                          uint4 w4, PhotonOutS& R, const MemberDrawS* mb = nullptr) {
+    const int si = H.si;
+    ds p0 = H.px, p1 = H.py;
+    ds dl[3] = {H.dl[0], H.dl[1], H.dl[2]}, Nv[3] = {H.N[0], H.N[1], H.N[2]};
+    uint32_t w_conv = w1.w, w_diff_a = w2.x, w_diff_b = w2.y, w_back = w4.z;
+    if (mb) {   // a bundle's photon: its offset from the ray's hit and its own sensor draws
+        p0 = p0 + mb->sx;
+        p1 = p1 + mb->sy;
+        w_conv = mb->conv; w_diff_a = mb->diff_a; w_diff_b = mb->diff_b; w_back = mb->back;
+    }
+    const ds hx = p0 - P.xlo_s, hy = p1 - P.ylo_s;
+    if (!(hx.hi >= 0.f && hy.hi >= 0.f && ds_lt(hx, P.chip_w_s) && ds_lt(hy, P.chip_h_s))) {
+        R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
+        return;
+    }
+    ds fx = p0, fy = p1;
+    R.xc = fx; R.yc = fy;
+    if (P.flags & PHOSIM_SENSOR) {
+        // refraction into the silicon, exponential conversion length (Sec. 2.4.2)
+        const float n_si = silicon_index_f(lam);
+        if (!refract_ds(dl, Nv, H.n_cur / ds_f(n_si))) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+        const float ell = lerp_table_f(P.ell32, P.n_ell, (lam - P.ell_lam0f) * P.inv_ell_dlamf);
+        const float L = ell * -logf(u32of(w_conv));
+        const float rf = (n_si - 1.f) / (n_si + 1.f);
+        float depth = L * fabsf(dl[2].hi);
+        if (!(depth <= P.t_sif)) {
+            // back-side reflection: the photon turns round at the back and converts on its way back
+            bool back = false;
+            if ((P.flags & PHOSIM_BACK_REFLECT) && u32of(w_back) < rf * rf) {
+                depth = 2.f * P.t_sif - depth;
+                back = depth >= 0.f;
+            }
+            if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
+        }
+        if (depth < P.dead_layerf) { R.flags = lost(PHOSIM_LOST_DEAD_LAYER, si); return; }
+        fx = dfma(dl[0], L, fx);
+        fy = dfma(dl[1], L, fy);
+        R.xc = fx; R.yc = fy;
+        // lateral Gaussian diffusion (Sec. 2.5)
+        const float sg = lerp_table_f(P.sig32, P.n_sig, depth * P.sig_scalef);
+        const float g = sqrtf(-2.f * logf(u32of(w_diff_a)));
+        float sn, cs;
+        sincospif(2.f * u32of(w_diff_b), &sn, &cs);
+        fx = fx + sg * g * cs;
+        fy = fy + sg * g * sn;
+    }
+    R.x = fx; R.y = fy;
+    const float px = ds_floor((fx - P.xlo_s) * P.inv_pixel_s), py = ds_floor((fy - P.ylo_s) * P.inv_pixel_s);
+    if (!(px >= 0.f && py >= 0.f && px < (float)P.nx && py < (float)P.ny)) {
+        R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
+        return;
+    }
+    R.pix = (int)py * P.nx + (int)px;
+    R.flags = PHOSIM_F_DETECTED;
+}
+
+// Surfaces and sensor (Sec. 2.4.2, 2.5): the steps of optics<MIXED = true, FULL = true> in photon.cuh.
+__device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3], float lam, uint4 w1, uint4 w2,
+                                          uint4 w3, uint4 w4, PhotonOutS& R, const MemberDrawS* mb = nullptr) {
+    DetectorHit H;
+    uint32_t lost_flags = 0;
+    if (optics_to_detector_ds(P, X, D, lam, w2, w3, lost_flags, H)) detect_ds(P, H, lam, w1, w2, w4, R, mb);
+    else R.flags = lost_flags;
 }
 
 // Bilinear screen gradient (Sec. 2.3.2) at a double-single screen position; single-precision weights
@@ -424,12 +526,29 @@ __device__ __forceinline__ void screen_gradient_ds(const DScale& S, ds sx, ds sy
     gy += w00 * A.y + w10 * A.w + w01 * B.y + w11 * B.w;
 }
 
-// One photon from the top of the atmosphere to the pixel: the steps of trace_photon<MIXED = true>.
-__device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
-                                                PhotonOutS& R) {
+// The random words the surfaces and the sensor read: blocks 1 (conversion), 2 (diffusion, coatings 0-1),
+// 3 (coatings 2-5) and 4 (back-side reflection), the last two only when the scene uses them; i is the ray.
+__device__ __forceinline__ void optics_words(const TraceParams& P, int src, uint64_t i, uint4& w1, uint4& w2, uint4& w3,
+                                             uint4& w4) {
+    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
+    w1 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
+    w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    w3 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
+    w4 = make_uint4(0u, 0u, 0u, 0u);
+    if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
+}
+
+// Ray i from the top of the atmosphere to the entrance plane of the telescope (Sec. 2.2, 2.3): the sampling
+// and layer steps of trace_photon<MIXED = true> (i is the photon, or for a bundle the ray).  False when the
+// dynamic transmission test drops it (R.flags says where); otherwise X, D are its position and direction on
+// the entrance plane.
+__device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
+                                                PhotonOutS& R, ds X[3], ds D[3], float& lam_out, uint4& w1,
+                                                uint4& w2, uint4& w3, uint4& w4) {
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
     const uint4 w0 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
-    const uint4 w1 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
+    w1 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
     R.flags = 0; R.pix = -1;
     R.x = R.y = R.xc = R.yc = ds_f(0.f);
     // time stamp, wavelength (Sec. 2.2)
@@ -455,12 +574,12 @@ __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const Sour
     }
     ds w = ds_f(1.f) - dfma(nx, nx, ny * ny);
     ds rinv = ds_rsqrt(w);
-    const uint4 w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
-    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
+    w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    w3 = make_uint4(0u, 0u, 0u, 0u);
     if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
     if (P.flags & PHOSIM_EARLY_REJECT) {
         const int si = early_coating_reject_f(P, lam, w2, w3);
-        if (si >= 0) { R.flags = lost(PHOSIM_LOST_COATING, si); return; }
+        if (si >= 0) { R.flags = lost(PHOSIM_LOST_COATING, si); return false; }
     }
     // pupil point on the annulus, on the nominal first surface, moved back to the top of the atmosphere
     const ds r = ds_sqrt(dfma(ds_uniform(w0.x), P.pr_dr2_s, P.pr_in2_s));
@@ -476,7 +595,7 @@ __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const Sour
         y = y - ny * l;
         z = P.h_top_s;
     }
-    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+    w4 = make_uint4(0u, 0u, 0u, 0u);
     if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
     // frozen-flow layers top to bottom (Sec. 2.3)
     if (P.flags & PHOSIM_ATMOSPHERE) {
@@ -515,8 +634,23 @@ __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const Sour
         y = dfma(ny, l, y);
         z = P.z_ent_s;
     }
-    ds X[3] = {x, y, z}, D[3] = {nx, ny, nz};
-    optics_ds(P, X, D, lam, w1, w2, w3, w4, R);
+    X[0] = x; X[1] = y; X[2] = z;
+    D[0] = nx; D[1] = ny; D[2] = nz;
+    lam_out = lam;
+    return true;
+}
+
+// One photon from the top of the atmosphere to the pixel: the steps of trace_photon<MIXED = true>.
+__device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
+                                                PhotonOutS& R) {
+    ds X[3], D[3];
+    float lam;
+    uint4 w1, w2, w3, w4;
+    if (!photon_entry_ds(P, s, src, ray_of(s.bundle, i), R, X, D, lam, w1, w2, w3, w4)) return;
+    MemberDrawS mb;
+    const bool bundled = s.bundle > 1;
+    if (bundled) mb = member_draw_s(P, s.bsig, src, i);
+    optics_ds(P, X, D, lam, w1, w2, w3, w4, R, bundled ? &mb : nullptr);
 }
 
 }  // namespace phosim

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
                     int rej = -1;
                     if constexpr (DS) {
                         float lam = 0.f;
-                        if (valid) rej = early_reject_surface_f(P, ss, src, first + k, lam);
+                        if (valid) rej = early_reject_surface_f(P, ss, src, ray_of(ss.bundle, first + k), lam);
                         R.x = R.y = R.xc = R.yc = ds_f(0.f);
                         R.lam = lam;
                     } else {
@@ -227,6 +227,240 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
     if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
 }
 
+// ---------------------------------------------------------------------------------------------------------
+// The double-single path in two kernels.  One megakernel that samples, crosses the atmosphere and traces
+// the optics keeps the whole path's code and live state at once; on this GPU its FP32 instruction stream
+// outruns the instruction cache and its registers spill.  Split at the entrance plane of the telescope
+// (the staging of wavefront path tracers), each half has a smaller code footprint and fewer live values:
+//   ds_entry_kernel:  early rejection, sampling and the layers for the tiles of one chunk; survivors append
+//                     their entrance-plane state (64 bytes) to a buffer in device memory;
+//   ds_optics_kernel: the surfaces, the sensor and the accounting, one state per thread.
+// The per-photon arithmetic and its order are those of trace_photon_ds, so both give the same results.
+// ---------------------------------------------------------------------------------------------------------
+#ifndef PHOSIM_DS_ENTRY_MIN_BLOCKS
+#define PHOSIM_DS_ENTRY_MIN_BLOCKS 6
+#endif
+#ifndef PHOSIM_DS_OPTICS_MIN_BLOCKS
+#define PHOSIM_DS_OPTICS_MIN_BLOCKS 8
+#endif
+
+// A work unit of the two-kernel path is a photon, or for a bundle of n photons per ray (Sec. 3.2) a ray:
+// the ray is traced once and its photons (those in the call's range) only go through the sensor apart.
+__device__ __forceinline__ void unit_members(const DSource& s, uint32_t nb, uint64_t u, uint64_t& lo, uint32_t& nm) {
+    if (nb <= 1) { lo = u; nm = 1; return; }
+    const uint64_t a = max(s.first, u * nb), b = min(s.first + s.count, (u + 1) * nb);
+    lo = a;
+    nm = b > a ? (uint32_t)(b - a) : 0u;
+}
+
+__global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kernel(const __grid_constant__ TraceParams P,
+                                                                                   const DSStage S) {
+    __shared__ uint32_t queue_mem[kWarpsPerBlock][64];
+    __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
+    __shared__ SourceS src_mem[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* queue = queue_mem[warp];
+    unsigned long long* cnt = cnt_mem[warp];
+    const unsigned lanes_below = (1u << lane) - 1u;
+    const bool early = (P.flags & PHOSIM_EARLY_REJECT) != 0;
+    if (lane < kNumCounters) cnt[lane] = 0;
+    __syncwarp();
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = S.tile_begin + atomicAdd(P.tile_counter, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= S.tile_end) break;
+        const int src = tile_source(P, t, lane);
+        const DSource& s = P.sources[src];
+        const uint64_t j = t - P.tile_prefix[src];
+        const uint64_t off = j * P.tile_photons;
+        const uint32_t count = (uint32_t)min((uint64_t)P.tile_photons, s.ucount - off);
+        const uint64_t ufirst = s.ufirst + off;
+        if (lane == 0) src_mem[warp] = source_s(s);
+        __syncwarp();
+        const SourceS& ss = src_mem[warp];
+        const uint32_t nb = ss.bundle;
+        TileAcc<true> A = {};
+        int queued = 0;
+        uint32_t base = 0;
+        for (;;) {
+            if (base < count) {
+                const uint32_t k = base + lane;
+                const bool valid = k < count;
+                const uint64_t u = ufirst + k;
+                uint64_t lo;
+                uint32_t nm;
+                unit_members(s, nb, u, lo, nm);
+                const unsigned traced = __reduce_add_sync(0xffffffffu, valid ? nm : 0u);
+                if (lane == 0) cnt[0] += traced;
+                bool go_on = valid;
+                if (early) {
+                    // stage 1: the early coating decision alone, for every photon of the unit
+                    int rej = -1;
+                    float lam = 0.f;
+                    if (valid) rej = early_reject_surface_f(P, ss, src, u, lam);
+                    go_on = valid && rej < 0;
+                    const bool dropped = valid && !go_on;
+                    if (__any_sync(0xffffffffu, dropped)) {
+                        PhotonOutS R;
+                        R.x = R.y = R.xc = R.yc = ds_f(0.f);
+                        R.lam = lam;
+                        R.pix = -1;
+                        R.flags = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
+                        for (uint32_t m = 0; m < nb; ++m)
+                            consume<true>(P, R, dropped && m < nm, s.rec_off + (lo + m - s.first), ss.ref_x, ss.ref_y,
+                                          lane, A, cnt);
+                    }
+                }
+                const unsigned gmask = __ballot_sync(0xffffffffu, go_on);
+                if (go_on) queue[queued + __popc(gmask & lanes_below)] = k;
+                queued += __popc(gmask);
+                base += 32;
+                __syncwarp();
+            }
+            const bool drained = base >= count;
+            if (queued >= 32 || (drained && queued > 0)) {
+                const int take = queued < 32 ? queued : 32;
+                queued -= take;
+                const bool v = lane < take;
+                const uint32_t kk = v ? queue[queued + lane] : 0u;
+                __syncwarp();
+                PhotonOutS Q;
+                Q.flags = 0; Q.pix = -1;
+                ds X[3], D[3];
+                float lam = 0.f;
+                uint4 w1, w2, w3, w4;
+                const uint64_t u = ufirst + kk;
+                const bool go = v && photon_entry_ds(P, ss, src, u, Q, X, D, lam, w1, w2, w3, w4);
+                // survivors append their state, a warp at a time
+                const unsigned amask = __ballot_sync(0xffffffffu, go);
+                unsigned long long slot = 0;
+                if (lane == 0 && amask) slot = atomicAdd(S.n_state, (unsigned long long)__popc(amask));
+                slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(amask & lanes_below);
+                if (go) {
+                    DSState e;
+                    e.x = X[0]; e.y = X[1]; e.z = X[2];
+                    e.nx = D[0]; e.ny = D[1]; e.nz = D[2];
+                    e.lam = lam;
+                    e.src = src;
+                    e.idx = u;
+                    S.state[slot] = e;
+                }
+                // units stopped here (by the dynamic transmission test when stage 1 is off): all their photons
+                const bool dropped = v && !go;
+                if (__any_sync(0xffffffffu, dropped)) {
+                    uint64_t lo;
+                    uint32_t nm;
+                    unit_members(s, nb, u, lo, nm);
+                    for (uint32_t m = 0; m < nb; ++m)
+                        consume<true>(P, Q, dropped && m < nm, s.rec_off + (lo + m - s.first), ss.ref_x, ss.ref_y, lane,
+                                      A, cnt);
+                }
+            }
+            if (drained && queued == 0) break;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
+}
+
+__global__ void __launch_bounds__(256, PHOSIM_DS_OPTICS_MIN_BLOCKS) ds_optics_kernel(const __grid_constant__ TraceParams P,
+                                                                                     const DSStage S) {
+    __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long* cnt = cnt_mem[warp];
+    if (lane < kNumCounters) cnt[lane] = 0;
+    __syncwarp();
+    const unsigned long long n = *S.n_state;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kWarpsPerBlock * 32ull;
+    for (unsigned long long b = ((unsigned long long)blockIdx.x * kWarpsPerBlock + warp) * 32ull; b < n; b += stride) {
+        const unsigned long long e = b + lane;
+        const bool v = e < n;
+        // the unit (photon or bundle ray) to the detector surface
+        DetectorHit H;
+        bool hit = false;
+        uint32_t lost_flags = 0;
+        float lam = 0.f;
+        int src = 0;
+        uint64_t u = 0;
+        uint32_t nb = 1;
+        uint4 w1 = make_uint4(0u, 0u, 0u, 0u), w2 = w1, w3 = w1, w4 = w1;
+        if (v) {
+            const DSState st = S.state[e];
+            src = st.src;
+            u = st.idx;
+            lam = st.lam;
+            nb = P.sources[src].bundle;
+            ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
+            optics_words(P, src, u, w1, w2, w3, w4);
+            hit = optics_to_detector_ds(P, X, D, st.lam, w2, w3, lost_flags, H);
+        }
+        const DSource& s = P.sources[src];
+        uint64_t lo;
+        uint32_t nm;
+        unit_members(s, nb, u, lo, nm);
+        const uint32_t n_loop = __reduce_max_sync(0xffffffffu, v ? nb : 0u);
+        // then each of its photons through the sensor and into the image
+        for (uint32_t m = 0; m < n_loop; ++m) {
+            const bool vm = v && m < nm;
+            const uint64_t i = lo + m;
+            PhotonOutS R;
+            R.flags = hit ? 0u : lost_flags; R.pix = -1; R.lam = lam;
+            R.x = R.y = R.xc = R.yc = ds_f(0.f);
+            if (vm && hit) {
+                MemberDrawS mb;
+                if (nb > 1) mb = member_draw_s(P, (float)s.bsig, src, i);
+                detect_ds(P, H, lam, w1, w2, w4, R, nb > 1 ? &mb : nullptr);
+            }
+            if (vm && P.records) {
+                phosim_photon_record rec;
+                rec.x = ds_value(R.x); rec.y = ds_value(R.y); rec.xc = ds_value(R.xc); rec.yc = ds_value(R.yc);
+                rec.lambda = (double)R.lam;
+                rec.flags = R.flags; rec.pix = R.pix;
+                P.records[s.rec_off + (i - s.first)] = rec;
+            }
+            const bool det = vm && (R.flags & PHOSIM_F_DETECTED);
+            const unsigned dmask = __ballot_sync(0xffffffffu, det);
+            if (det) {
+                const unsigned same = __match_any_sync(dmask, R.pix);
+                if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
+            }
+            if (lane == 0) cnt[1] += __popc(dmask);
+            const uint32_t reason = vm ? ((R.flags >> 8) & 0xffu) : 0u;
+#pragma unroll
+            for (int q = 1; q <= 8; ++q) {
+                const unsigned bq = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
+                if (lane == 0) cnt[1 + q] += __popc(bq);
+            }
+            // moment sums about the chief-ray position, reduced over the lanes of one source
+            if (P.moments && dmask) {
+                double mm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                if (det) {
+                    const double fx = (double)(R.x - ds_of(s.ref_x)).hi, fy = (double)(R.y - ds_of(s.ref_y)).hi;
+                    mm[0] = 1.0; mm[1] = fx; mm[2] = fy; mm[3] = fx * fx; mm[4] = fx * fy; mm[5] = fy * fy;
+                }
+                const int src0 = __shfl_sync(0xffffffffu, src, __ffs(dmask) - 1);
+                if (__all_sync(0xffffffffu, !det || src == src0)) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) mm[q] = warp_sum(mm[q]);
+                    if (lane == 0) {
+                        double* M = P.moments + (size_t)src0 * PHOSIM_MOMENT_WORDS;
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
+                    }
+                } else if (det) {
+                    double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
+}
+
 // Chief ray of each source (pupil centre, source centre direction, lambda_ref, no apertures): the
 // reference point of the moment sums.
 __global__ void chief_ray_kernel(const __grid_constant__ TraceParams P, DSource* sources, int n_src, double* moments) {
@@ -267,6 +501,24 @@ const void* trace_kernel_ptr(int mode) {
     return mode == kMixed ? (const void*)trace_kernel<kMixed> : (const void*)trace_kernel<kPlain>;
 }
 const void* chief_kernel_ptr() { return (const void*)chief_ray_kernel; }
+const void* ds_entry_kernel_ptr() { return (const void*)ds_entry_kernel; }
+const void* ds_optics_kernel_ptr() { return (const void*)ds_optics_kernel; }
+
+cudaError_t launch_ds_entry(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st) {
+    ds_entry_kernel<<<blocks, threads, 0, st>>>(P, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ds_optics(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st) {
+    ds_optics_kernel<<<blocks, threads, 0, st>>>(P, S);
+    return cudaGetLastError();
+}
+
+cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(entry_per_sm, ds_entry_kernel, threads, 0);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(optics_per_sm, ds_optics_kernel, threads, 0);
+}
 
 cudaError_t trace_occupancy(int mode, int threads, int* blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel_ptr(mode), threads, 0);

@@ -88,13 +88,20 @@ extern "C" phosim_status phosim_trace_noalloc(phosim_scene* sc, const phosim_sou
         if (q.kind == PHOSIM_SERSIC && (q.table < 0 || q.table >= sc->sersic_tables)) return PHOSIM_ERR_INVALID_ARGUMENT;
         if (!finite_value(q.xi) || !finite_value(q.eta) || q.xi * q.xi + q.eta * q.eta >= 1.0 || !(q.redshift > -1.0))
             return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (q.bundle < 0 || (q.bundle > 1 && !(q.bundle_sigma >= 0.0 && finite_value(q.bundle_sigma))))
+            return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (q.bundle > PHOSIM_MAX_BUNDLE) return PHOSIM_ERR_LIMIT;
         DSource& d = hs[i];
         std::memset(&d, 0, sizeof(d));
         d.kind = q.kind; d.sed = q.sed; d.table = q.table;
         d.xi = q.xi; d.eta = q.eta; d.zfac = 1.0 + q.redshift; d.t0 = q.t0; d.t_exp = q.t_exp;
         d.a = q.a; d.b = q.b; d.cpa = std::cos(q.pa); d.spa = std::sin(q.pa);
+        d.bundle = q.bundle > 1 ? (uint32_t)q.bundle : 1u;
+        d.bsig = q.bundle > 1 ? q.bundle_sigma : 0.0;
         d.first = first ? first[i] : 0;
         d.count = n_photons[i];
+        d.ufirst = d.first;
+        d.ucount = d.count;
         d.rec_off = rec;
         rec += n_photons[i];
         prefix[i + 1] = prefix[i] + (n_photons[i] + T - 1) / T;

@@ -115,12 +115,15 @@ class Sources:
     pa: np.ndarray               # position angle (rad)
     table: np.ndarray            # int32, Sersic radial table index
     n_photons: np.ndarray        # uint64
+    bundle: np.ndarray = None    # int32, photons per ray (Sec. 3.2 background optimisation); None or <= 1: one
+    bundle_sigma: np.ndarray = None   # float64, sigma (mm) of the spread of a ray's photons on the detector
 
     def __len__(self):
         return len(self.kind)
 
     def subset(self, idx):
-        return Sources(**{f.name: np.asarray(getattr(self, f.name))[idx] for f in dataclasses.fields(self)})
+        return Sources(**{f.name: (None if getattr(self, f.name) is None else np.asarray(getattr(self, f.name))[idx])
+                          for f in dataclasses.fields(self)})
 
 
 @dataclass
@@ -301,8 +304,21 @@ def point_sources(xi, eta, n_photons, sed=None, t0=0.0, t_exp=15.0):
 
 
 def concat_sources(parts: Sequence[Sources]) -> Sources:
-    return Sources(**{f.name: np.concatenate([np.asarray(getattr(p, f.name)) for p in parts])
-                      for f in dataclasses.fields(Sources)})
+    defaults = {"bundle": (np.int32, 1), "bundle_sigma": (np.float64, 0.0)}
+
+    def field(p, name):
+        v = getattr(p, name)
+        if v is None:
+            dt, fill = defaults[name]
+            return np.full(len(p), fill, dt)
+        return np.asarray(v)
+    out = {}
+    for f in dataclasses.fields(Sources):
+        if f.name in defaults and all(getattr(p, f.name) is None for p in parts):
+            out[f.name] = None
+        else:
+            out[f.name] = np.concatenate([field(p, f.name) for p in parts])
+    return Sources(**out)
 
 
 # ----------------------------------------------------------------------------------------------------------
@@ -468,9 +484,11 @@ def galaxy_and_star_catalog(n_sources, rng, half_field_deg=0.1, star_frac=0.7, l
     return src, temps, tables
 
 
-def background_nodes(n_photons, chip_half_mm, plate_arcsec_per_mm, sed_index, spacing_arcsec=15.0, t_exp=15.0):
+def background_nodes(n_photons, chip_half_mm, plate_arcsec_per_mm, sed_index, spacing_arcsec=15.0, t_exp=15.0,
+                     bundle=1, bundle_sigma_arcsec=0.0):
     """Diffuse sky as Gaussian sources (sigma = spacing) on a square grid every 15 arcsec covering the chip
-    plus one spacing of margin (Sec. 2.2.2); the photons are split equally."""
+    plus one spacing of margin (Sec. 2.2.2); the photons are split equally.  bundle > 1: each ray carries that
+    many photons, spread on the detector with a Gaussian of bundle_sigma_arcsec (Sec. 3.2)."""
     half = chip_half_mm * plate_arcsec_per_mm + spacing_arcsec
     k = int(math.ceil(half / spacing_arcsec))
     g = np.arange(-k, k + 1) * spacing_arcsec * ARCSEC
@@ -480,18 +498,23 @@ def background_nodes(n_photons, chip_half_mm, plate_arcsec_per_mm, sed_index, sp
     per[: int(n_photons - per.sum())] += np.uint64(1)
     return Sources(kind=np.full(n, GAUSS, np.int32), sed=np.full(n, sed_index, np.int32), xi=X.ravel(), eta=Y.ravel(),
                    redshift=np.zeros(n), t0=np.zeros(n), t_exp=np.full(n, t_exp), a=np.full(n, spacing_arcsec * ARCSEC),
-                   b=np.zeros(n), pa=np.zeros(n), table=np.zeros(n, np.int32), n_photons=per)
+                   b=np.zeros(n), pa=np.zeros(n), table=np.zeros(n, np.int32), n_photons=per,
+                   bundle=np.full(n, bundle, np.int32),
+                   bundle_sigma=np.full(n, bundle_sigma_arcsec / plate_arcsec_per_mm))
 
 
 def batched_scene(n_sources=10_000, background_photons=1_000_000_000, seed=4, fine_n=4096, coarse_n=1024,
-                  photon_scale=1.0):
+                  photon_scale=1.0, sky_bundle=8, sky_bundle_sigma_arcsec=5.0):
     """The batched workload: 10^4 stars and galaxies (counts log-uniform 1e2-1e7, ~5e9 photons) plus 1e9
     sky-background photons on 15 arcsec nodes, through the three-mirror optics and seven-layer atmosphere.
-    photon_scale multiplies every count (sub-sampled runs)."""
+    photon_scale multiplies every count (sub-sampled runs).  The sky uses the background optimisation of
+    Sec. 3.2: rays of sky_bundle photons (about the square root of the ~60 sky photons per pixel) spread by
+    sky_bundle_sigma_arcsec on the detector; sky_bundle = 1 traces every sky photon on its own."""
     d, surfaces, materials = three_mirror_optics()
     rng = np.random.default_rng(seed)
     src, temps, tables = galaxy_and_star_catalog(n_sources, rng)
-    sky = background_nodes(int(background_photons), 0.5 * 4096 * 0.01, d["plate_scale_arcsec_per_mm"], n_sources)
+    sky = background_nodes(int(background_photons), 0.5 * 4096 * 0.01, d["plate_scale_arcsec_per_mm"], n_sources,
+                           bundle=sky_bundle, bundle_sigma_arcsec=sky_bundle_sigma_arcsec)
     sources = concat_sources([src, sky])
     if photon_scale != 1.0:
         sources.n_photons = np.maximum(1, np.rint(sources.n_photons * photon_scale)).astype(np.uint64)

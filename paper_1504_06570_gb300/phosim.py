@@ -68,9 +68,10 @@ class Layer(C.Structure):
 
 
 class Source(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("sed", C.c_int32), ("table", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("kind", C.c_int32), ("sed", C.c_int32), ("table", C.c_int32), ("bundle", C.c_int32),
                 ("xi", C.c_double), ("eta", C.c_double), ("redshift", C.c_double), ("t0", C.c_double),
-                ("t_exp", C.c_double), ("a", C.c_double), ("b", C.c_double), ("pa", C.c_double)]
+                ("t_exp", C.c_double), ("a", C.c_double), ("b", C.c_double), ("pa", C.c_double),
+                ("bundle_sigma", C.c_double)]
 
 
 RECORD_DTYPE = np.dtype([("x", "<f8"), ("y", "<f8"), ("xc", "<f8"), ("yc", "<f8"), ("lam", "<f8"),
@@ -134,6 +135,9 @@ def sources_struct(src: I.Sources):
         s.xi = float(src.xi[i]); s.eta = float(src.eta[i]); s.redshift = float(src.redshift[i])
         s.t0 = float(src.t0[i]); s.t_exp = float(src.t_exp[i])
         s.a = float(src.a[i]); s.b = float(src.b[i]); s.pa = float(src.pa[i])
+        if src.bundle is not None:
+            s.bundle = int(src.bundle[i])
+            s.bundle_sigma = float(src.bundle_sigma[i]) if src.bundle_sigma is not None else 0.0
     return arr
 
 

@@ -49,7 +49,7 @@ def test_struct_layout_matches_header():
               "phosim_coating": (P.Coating, ["n_lambda", "table"]),
               "phosim_screen_scale": (P.ScreenScale, ["n", "phase"]),
               "phosim_layer": (P.Layer, ["n_scales", "scales"]),
-              "phosim_source": (P.Source, ["xi", "pa"])}
+              "phosim_source": (P.Source, ["bundle", "xi", "pa", "bundle_sigma"])}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "phosim.h"', "int main(void){"]
     for st, (_, fields) in checks.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')

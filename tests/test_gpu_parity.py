@@ -235,3 +235,35 @@ def test_invalid_sources_are_rejected():
         s.trace(img)
     assert e.value.code == -1
     s.close()
+
+
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED, P.MIXED_DS])
+def test_background_bundles(oracle_mod, precision):
+    """Sec. 3.2 background optimisation: a sky-like Gaussian source traced as bundles of 8 photons per ray
+    (ragged ranges included) against the oracle: in FP64 photon by photon, in the mixed precisions through the
+    moments; a bundle of one is the unbundled source."""
+    counts = [4003, 700, 2500]
+    src = G.mixed_sources(counts, seed=14)
+    src.kind = np.array([I.GAUSS, I.POINT, I.GAUSS], np.int32)
+    src.a = np.array([6e-5, 0.0, 3e-5])
+    src.bundle = np.array([8, 1, 3], np.int32)
+    src.bundle_sigma = np.array([0.003, 0.0, 0.01])
+    sc = G.test_system_scene(sources=src)
+    first = np.array([5, 0, 1], np.uint64)
+    # photon fates are compared in full, so no dynamic transmission test (it renames some losses) in FP64
+    gpu = G.run_gpu(sc, precision, early_reject=precision != P.PLAIN_FP64, first=first)
+    ora = G.oracle_trace(oracle_mod, sc, first=first)
+    if precision == P.PLAIN_FP64:
+        r = G.compare_records(sc, gpu, ora)
+        assert r["max_err_px"] < 1e-6, r
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
+    else:
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+    assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
+    # one photon per ray: exactly the unbundled trace
+    sc.sources.bundle = np.array([1, 1, 1], np.int32)
+    one = G.run_gpu(sc, precision, early_reject=True, first=first)
+    sc.sources.bundle = None
+    sc.sources.bundle_sigma = None
+    none = G.run_gpu(sc, precision, early_reject=True, first=first)
+    assert np.array_equal(one["rec"], none["rec"])

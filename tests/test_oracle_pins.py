@@ -583,3 +583,68 @@ def test_bleeding_conserves_charge_and_respects_the_implant(oracle_mod):
     for half in (slice(0, 32), slice(32, 64)):
         before, after = img[:, half].sum(1).astype(np.int64), out[:, half].sum(1).astype(np.int64)
         assert np.all(after <= before) and np.all((after == before) | (after == w * 32))
+
+
+def _philox_uniform(oracle_mod, i, src, blk, seed):
+    """The four uniforms of block blk of photon i's counter, from the oracle's Philox (itself pinned to the
+    published known answers)."""
+    w = oracle_mod.philox([i & 0xFFFFFFFF, i >> 32, src, blk], [seed & 0xFFFFFFFF, seed >> 32])
+    return [(x + 0.5) * 2.0 ** -32 for x in w]
+
+
+def test_background_bundle_follows_its_ray_and_spreads(oracle_mod):
+    """Sec. 3.2 background optimisation: photon i of a bundle of n follows ray i // n to the detector surface
+    (the unbundled photon of that index, sensor off) and lands at a Gaussian offset drawn by Box-Muller from
+    block 5 of its own counter; with one photon per ray nothing changes."""
+    sc = I.paraboloid_scene(n_photons=2000, atmosphere=True, sensor=False, screen_n=128)
+    plain = oracle_mod.Oracle(sc).trace(n_threads=4)
+    n_b, sig = 8, 0.004
+    sc_b = I.paraboloid_scene(n_photons=2000, atmosphere=True, sensor=False, screen_n=128)
+    sc_b.sources.bundle = np.array([n_b], np.int32)
+    sc_b.sources.bundle_sigma = np.array([sig])
+    bund = oracle_mod.Oracle(sc_b).trace(n_threads=4)
+    ones = I.paraboloid_scene(n_photons=2000, atmosphere=True, sensor=False, screen_n=128)
+    ones.sources.bundle = np.array([1], np.int32)
+    ones.sources.bundle_sigma = np.array([sig])
+    same = oracle_mod.Oracle(ones).trace(n_threads=4)
+    assert np.array_equal(same["x"], plain["x"]) and np.array_equal(same["flags"], plain["flags"])
+    checked = 0
+    for i in range(0, 2000, 37):
+        r = i // n_b
+        if not (plain["flags"][r] & 1) or not (bund["flags"][i] & 1):
+            continue
+        ua, ub = _philox_uniform(oracle_mod, i, 0, 5, sc.seed)[:2]
+        g = math.sqrt(-2.0 * math.log(ua))
+        sx, sy = sig * g * math.cos(2 * math.pi * ub), sig * g * math.sin(2 * math.pi * ub)
+        assert abs(bund["x"][i] - (plain["x"][r] + sx)) < 1e-12
+        assert abs(bund["y"][i] - (plain["y"][r] + sy)) < 1e-12
+        assert bund["lam"][i] == plain["lam"][r]
+        checked += 1
+    assert checked > 40
+    # the offsets are Gaussian with the given sigma
+    det = (bund["flags"] & 1) == 1
+    ray_x = plain["x"][np.arange(2000) // n_b]
+    dx = (bund["x"] - ray_x)[det & ((plain["flags"][np.arange(2000) // n_b] & 1) == 1)]
+    assert abs(dx.std() / sig - 1.0) < 0.06 and abs(dx.mean()) < 4 * sig / math.sqrt(len(dx))
+
+
+def test_background_bundles_keep_the_mean_image(oracle_mod):
+    """A diffuse source traced one photon per ray and eight photons per ray (spread over a few pixels) gives
+    the same mean image: counts in coarse bins agree within Poisson errors (the bundle's correlated photons
+    raise the variance by at most the bundle size)."""
+    def scene(bundle):
+        sc = I.paraboloid_scene(n_photons=60000, atmosphere=False, sensor=True)
+        sc.sources = I.Sources(kind=np.array([I.GAUSS], np.int32), sed=np.zeros(1, np.int32), xi=np.zeros(1),
+                               eta=np.zeros(1), redshift=np.zeros(1), t0=np.zeros(1), t_exp=np.ones(1),
+                               a=np.array([4e-5]), b=np.array([4e-5]), pa=np.zeros(1), table=np.zeros(1, np.int32),
+                               n_photons=np.array([60000], np.uint64), bundle=np.array([bundle], np.int32),
+                               bundle_sigma=np.array([0.02]))
+        return sc
+    a = oracle_mod.Oracle(scene(1)).trace(n_threads=8)["image"].astype(float)
+    b = oracle_mod.Oracle(scene(8)).trace(n_threads=8)["image"].astype(float)
+    A = a.reshape(16, 16, 16, 16).sum(axis=(1, 3))
+    B = b.reshape(16, 16, 16, 16).sum(axis=(1, 3))
+    assert abs(A.sum() - B.sum()) < 5 * math.sqrt(A.sum())
+    m = (A + B) > 50
+    chi2 = ((A - B)[m] ** 2 / (A + B)[m]).sum() / m.sum()
+    assert chi2 < 8.0, chi2

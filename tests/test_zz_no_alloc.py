@@ -55,3 +55,29 @@ def test_noalloc_matches_trace_twice_in_a_row():
     host = torch.zeros((d.ny, d.nx), dtype=torch.int32)
     assert _call(L, s, host, rec, mom, stream) == -1
     s.close()
+
+
+def test_noalloc_double_single_matches_two_kernel_trace():
+    """In the double-single precision the allocation-free entry runs the one-kernel form of the path and
+    phosim_trace the two-kernel form (entry stage, states in device memory, optics stage): the same
+    per-photon arithmetic, so identical records and images; the moment sums differ only by the order of the
+    single-precision partial sums."""
+    L = P.lib()
+    L.phosim_trace_noalloc.argtypes = [C.c_void_p, C.POINTER(P.Source), C.c_int, C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_uint64), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    counts = [0, 1, 31, 33, 1000, 4097, 3000]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=13), hf=True)
+    n = int(np.sum(counts))
+    ref = G.run_gpu(sc, P.MIXED_DS, early_reject=True)
+    s = P.Scene(sc, P.MIXED_DS, early_reject=True)
+    stream = torch.cuda.current_stream().cuda_stream
+    d = sc.detector
+    img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+    rec = torch.zeros(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    mom = torch.zeros((len(counts), P.MOMENT_WORDS), dtype=torch.float64, device="cuda")
+    assert _call(L, s, img, rec, mom, stream) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(img.cpu().numpy().view(np.uint32), ref["image"])
+    assert np.array_equal(P.records_to_numpy(rec), ref["rec"])
+    np.testing.assert_allclose(mom.cpu().numpy(), ref["moments"], rtol=1e-5, atol=1e-6)
+    s.close()
