@@ -429,11 +429,11 @@ def main():
         import ctypes as C
         L = P.lib()
         L.phosim_set_stage_timing(scene.h, 1)
-        acc = np.zeros(4)
-        ms = (C.c_double * 4)()
+        acc = np.zeros(5)
+        ms = (C.c_double * 5)()
         for _ in range(steps):
             scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
-            if L.phosim_stage_times(scene.h, ms, 4) != 0:
+            if L.phosim_stage_times(scene.h, ms, 5) != 0:
                 raise RuntimeError("phosim_stage_times failed")
             acc += np.array(ms[:])
         L.phosim_set_stage_timing(scene.h, 0)

@@ -42,6 +42,7 @@ typedef int phosim_status;
 #define PHOSIM_MAX_ZERNIKE 28        /* Noll j <= 28: radial order <= 6 */
 #define PHOSIM_MAX_COATED 6          /* coated surfaces with an accept-reject draw */
 #define PHOSIM_MAX_BUNDLE 4096       /* photons per ray of a background bundle */
+#define PHOSIM_MAX_GHOST_BOUNCES 8   /* coating reflections a ghost photon may undergo */
 
 /* surface kinds, materials, source kinds (Sec. 2.4.1, 2.2) */
 enum { PHOSIM_MIRROR = 0, PHOSIM_REFRACT = 1, PHOSIM_DETECTOR = 2 };
@@ -133,12 +134,21 @@ typedef struct phosim_material {
     double B[3], C[3];
 } phosim_material;
 
-/* transmission probability, piecewise constant in (lambda, incidence angle) (Sec. 2.4.2) */
+/* transmission probability, piecewise constant in (lambda, incidence angle) (Sec. 2.4.2), and optionally the
+   reflection probability on the same grid (the four-column coating interface: T and R against wavelength and
+   angle).  A photon meeting a coated refracting surface is transmitted with probability T, reflected with
+   probability R (a ghost: it travels back through the surfaces, refracting and meeting coatings on its way,
+   until another reflection turns it round; after a photon's first reflection each coating decision draws the
+   next word of Philox blocks 7, 8, ... of the photon's (or its ray's) counter; a photon reflected more than
+   PHOSIM_MAX_GHOST_BOUNCES times, leaving the first surface backwards or missing a surface is MISSED) and
+   absorbed otherwise; on a mirror T is the reflectance and the rest is absorbed.  Ghosts are not available to
+   phosim_grad (UNSUPPORTED). */
 typedef struct phosim_coating {
     double lam0, dlam;          /* nm */
     double theta0, dtheta;      /* rad */
     int32_t n_lambda, n_theta;
     const double* table;        /* host, n_lambda x n_theta, row-major */
+    const double* reflect;      /* host, n_lambda x n_theta, or NULL (no reflection); table + reflect <= 1 */
 } phosim_coating;
 
 /* One frozen-flow layer (Sec. 2.3.1): up to two screen scales whose gradients add. */

@@ -38,9 +38,9 @@ phosim_status phosim_ds_eval(int op, const double* a, const double* b, double* o
    one by one (no CUDA graph) with a CUDA event recorded on the call's stream before and after each launch.
    phosim_stage_times waits for the events of the scene's last phosim_trace call and returns the summed
    milliseconds of each kernel: ms[0] chief rays, ms[1] the one-kernel trace (PHOSIM_PLAIN_FP64,
-   PHOSIM_MIXED), ms[2] the entry stage and ms[3] the optics stage of the two-kernel double-single path
-   (PHOSIM_MIXED_DS); kernels the call did not launch read 0.  n >= 4.
-   Errors: INVALID_ARGUMENT (null scene or output, n < 4), CUDA. */
+   PHOSIM_MIXED), ms[2] the entry stage, ms[3] the optics stage and ms[4] the bundle stage (background
+   bundles) of the two-kernel double-single path (PHOSIM_MIXED_DS); kernels the call did not launch read 0.
+   n >= 5.  Errors: INVALID_ARGUMENT (null scene or output, n < 5), CUDA. */
 phosim_status phosim_set_stage_timing(phosim_scene* scene, int on);
 phosim_status phosim_stage_times(phosim_scene* scene, double* ms, int n);
 

@@ -70,10 +70,15 @@ class Oracle:
         self._keep = []
         for m in scene.materials:
             L.oracle_add_material(self.h, C.c_int(m.kind), _dp(m.B), _dp(m.C))
+        self._coat_keep = []
         for c in scene.coatings:
             T = _arr(c.table, np.float64)
+            R = getattr(c, "reflect", None)
+            R = None if R is None else _arr(R, np.float64)
+            self._coat_keep.append((T, R))
             L.oracle_add_coating(self.h, C.c_double(c.lam0), C.c_double(c.dlam), C.c_double(c.theta0),
-                                 C.c_double(c.dtheta), C.c_int(T.shape[0]), C.c_int(T.shape[1]), _dp(T))
+                                 C.c_double(c.dtheta), C.c_int(T.shape[0]), C.c_int(T.shape[1]), _dp(T),
+                                 None if R is None else _dp(R))
         for s in scene.surfaces:
             self._add_surface(s)
         d = scene.detector

@@ -146,7 +146,7 @@ struct Surf {
     std::vector<double> zern;      // Noll c_1 ..
 };
 struct Mat { int kind; double B[3], C[3]; };
-struct Coat { double lam0, dlam, th0, dth; int nl, nt; std::vector<double> T; };
+struct Coat { double lam0, dlam, th0, dth; int nl, nt; std::vector<double> T, R; };   // R empty: no reflection
 struct Scale { double pixel; int N; std::vector<double> phase; };
 struct Layer { double z, vx, vy; std::vector<Scale> scales; };
 
@@ -435,10 +435,16 @@ bool refract(T d[3], const T Nin[3], T n1, T n2) {
 // ------------------------------------------------------------------------------------------------------
 // photon
 // ------------------------------------------------------------------------------------------------------
-struct Draws { uint32_t w[N_SLOTS]; };
+struct Draws {
+    uint32_t w[N_SLOTS];
+    const Scene* sc;
+    int src;
+    uint64_t i;
+};
 
 Draws draw_photon(const Scene& sc, int src_id, uint64_t i) {
     Draws D;
+    D.sc = &sc; D.src = src_id; D.i = i;
     for (uint32_t blk = 0; blk < 5; ++blk) {
         uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(i >> 32), (uint32_t)src_id, blk};
         philox4x32_10(ctr, (uint32_t)sc.seed, (uint32_t)(sc.seed >> 32), &D.w[4 * blk]);
@@ -467,6 +473,15 @@ Member member_draws(const Scene& sc, int src_id, uint64_t i, double sigma) {
 inline int bundle_of(const Scene& sc, int s) {
     return (s < (int)sc.bundle_n.size() && sc.bundle_n[s] > 1) ? sc.bundle_n[s] : 1;
 }
+
+// Ghosts (Sec. 2.4.2): after a photon's first reflection by a coating, each coated-surface decision takes the
+// next word of blocks 7, 8, ... of its counter (word n of block 7 + n / 4).
+uint32_t ghost_word(const Draws& D, int n) {
+    uint32_t ctr[4] = {(uint32_t)D.i, (uint32_t)(D.i >> 32), (uint32_t)D.src, (uint32_t)(7 + n / 4)}, w[4];
+    philox4x32_10(ctr, (uint32_t)D.sc->seed, (uint32_t)(D.sc->seed >> 32), w);
+    return w[n % 4];
+}
+constexpr int kMaxGhostBounces = 8;
 
 inline void min_margin(double& m, double v) { v = std::fabs(v); if (v < m) m = v; }
 
@@ -608,7 +623,12 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
     int coat_k = 0;
     out.flags = 0; out.pix = -1; out.margin_mm = 1e300; out.margin_nm = 1e300;
     out.x = T(0.0); out.y = T(0.0); out.xc = out.yc = 0.0;
-    for (size_t si = 0; si < ST.size(); ++si) {
+    // Surfaces are met in order (dir = +1); a photon reflected by a refracting surface's coating (a ghost)
+    // travels back through them (dir = -1) until another reflection turns it round again.
+    int si = 0, dir = 1, bounces = 0, n_ghost = 0;
+    const int n_surf = (int)ST.size();
+    for (;;) {
+        if (si < 0 || si >= n_surf) { out.flags = lost_flag(LOST_MISSED, si < 0 ? 0 : n_surf); return; }
         const SurfT<T>& st = ST[si];
         const Surf& s = *st.s;
         // into the frame of the optic
@@ -620,6 +640,8 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
         T l;
         uint32_t why = intersect(st, p, dl, l);
         if (why) { out.flags = lost_flag(why, (int)si); return; }
+        // a ghost only meets surfaces ahead of it
+        if (bounces > 0 && !(val(l) > 0.0)) { out.flags = lost_flag(LOST_MISSED, (int)si); return; }
         for (int i = 0; i < 3; ++i) p[i] = p[i] + l * dl[i];
         T zs, zx, zy;
         surface_sag(st, p[0], p[1], zs, zx, zy);
@@ -723,15 +745,37 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
             min_margin(out.margin_nm, (fl - std::round(fl)) * C.dlam);
             int il = std::min(C.nl - 1, std::max(0, (int)std::floor(fl)));
             int it = std::min(C.nt - 1, std::max(0, (int)std::floor(ft)));
-            double Tr = C.T[(size_t)il * C.nt + it];
-            double u = D ? uniform01(D->w[S_COAT0 + coat_k]) : 0.0;
-            ++coat_k;
-            if (!(u < Tr)) { out.flags = lost_flag(LOST_COATING, (int)si); return; }
+            const size_t ix = (size_t)il * C.nt + it;
+            const double Tr = C.T[ix], Rr = C.R.empty() ? 0.0 : C.R[ix];
+            // the first pass takes the coated surface's own slot; after a ghost reflection, the ghost words
+            double u = 0.0;
+            if (D) u = uniform01(bounces == 0 ? D->w[S_COAT0 + coat_k] : ghost_word(*D, n_ghost++));
+            if (bounces == 0) ++coat_k;
+            if (!(u < Tr)) {
+                // reflected backwards (a ghost) with probability R, absorbed otherwise
+                if (s.kind == K_MIRROR || !(u < Tr + Rr)) { out.flags = lost_flag(LOST_COATING, (int)si); return; }
+                reflect(dl, N);
+                dir = -dir;
+                if (++bounces > kMaxGhostBounces) { out.flags = lost_flag(LOST_MISSED, (int)si); return; }
+                for (int i = 0; i < 3; ++i) {
+                    x[i] = st.M[0][i] * p[0] + st.M[1][i] * p[1] + st.M[2][i] * p[2] + st.o[i];
+                    d[i] = st.M[0][i] * dl[0] + st.M[1][i] * dl[1] + st.M[2][i] * dl[2];
+                }
+                si += dir;
+                continue;
+            }
         }
         if (s.kind == K_MIRROR) {
             reflect(dl, N);
         } else {
-            T n_next = refractive_index_t<T>(sc, s.material, lamT);
+            // the medium beyond the surface in the direction of travel
+            int m_next = s.material;
+            if (dir < 0) {
+                m_next = -1;
+                for (int j = 0; j < si; ++j)
+                    if (sc.surf[j].kind != K_MIRROR) m_next = sc.surf[j].material;
+            }
+            T n_next = m_next < 0 ? T(1.0) : refractive_index_t<T>(sc, m_next, lamT);
             if (!refract(dl, N, n_cur, n_next)) { out.flags = lost_flag(LOST_TIR, (int)si); return; }
             n_cur = n_next;
         }
@@ -740,8 +784,8 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
             x[i] = st.M[0][i] * p[0] + st.M[1][i] * p[1] + st.M[2][i] * p[2] + st.o[i];
             d[i] = st.M[0][i] * dl[0] + st.M[1][i] * dl[1] + st.M[2][i] * dl[2];
         }
+        si += dir;
     }
-    out.flags = lost_flag(LOST_MISSED, (int)ST.size());
 }
 
 template <class T>
@@ -811,10 +855,12 @@ int oracle_add_material(void* p, int kind, const double* B, const double* C) {
     sc->mat.push_back(m);
     return (int)sc->mat.size() - 1;
 }
-int oracle_add_coating(void* p, double lam0, double dlam, double th0, double dth, int nl, int nt, const double* T) {
+int oracle_add_coating(void* p, double lam0, double dlam, double th0, double dth, int nl, int nt, const double* T,
+                       const double* R) {
     Scene* sc = (Scene*)p;
     Coat c; c.lam0 = lam0; c.dlam = dlam; c.th0 = th0; c.dth = dth; c.nl = nl; c.nt = nt;
     c.T.assign(T, T + (size_t)nl * nt);
+    if (R) c.R.assign(R, R + (size_t)nl * nt);
     sc->coat.push_back(c);
     return (int)sc->coat.size() - 1;
 }

@@ -48,9 +48,10 @@ phosim_status upload(std::vector<void*>& owner, const T* host, size_t n, T** out
 bool is_finite(double v) { return std::isfinite(v); }
 
 // device counter words of a scene: [0] tile counter, [1 .. kNumCounters] launch counters, then the state
-// count of the two-kernel double-single path
+// and bundle-hit counts of the two-kernel double-single path
 constexpr int kStateCountWord = 1 + kNumCounters;
-constexpr int kCounterWords = kStateCountWord + 1;
+constexpr int kHitCountWord = kStateCountWord + 1;
+constexpr int kCounterWords = kHitCountWord + 1;
 // photons per chunk of the two-kernel path: its state buffer holds one chunk (64 bytes a photon, 8.6 GB)
 constexpr uint64_t kStateChunk = 1ull << 27;
 
@@ -470,6 +471,7 @@ void phosim_destroy_scene(phosim_scene* sc) {
     cudaFree(sc->d_counters);
     cudaFree(sc->d_stage);
     cudaFree(sc->d_state);
+    cudaFree(sc->d_hits);
     cudaFree(sc->d_grad_scratch);
     cudaFree(sc->d_mom_scratch);
     for (TraceGraph& g : sc->graphs) destroy_graph(g);
@@ -497,10 +499,15 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
     }
     for (int k = 0; k < n_mat; ++k)
         if (mats[k].kind < PHOSIM_VACUUM || mats[k].kind > PHOSIM_SILICON) return PHOSIM_ERR_INVALID_ARGUMENT;
-    for (int k = 0; k < n_coat; ++k)
+    for (int k = 0; k < n_coat; ++k) {
         if (!coats[k].table || coats[k].n_lambda < 1 || coats[k].n_theta < 1 || !(coats[k].dlam > 0.0) ||
             !(coats[k].dtheta > 0.0))
             return PHOSIM_ERR_INVALID_ARGUMENT;
+        if (coats[k].reflect)
+            for (size_t i = 0; i < (size_t)coats[k].n_lambda * coats[k].n_theta; ++i)
+                if (!(coats[k].reflect[i] >= 0.0) || !(coats[k].table[i] + coats[k].reflect[i] <= 1.0 + 1e-12))
+                    return PHOSIM_ERR_INVALID_ARGUMENT;
+    }
     TraceParams P = sc->base;
     int coated = 0;
     for (int i = 0; i < n_surf; ++i) {
@@ -529,32 +536,54 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
         }
     }
     std::vector<void*> mem;
+    bool ghosts = false;
     for (int k = 0; k < n_coat; ++k) {
         double *d, *dmax;
         unsigned long long *dthr, *dmax_thr;
         const int nl = coats[k].n_lambda, nt = coats[k].n_theta;
-        std::vector<double> tmax((size_t)nl, 0.0);
-        std::vector<unsigned long long> thr((size_t)nl * nt), tmax_thr((size_t)nl);
+        // the dynamic transmission test (early rejection) keeps a photon while it can still be transmitted or,
+        // with a reflection table, reflected: its bound is the largest T + R over angles
+        const double* R = coats[k].reflect;
+        std::vector<double> tr((size_t)nl * nt), tmax((size_t)nl, 0.0);
+        for (size_t i = 0; i < tr.size(); ++i) tr[i] = coats[k].table[i] + (R ? R[i] : 0.0);
+        std::vector<unsigned long long> thr((size_t)nl * nt), tr_thr((size_t)nl * nt), tmax_thr((size_t)nl);
         for (int il = 0; il < nl; ++il)
-            for (int it = 0; it < nt; ++it) tmax[il] = std::max(tmax[il], coats[k].table[(size_t)il * nt + it]);
+            for (int it = 0; it < nt; ++it) tmax[il] = std::max(tmax[il], tr[(size_t)il * nt + it]);
         for (size_t i = 0; i < thr.size(); ++i) thr[i] = accept_threshold(coats[k].table[i]);
+        for (size_t i = 0; i < tr.size(); ++i) tr_thr[i] = accept_threshold(tr[i]);
         for (int il = 0; il < nl; ++il) tmax_thr[il] = accept_threshold(tmax[il]);
+        double* dtr = nullptr;
+        unsigned long long* dtr_thr = nullptr;
         phosim_status st = upload(mem, coats[k].table, (size_t)nl * nt, &d);
         if (st == PHOSIM_OK) st = upload(mem, tmax.data(), tmax.size(), &dmax);
         if (st == PHOSIM_OK) st = upload(mem, thr.data(), thr.size(), &dthr);
         if (st == PHOSIM_OK) st = upload(mem, tmax_thr.data(), tmax_thr.size(), &dmax_thr);
+        if (st == PHOSIM_OK && R) st = upload(mem, tr.data(), tr.size(), &dtr);
+        if (st == PHOSIM_OK && R) st = upload(mem, tr_thr.data(), tr_thr.size(), &dtr_thr);
         if (st != PHOSIM_OK) { free_all(mem); return st; }
+        if (R) ghosts = true;
         DCoating& C = P.coat[k];
         C.lam0 = coats[k].lam0; C.inv_dlam = 1.0 / coats[k].dlam;
         C.th0 = coats[k].theta0; C.inv_dth = 1.0 / coats[k].dtheta;
         C.lam0f = (float)C.lam0; C.inv_dlamf = (float)C.inv_dlam; C.th0f = (float)C.th0; C.inv_dthf = (float)C.inv_dth;
         C.T_thr = dthr;
         C.Tmax_thr = dmax_thr;
+        C.TR = dtr;
+        C.TR_thr = dtr_thr;
         C.nl = coats[k].n_lambda; C.nt = coats[k].n_theta;
         C.T = d;
         C.Tmax = dmax;
     }
     P.n_coat = n_coat;
+    P.flags = ghosts ? (P.flags | kGhostFlag) : (P.flags & ~kGhostFlag);
+    // the medium in front of each surface, for ghosts that refract on their way back
+    {
+        int m = -1;
+        for (int i = 0; i < n_surf; ++i) {
+            P.surf[i].mat_before = m;
+            if (surf[i].kind != PHOSIM_MIRROR) m = surf[i].material;
+        }
+    }
     {
         std::vector<double> zm((size_t)PHOSIM_MAX_ZERNIKE * kZPoly, 0.0);
         for (int j = 1; j <= PHOSIM_MAX_ZERNIKE; ++j) {
@@ -801,7 +830,7 @@ phosim_status phosim_set_stage_timing(phosim_scene* sc, int on) {
 }
 
 phosim_status phosim_stage_times(phosim_scene* sc, double* ms, int n) {
-    if (!sc || !ms || n < 4) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!sc || !ms || n < 5) return PHOSIM_ERR_INVALID_ARGUMENT;
     for (int k = 0; k < n; ++k) ms[k] = 0.0;
     for (int k = 0; k < sc->timing_used; ++k) {
         CU(cudaEventSynchronize(sc->timing_events[2 * k + 1]));
@@ -830,12 +859,14 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     const int mode = sc->precision;
     const bool staged = mode == PHOSIM_MIXED_DS;        // the two-kernel double-single path
     // launch shape
-    int per_sm = 0, per_sm_optics = 0;
-    if (staged) CU(ds_stage_occupancy(sc->threads, &per_sm, &per_sm_optics));
+    int per_sm = 0, per_sm_optics = 0, per_sm_members = 0;
+    if (staged) CU(ds_stage_occupancy(sc->threads, &per_sm, &per_sm_optics, &per_sm_members));
     else CU(trace_occupancy(mode, sc->threads, &per_sm));
     per_sm = std::max(per_sm, 1);
     per_sm_optics = std::max(per_sm_optics, 1);
+    per_sm_members = std::max(per_sm_members, 1);
     const int blocks = sc->sm_count * per_sm, blocks_optics = sc->sm_count * per_sm_optics;
+    const int blocks_members = sc->sm_count * per_sm_members;
     const uint64_t warps = (uint64_t)blocks * (sc->threads / 32);
     uint64_t total = 0;
     for (int s = 0; s < n_src; ++s) total += n_photons[s];
@@ -847,7 +878,7 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     // sources and per-source tile prefix
     std::vector<DSource> hs((size_t)n_src);
     std::vector<unsigned long long> prefix((size_t)n_src + 1, 0);
-    uint64_t rec = 0;
+    uint64_t rec = 0, bundled_units = 0;
     for (int s = 0; s < n_src; ++s) {
         const phosim_source& q = src[s];
         if (q.kind < PHOSIM_POINT || q.kind > PHOSIM_GAUSS) return PHOSIM_ERR_INVALID_ARGUMENT;
@@ -875,6 +906,7 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         if (staged && d.bundle > 1 && d.count > 0) {
             d.ufirst = d.first / d.bundle;
             d.ucount = (d.first + d.count + d.bundle - 1) / d.bundle - d.ufirst;
+            bundled_units += d.ucount;
         }
         prefix[s + 1] = prefix[s] + (d.ucount + T - 1) / T;
     }
@@ -920,6 +952,13 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
             sc->d_state = nullptr; sc->cap_state = 0;
             CU(cudaMalloc(&sc->d_state, need * sizeof(DSState)));
             sc->cap_state = need;
+        }
+        const size_t need_hits = (size_t)std::min<uint64_t>(bundled_units, chunk_tiles * T);
+        if (sc->cap_hits < need_hits) {
+            cudaFree(sc->d_hits);
+            sc->d_hits = nullptr; sc->cap_hits = 0;
+            CU(cudaMalloc(&sc->d_hits, need_hits * sizeof(DSHit)));
+            sc->cap_hits = need_hits;
         }
     }
     CU(cudaMemsetAsync(sc->d_counters, 0, kCounterWords * sizeof(unsigned long long), st));
@@ -968,15 +1007,19 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         DSStage S;
         S.state = sc->d_state;
         S.n_state = sc->d_counters + kStateCountWord;
+        S.hits = sc->d_hits;
+        S.n_hits = sc->d_counters + kHitCountWord;
         S.tile_begin = 0;
         S.tile_end = std::min(n_tiles, chunk_tiles);
         void* stage_args[2] = {&P, &S};
         const dim3 block((unsigned)sc->threads);
+        const bool bundles = bundled_units > 0;
         if (use_graph && chunk_tiles >= n_tiles) {
-            const KernelLaunch L[3] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
+            const KernelLaunch L[4] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
                                        {ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, stage_args},
-                                       {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics), block, stage_args}};
-            phosim_status gs = launch_graph(sc, mode, L, 3, st);
+                                       {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics), block, stage_args},
+                                       {ds_members_kernel_ptr(), dim3((unsigned)blocks_members), block, stage_args}};
+            phosim_status gs = launch_graph(sc, mode, L, bundles ? 4 : 3, st);
             if (gs != PHOSIM_OK) return gs;
         } else {
             phosim_status ls = timed(0, [&] { return launch_chief_rays(P, sc->d_src, n_src, moments, st); });
@@ -986,10 +1029,12 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
                 S.tile_end = std::min(n_tiles, t0 + chunk_tiles);
                 if (t0 > 0) {
                     CU(cudaMemsetAsync(sc->d_counters, 0, sizeof(unsigned long long), st));
-                    CU(cudaMemsetAsync(sc->d_counters + kStateCountWord, 0, sizeof(unsigned long long), st));
+                    CU(cudaMemsetAsync(sc->d_counters + kStateCountWord, 0, 2 * sizeof(unsigned long long), st));
                 }
                 ls = timed(2, [&] { return launch_ds_entry(P, S, blocks, sc->threads, st); });
                 if (ls == PHOSIM_OK) ls = timed(3, [&] { return launch_ds_optics(P, S, blocks_optics, sc->threads, st); });
+                if (ls == PHOSIM_OK && bundles)
+                    ls = timed(4, [&] { return launch_ds_members(P, S, blocks_members, sc->threads, st); });
                 if (ls != PHOSIM_OK) return ls;
             }
         }
@@ -1009,6 +1054,7 @@ phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src,
         return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
     if (n_params > kMaxGradParams) return PHOSIM_ERR_LIMIT;
+    if (sc->base.flags & kGhostFlag) return PHOSIM_ERR_UNSUPPORTED;   // the adjoint follows forward paths only
     const TraceParams& B = sc->base;
     GradParams G;
     std::memset(&G, 0, sizeof(G));

@@ -23,7 +23,9 @@ enum SurfFlags : int { SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FL
 
 struct DSurface {
     int kind, material, coating, coat_slot;   // coat_slot: index of this surface's accept draw, -1 none
-    int flags, pad0, pad1, pad2;
+    int flags;
+    int mat_before;                           // medium in front of the surface (material index, -1 vacuum)
+    int pad1, pad2;
     double c, k1c2, kc;                       // 1/R, (1 + kappa) / R^2, (1 + kappa) / R
     double ae[4];                             // alpha_4, alpha_6, alpha_8, alpha_10
     double ao[4];                             // alpha_3, alpha_5, alpha_7, alpha_9
@@ -63,7 +65,13 @@ struct DCoating {
     const double* Tmax;                       // nl: the largest transmission over angles at each wavelength
     const unsigned long long* T_thr;          // the same as integer thresholds ceil(T 2^32 - 1/2) on the draw
     const unsigned long long* Tmax_thr;
+    const double* TR;                         // T + R (ghosts), or null when the coating does not reflect
+    const unsigned long long* TR_thr;
 };
+
+// internal scene flag: a coating reflects (ghosts)
+constexpr uint32_t kGhostFlag = 1u << 24;
+constexpr int kMaxGhostBounces = PHOSIM_MAX_GHOST_BOUNCES;
 
 // A screen scale's central-difference gradient (rad / mm), stored per node (i, j) as the 2 x 2 block of
 // nodes the bilinear interpolation needs, (i, j), (i+1, j), (i, j+1), (i+1, j+1) (periodic): one lookup is
@@ -170,6 +178,7 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 //   block 4: high-frequency kick magnitude, direction, back-side reflection
 //   blocks 5, 6 (photons of a bundle, counter of the photon; the ray uses blocks 0-4 of the ray's counter):
 //            spread a, spread b, conversion, diffusion a; diffusion b, back-side reflection
+//   blocks 7, 8, ... (ghosts): the coating decisions after the first reflection, one word each, in order
 __device__ __forceinline__ double u64of(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
 __device__ __forceinline__ float u32of(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
 

@@ -7,9 +7,9 @@
 #include "photon_ds.cuh"
 
 // One captured [chief rays, trace] launch pair, replayed with updated kernel parameters.
-// One captured sequence of kernel launches ([chief rays, trace] or [chief rays, entry, optics]), replayed
+// One captured sequence of kernel launches ([chief rays, trace] or [chief rays, entry, optics(, bundles)]), replayed
 // with each call's kernel parameters and launch shapes.
-constexpr int kMaxGraphNodes = 3;
+constexpr int kMaxGraphNodes = 4;
 struct TraceGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -44,6 +44,8 @@ struct phosim_scene {
     uint32_t* d_stage = nullptr;                // staging image for host image pointers
     phosim::DSState* d_state = nullptr;         // entrance-plane states of the two-kernel double-single path
     size_t cap_state = 0;
+    phosim::DSHit* d_hits = nullptr;            // detector hits of its bundle rays
+    size_t cap_hits = 0;
     size_t cap_stage = 0;
     cudaStream_t last_stream = nullptr;
     // adjoint: Zernike monomial table (owned with the optics) and per-call scratch
@@ -73,7 +75,9 @@ const void* chief_kernel_ptr();
 // the two-kernel double-single path (PHOSIM_MIXED_DS in phosim_trace)
 cudaError_t launch_ds_entry(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_ds_optics(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);
-cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm);
+cudaError_t launch_ds_members(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);
+const void* ds_members_kernel_ptr();
+cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm, int* members_per_sm);
 const void* ds_entry_kernel_ptr();
 const void* ds_optics_kernel_ptr();
 void free_all(std::vector<void*>& v);

@@ -126,15 +126,29 @@ __device__ __forceinline__ MemberDraw member_draw(const TraceParams& P, double b
 // the ray a photon follows: itself, or for a bundle of n photons per ray, photon index / n
 __device__ __forceinline__ uint64_t ray_of(uint32_t bundle, uint64_t i) { return bundle > 1 ? i / bundle : i; }
 
+// Ghosts (Sec. 2.4.2): after a photon's first reflection by a coating, each coating decision draws the next
+// word of blocks 7, 8, ... of the ray's counter.
+__device__ __forceinline__ uint32_t ghost_word(const TraceParams& P, int src, uint64_t ray, int n) {
+    return word(philox(make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), (uint32_t)src, 7u + (uint32_t)n / 4u), P.k0, P.k1),
+                n & 3);
+}
+
+// Surfaces in order (dir = +1); with reflecting coatings a photon reflected by a refracting surface (a ghost)
+// travels back through them (dir = -1) until another reflection turns it round again.  src and ray identify
+// the ghost draws.
 template <bool MIXED, bool FULL, bool RECORD = false>
 __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double D[3], double lam, uint4 w1, uint4 w2,
                                        uint4 w3, uint4 w4, PhotonOut& R, ForwardRecord* fr = nullptr,
-                                       const MemberDraw* mb = nullptr) {
+                                       const MemberDraw* mb = nullptr, int src = 0, uint64_t ray = 0) {
+    constexpr bool GHOSTS = FULL && !RECORD;
+    const bool ghosts = GHOSTS && (P.flags & kGhostFlag);
     double n_cur = 1.0;
     int glass_mat = -1;
     double glass_n = 1.0, glass_inv = 1.0;
+    int si = 0, dir = 1, bounces = 0, n_ghost = 0;
 #pragma unroll 1
-    for (int si = 0; si < P.n_surf; ++si) {
+    for (;;) {
+        if (si < 0 || si >= P.n_surf) break;
         const DSurface& S = P.surf[si];
         if constexpr (RECORD) {
             fr->XD[si][0] = X[0]; fr->XD[si][1] = X[1]; fr->XD[si][2] = X[2];
@@ -145,6 +159,7 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
         double l, Nv[3];
         const uint32_t why = intersect(S, p, dl, l, Nv);
         if (why) { R.flags = lost(why, si); return; }
+        if (GHOSTS && bounces > 0 && !(l > 0.0)) { R.flags = lost(PHOSIM_LOST_MISSED, si); return; }
         p[0] = fma(l, dl[0], p[0]);
         p[1] = fma(l, dl[1], p[1]);
         p[2] = fma(l, dl[2], p[2]);
@@ -244,10 +259,31 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                 }
                 int il = (int)floor((lam - C.lam0) * C.inv_dlam);
                 il = il < 0 ? 0 : (il > C.nl - 1 ? C.nl - 1 : il);
-                const double T = __ldg(C.T + (size_t)il * C.nt + it);
-                const int k = S.coat_slot;
-                const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
-                if (!(u64of(w) < T)) { R.flags = lost(PHOSIM_LOST_COATING, si); return; }
+                const size_t ix = (size_t)il * C.nt + it;
+                const double T = __ldg(C.T + ix);
+                uint32_t w;
+                if (GHOSTS && bounces > 0) {
+                    w = ghost_word(P, src, ray, n_ghost++);
+                } else {
+                    const int k = S.coat_slot;
+                    w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
+                }
+                if (!(u64of(w) < T)) {
+                    // reflected backwards (a ghost) with probability R, absorbed otherwise
+                    if (ghosts && S.kind != PHOSIM_MIRROR && C.TR && u64of(w) < __ldg(C.TR + ix)) {
+                        const double dn = dl[0] * Nx + dl[1] * Ny + dl[2] * Nz;
+                        dl[0] = fma(-2.0 * dn, Nx, dl[0]);
+                        dl[1] = fma(-2.0 * dn, Ny, dl[1]);
+                        dl[2] = fma(-2.0 * dn, Nz, dl[2]);
+                        dir = -dir;
+                        if (++bounces > kMaxGhostBounces) { R.flags = lost(PHOSIM_LOST_MISSED, si); return; }
+                        from_surface(S, p, dl, X, D);
+                        si += dir;
+                        continue;
+                    }
+                    R.flags = lost(PHOSIM_LOST_COATING, si);
+                    return;
+                }
             }
         }
         if (S.kind == PHOSIM_MIRROR) {
@@ -256,26 +292,31 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
             dl[1] = fma(-2.0 * dn, Ny, dl[1]);
             dl[2] = fma(-2.0 * dn, Nz, dl[2]);
         } else {
-            const DMaterial& m = P.mat[S.material];
+            // the medium beyond the surface in the direction of travel (-1: vacuum)
+            const int mi = (GHOSTS && dir < 0) ? S.mat_before : S.material;
             double n_next = 1.0, inv_next = 1.0;
-            if (m.kind == PHOSIM_SELLMEIER) {
-                if (glass_mat != S.material) {
-                    glass_n = sellmeier(m, lam);
-                    glass_inv = 1.0 / glass_n;
-                    glass_mat = S.material;
+            if (mi >= 0) {
+                const DMaterial& m = P.mat[mi];
+                if (m.kind == PHOSIM_SELLMEIER) {
+                    if (glass_mat != mi) {
+                        glass_n = sellmeier(m, lam);
+                        glass_inv = 1.0 / glass_n;
+                        glass_mat = mi;
+                    }
+                    n_next = glass_n;
+                    inv_next = glass_inv;
+                } else if (m.kind == PHOSIM_SILICON) {
+                    n_next = silicon_index(lam);
+                    inv_next = 1.0 / n_next;
                 }
-                n_next = glass_n;
-                inv_next = glass_inv;
-            } else if (m.kind == PHOSIM_SILICON) {
-                n_next = silicon_index(lam);
-                inv_next = 1.0 / n_next;
             }
             if (!refract(dl, Nx, Ny, Nz, n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
             n_cur = n_next;
         }
         from_surface(S, p, dl, X, D);
+        si += dir;
     }
-    R.flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
+    R.flags = lost(PHOSIM_LOST_MISSED, si < 0 ? 0 : P.n_surf);
 }
 
 // Wavelength (Sec. 2.2): cumulative photon-number table, blur within the bin, redshift.
@@ -294,8 +335,11 @@ __device__ __forceinline__ double sample_wavelength(const TraceParams& P, const 
 // largest transmission any incidence angle allows at this wavelength (the photon is certainly rejected
 // there), or -1.
 __device__ __forceinline__ int early_coating_reject(const TraceParams& P, double lam, const uint4& w2, const uint4& w3) {
+    // with reflecting coatings only the first coated surface's draw is certain to be used (a ghost decides
+    // later surfaces with its own words)
+    const int nk = (P.flags & kGhostFlag) ? min(1, P.n_coated) : P.n_coated;
 #pragma unroll 1
-    for (int k = 0; k < P.n_coated; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const int si = P.coated_surface[k];
         const DCoating& C = P.coat[P.surf[si].coating];
         int il = (int)floor((lam - C.lam0) * C.inv_dlam);
@@ -457,7 +501,7 @@ __device__ __forceinline__ void trace_photon(const TraceParams& P, const DSource
     MemberDraw mb;
     const bool bundled = s.bundle > 1;
     if (bundled) mb = member_draw<MIXED>(P, s.bsig, src, photon);
-    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, w4, R, fr, bundled ? &mb : nullptr);
+    optics<MIXED, true, RECORD>(P, X, D, lam, w1, w2, w3, w4, R, fr, bundled ? &mb : nullptr, src, i);
 }
 
 

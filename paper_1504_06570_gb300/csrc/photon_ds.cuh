@@ -22,11 +22,6 @@
 #ifndef PHOSIM_DS_STEP
 #define PHOSIM_DS_STEP __forceinline__
 #endif
-// code for rare surface features (odd asphere terms, Zernike figure, tilts): inline (measured faster than
-// out of line)
-#ifndef PHOSIM_DS_RARE
-#define PHOSIM_DS_RARE __forceinline__
-#endif
 
 namespace phosim {
 
@@ -49,10 +44,29 @@ struct __align__(16) DSState {
     unsigned long long idx;       // photon index within its source's stream
 };
 
-// one chunk of the two-kernel path: tiles [tile_begin, tile_end) of the launch, their states, the count
+// A ray on the detector surface (detector frame): hit point, direction, normal, index of the medium in front.
+struct DetectorHit {
+    ds px, py;
+    ds dl[3], N[3];
+    ds n_cur;
+    int si;
+};
+
+// A bundle's ray on the detector surface, handed from the optics stage to the photons of the bundle
+struct __align__(16) DSHit {
+    DetectorHit H;
+    float lam;
+    int src;
+    unsigned long long ray;
+};
+
+// one chunk of the two-kernel path: tiles [tile_begin, tile_end) of the launch, their states and the
+// bundle rays' detector hits, with their counts
 struct DSStage {
     DSState* state;
     unsigned long long* n_state;
+    DSHit* hits;
+    unsigned long long* n_hits;
     uint64_t tile_begin, tile_end;
 };
 
@@ -145,28 +159,8 @@ __device__ __forceinline__ void zern_eval_f(const float* __restrict__ zp, float 
     z = zz; zu = zzu; zv = zzv;
 }
 
-// The odd asphere terms and the Zernike figure of a sag, out of line: surfaces without them (the common
-// case) keep the surface loop's code compact in the instruction cache.
-static __device__ PHOSIM_DS_RARE void sag_odd_ds(const DSurfaceS& E, ds r2, ds& z, ds& g) {
-    const ds rho = ds_sqrt(r2) * E.inv_rn;
-    const ds u = rho * rho;
-    const ds po = dfma(dfma(dfma(E.ao[3], u, E.ao[2]), u, E.ao[1]), u, E.ao[0]);
-    z = dfma(u * rho, po, z);
-    const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
-    g = dfma(rho * E.inv_rn2, pd, g);
-}
-
-// The Zernike figure (tens of nanometres) is evaluated in single precision: its absolute error is far below
-// the 1e-8 mm the intersection resolves.
-static __device__ PHOSIM_DS_RARE void sag_zern_ds(const DSurfaceS& E, ds x, ds y, ds& z, ds& zx, ds& zy) {
-    float zz, zu, zv;
-    zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
-    z = z + zz;
-    zx = zx + zu * E.zinv;
-    zy = zy + zv * E.zinv;
-}
-
-// Sag and slopes (Sec. 2.4.1).
+// Sag and slopes (Sec. 2.4.1).  The Zernike figure (tens of nanometres) is evaluated in single precision:
+// its absolute error is far below the 1e-8 mm the intersection resolves.
 static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy) {
     const ds r2 = dfma(x, x, y * y);
     ds g = ds_f(0.f);
@@ -185,10 +179,23 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
         const ds pd = dfma(dfma(dfma(E.aed[3], u, E.aed[2]), u, E.aed[1]), u, E.aed[0]);
         g = dfma(u * E.inv_rn2, pd, g);
     }
-    if (flags & SF_ODD) sag_odd_ds(E, r2, z, g);
+    if (flags & SF_ODD) {
+        const ds rho = ds_sqrt(r2) * E.inv_rn;
+        const ds u = rho * rho;
+        const ds po = dfma(dfma(dfma(E.ao[3], u, E.ao[2]), u, E.ao[1]), u, E.ao[0]);
+        z = dfma(u * rho, po, z);
+        const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
+        g = dfma(rho * E.inv_rn2, pd, g);
+    }
     zx = x * g;
     zy = y * g;
-    if (flags & SF_ZERN) sag_zern_ds(E, x, y, z, zx, zy);
+    if (flags & SF_ZERN) {
+        float zz, zu, zv;
+        zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
+        z = z + zz;
+        zx = zx + zu * E.zinv;
+        zy = zy + zv * E.zinv;
+    }
     return true;
 }
 
@@ -256,42 +263,33 @@ static __device__ PHOSIM_DS_STEP bool refract_ds(ds d[3], ds N[3], ds mu) {
     return true;
 }
 
-// rotations into and out of a tilted surface's frame, out of line (aligned surfaces only translate)
-static __device__ PHOSIM_DS_RARE void rotate_in_ds(const DSurfaceS& E, ds rx, ds ry, ds rz, const ds d[3], ds p[3],
-                                                ds dl[3]) {
+__device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, const ds x[3], const ds d[3], ds p[3],
+                                              ds dl[3]) {
+    const ds rx = x[0] - E.o[0], ry = x[1] - E.o[1], rz = x[2] - E.o[2];
+    if (!(flags & SF_ROTATED)) {
+        p[0] = rx; p[1] = ry; p[2] = rz;
+        dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         p[i] = dfma(E.M[3 * i], rx, dfma(E.M[3 * i + 1], ry, E.M[3 * i + 2] * rz));
         dl[i] = dfma(E.M[3 * i], d[0], dfma(E.M[3 * i + 1], d[1], E.M[3 * i + 2] * d[2]));
     }
 }
-static __device__ PHOSIM_DS_RARE void rotate_out_ds(const DSurfaceS& E, const ds p[3], const ds dl[3], ds x[3], ds d[3]) {
+
+__device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, const ds p[3], const ds dl[3], ds x[3],
+                                                ds d[3]) {
+    if (!(flags & SF_ROTATED)) {
+        x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1]; x[2] = p[2] + E.o[2];
+        d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         x[i] = dfma(E.M[i], p[0], dfma(E.M[3 + i], p[1], dfma(E.M[6 + i], p[2], E.o[i])));
         d[i] = dfma(E.M[i], dl[0], dfma(E.M[3 + i], dl[1], E.M[6 + i] * dl[2]));
     }
-}
-
-__device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, const ds x[3], const ds d[3], ds p[3],
-                                              ds dl[3]) {
-    const ds rx = x[0] - E.o[0], ry = x[1] - E.o[1], rz = x[2] - E.o[2];
-    if (flags & SF_ROTATED) {
-        rotate_in_ds(E, rx, ry, rz, d, p, dl);
-        return;
-    }
-    p[0] = rx; p[1] = ry; p[2] = rz;
-    dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
-}
-
-__device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, const ds p[3], const ds dl[3], ds x[3],
-                                                ds d[3]) {
-    if (flags & SF_ROTATED) {
-        rotate_out_ds(E, p, dl, x, d);
-        return;
-    }
-    x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1]; x[2] = p[2] + E.o[2];
-    d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
 }
 
 // the coating accept-reject: the draw (w + 1/2) 2^-32 < T exactly when w < ceil(T 2^32 - 1/2)
@@ -308,8 +306,9 @@ __device__ __forceinline__ float sample_wavelength_f(const TraceParams& P, const
 
 // dynamic transmission (Sec. 3.2) on the single-precision wavelength, as early_coating_reject
 __device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, float lam, const uint4& w2, const uint4& w3) {
+    const int nk = (P.flags & kGhostFlag) ? min(1, P.n_coated) : P.n_coated;   // see early_coating_reject
 #pragma unroll 1
-    for (int k = 0; k < P.n_coated; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const int si = P.coated_surface[k];
         const DCoating& C = P.coat[P.surf[si].coating];
         const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
@@ -350,104 +349,50 @@ __device__ __forceinline__ MemberDrawS member_draw_s(const TraceParams& P, float
     return m;
 }
 
-// A ray on the detector surface (detector frame): hit point, direction, normal, index of the medium in front.
-struct DetectorHit {
-    ds px, py;
-    ds dl[3], N[3];
-    ds n_cur;
-    int si;
+// The random words of the surfaces and the sensor, drawn where they are used (keeping the 16 words of blocks
+// 1-4 live through the whole surface loop would cost registers): the accept draw of coated surface k, and the
+// sensor's conversion, diffusion and back-side reflection words (blocks 1, 2 and 4 of the ray's counter).
+__device__ __forceinline__ uint32_t coat_word(const TraceParams& P, int src, uint64_t ray, int k) {
+    const uint4 w = philox_ds(make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), (uint32_t)src, k < 2 ? 2u : 3u), P.k0, P.k1);
+    return k < 2 ? word(w, 2 + k) : word(w, k - 2);
+}
+
+// the ghost draws (ghost_word in photon.cuh), through the out-of-line generator
+__device__ __forceinline__ uint32_t ghost_word_ds(const TraceParams& P, int src, uint64_t ray, int n) {
+    return word(philox_ds(make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), (uint32_t)src, 7u + (uint32_t)n / 4u), P.k0,
+                          P.k1),
+                n & 3);
+}
+
+struct SensorWords {
+    uint32_t conv, diff_a, diff_b, back;
 };
 
-// Surfaces in order up to the detector surface (Sec. 2.4.2): the steps of optics<MIXED = true, FULL = true>
-// in photon.cuh before the sensor.  False when the ray is lost on the way (R.flags says where and why).
-__device__ __forceinline__ bool optics_to_detector_ds(const TraceParams& P, ds X[3], ds D[3], float lam, uint4 w2,
-                                                      uint4 w3, uint32_t& lost_flags, DetectorHit& H) {
-    ds n_cur = ds_f(1.f);
-    int glass_mat = -1;
-    ds glass_n = ds_f(1.f), glass_inv = ds_f(1.f);
-#pragma unroll 1
-    for (int si = 0; si < P.n_surf; ++si) {
-        const DSurface& S = P.surf[si];
-        const DSurfaceS& E = P.surf_s[si];
-        const int flags = S.flags;
-        ds p[3], dl[3];
-        to_surface_ds(E, flags, X, D, p, dl);
-        ds l, Nv[3];
-        const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
-        if (why) { lost_flags = lost(why, si); return false; }
-        p[0] = dfma(l, dl[0], p[0]);
-        p[1] = dfma(l, dl[1], p[1]);
-        p[2] = dfma(l, dl[2], p[2]);
-        if (S.kind == PHOSIM_DETECTOR) {
-            // the hit on the detector surface, its direction and the medium in front of it
-            H.px = p[0]; H.py = p[1];
-            H.dl[0] = dl[0]; H.dl[1] = dl[1]; H.dl[2] = dl[2];
-            H.N[0] = Nv[0]; H.N[1] = Nv[1]; H.N[2] = Nv[2];
-            H.n_cur = n_cur;
-            H.si = si;
-            return true;
-        }
-        // clear aperture
-        const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
-        if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { lost_flags = lost(PHOSIM_LOST_VIGNETTED, si); return false; }
-        // coating accept-reject at the incidence angle and wavelength
-        if (S.coat_slot >= 0) {
-            const DCoating& C = P.coat[S.coating];
-            int it = 0;
-            if (C.nt > 1) {
-                const float cosi = fabsf(dl[0].hi * Nv[0].hi + dl[1].hi * Nv[1].hi + dl[2].hi * Nv[2].hi);
-                const float th = acosf(fminf(1.f, cosi));
-                it = (int)floorf((th - C.th0f) * C.inv_dthf);
-                it = it < 0 ? 0 : (it > C.nt - 1 ? C.nt - 1 : it);
-            }
-            const int k = S.coat_slot;
-            const uint32_t w = k < 2 ? word(w2, 2 + k) : word(w3, k - 2);
-            if (!((unsigned long long)w < __ldg(C.T_thr + (size_t)coat_lambda_bin(C, lam) * C.nt + it))) {
-                lost_flags = lost(PHOSIM_LOST_COATING, si);
-                return false;
-            }
-        }
-        if (S.kind == PHOSIM_MIRROR) {
-            const ds dn2 = dot3(dl, Nv) * -2.f;
-            dl[0] = dfma(dn2, Nv[0], dl[0]);
-            dl[1] = dfma(dn2, Nv[1], dl[1]);
-            dl[2] = dfma(dn2, Nv[2], dl[2]);
-        } else {
-            const DMaterial& m = P.mat[S.material];
-            ds n_next = ds_f(1.f), inv_next = ds_f(1.f);
-            if (m.kind == PHOSIM_SELLMEIER) {
-                if (glass_mat != S.material) {
-                    glass_n = sellmeier_ds(m, lam);
-                    glass_inv = ds_rcp(glass_n);
-                    glass_mat = S.material;
-                }
-                n_next = glass_n;
-                inv_next = glass_inv;
-            } else if (m.kind == PHOSIM_SILICON) {
-                n_next = ds_f(silicon_index_f(lam));
-                inv_next = ds_rcp(n_next);
-            }
-            if (!refract_ds(dl, Nv, n_cur * inv_next)) { lost_flags = lost(PHOSIM_LOST_TIR, si); return false; }
-            n_cur = n_next;
-        }
-        from_surface_ds(E, flags, p, dl, X, D);
-    }
-    lost_flags = lost(PHOSIM_LOST_MISSED, P.n_surf);
-    return false;
+__device__ __forceinline__ SensorWords sensor_words(const TraceParams& P, int src, uint64_t ray) {
+    const uint32_t clo = (uint32_t)ray, chi = (uint32_t)(ray >> 32);
+    const uint4 w1 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
+    const uint4 w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
+    SensorWords sw;
+    sw.conv = w1.w; sw.diff_a = w2.x; sw.diff_b = w2.y; sw.back = 0u;
+    if (P.flags & PHOSIM_BACK_REFLECT) sw.back = philox_ds(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1).z;
+    return sw;
 }
 
 // The sensor and the pixel for a ray's hit on the detector surface (Sec. 2.4.2, 2.5): the detector steps of
 // optics<MIXED = true, FULL = true>, with a bundle photon's offset and draws when mb is given.
-__device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHit& H, float lam, uint4 w1, uint4 w2,
-                                          uint4 w4, PhotonOutS& R, const MemberDrawS* mb = nullptr) {
+__device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHit& H, float lam, int src, uint64_t ray,
+                                          PhotonOutS& R, const MemberDrawS* mb = nullptr) {
     const int si = H.si;
     ds p0 = H.px, p1 = H.py;
     ds dl[3] = {H.dl[0], H.dl[1], H.dl[2]}, Nv[3] = {H.N[0], H.N[1], H.N[2]};
-    uint32_t w_conv = w1.w, w_diff_a = w2.x, w_diff_b = w2.y, w_back = w4.z;
+    uint32_t w_conv, w_diff_a, w_diff_b, w_back;
     if (mb) {   // a bundle's photon: its offset from the ray's hit and its own sensor draws
         p0 = p0 + mb->sx;
         p1 = p1 + mb->sy;
         w_conv = mb->conv; w_diff_a = mb->diff_a; w_diff_b = mb->diff_b; w_back = mb->back;
+    } else {
+        const SensorWords sw = sensor_words(P, src, ray);
+        w_conv = sw.conv; w_diff_a = sw.diff_a; w_diff_b = sw.diff_b; w_back = sw.back;
     }
     const ds hx = p0 - P.xlo_s, hy = p1 - P.ylo_s;
     if (!(hx.hi >= 0.f && hy.hi >= 0.f && ds_lt(hx, P.chip_w_s) && ds_lt(hy, P.chip_h_s))) {
@@ -495,13 +440,113 @@ __device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHi
     R.flags = PHOSIM_F_DETECTED;
 }
 
-// Surfaces and sensor (Sec. 2.4.2, 2.5): the steps of optics<MIXED = true, FULL = true> in photon.cuh.
-__device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3], float lam, uint4 w1, uint4 w2,
-                                          uint4 w3, uint4 w4, PhotonOutS& R, const MemberDrawS* mb = nullptr) {
-    DetectorHit H;
-    uint32_t lost_flags = 0;
-    if (optics_to_detector_ds(P, X, D, lam, w2, w3, lost_flags, H)) detect_ds(P, H, lam, w1, w2, w4, R, mb);
-    else R.flags = lost_flags;
+// Surfaces in order (Sec. 2.4.2) and at the detector surface the sensor (detect_ds): the steps of
+// optics<MIXED = true, FULL = true> in photon.cuh.  For a bundle's ray (hand_off given) the hit on the detector
+// surface is handed over for its photons instead, and R.flags = kHandedOff.
+constexpr uint32_t kHandedOff = 0x80000000u;
+
+__device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3], float lam, int src, uint64_t ray,
+                                          PhotonOutS& R, const MemberDrawS* mb = nullptr,
+                                          DetectorHit* hand_off = nullptr) {
+    const bool ghosts = (P.flags & kGhostFlag) != 0;
+    ds n_cur = ds_f(1.f);
+    int glass_mat = -1;
+    ds glass_n = ds_f(1.f), glass_inv = ds_f(1.f);
+    int si = 0, dir = 1, bounces = 0, n_ghost = 0;
+#pragma unroll 1
+    for (;;) {
+        if (si < 0 || si >= P.n_surf) break;
+        const DSurface& S = P.surf[si];
+        const DSurfaceS& E = P.surf_s[si];
+        const int flags = S.flags;
+        ds p[3], dl[3];
+        to_surface_ds(E, flags, X, D, p, dl);
+        ds l, Nv[3];
+        const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
+        if (why) { R.flags = lost(why, si); return; }
+        if (bounces > 0 && !(l.hi > 0.f)) { R.flags = lost(PHOSIM_LOST_MISSED, si); return; }
+        p[0] = dfma(l, dl[0], p[0]);
+        p[1] = dfma(l, dl[1], p[1]);
+        p[2] = dfma(l, dl[2], p[2]);
+        if (S.kind == PHOSIM_DETECTOR) {
+            // the hit on the detector surface, its direction and the medium in front of it
+            DetectorHit H;
+            H.px = p[0]; H.py = p[1];
+            H.dl[0] = dl[0]; H.dl[1] = dl[1]; H.dl[2] = dl[2];
+            H.N[0] = Nv[0]; H.N[1] = Nv[1]; H.N[2] = Nv[2];
+            H.n_cur = n_cur;
+            H.si = si;
+            if (hand_off) {
+                *hand_off = H;
+                R.flags = kHandedOff;
+                return;
+            }
+            detect_ds(P, H, lam, src, ray, R, mb);
+            return;
+        }
+        // clear aperture
+        const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
+        if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return; }
+        // coating accept-reject at the incidence angle and wavelength
+        if (S.coat_slot >= 0) {
+            const DCoating& C = P.coat[S.coating];
+            int it = 0;
+            if (C.nt > 1) {
+                const float cosi = fabsf(dl[0].hi * Nv[0].hi + dl[1].hi * Nv[1].hi + dl[2].hi * Nv[2].hi);
+                const float th = acosf(fminf(1.f, cosi));
+                it = (int)floorf((th - C.th0f) * C.inv_dthf);
+                it = it < 0 ? 0 : (it > C.nt - 1 ? C.nt - 1 : it);
+            }
+            const size_t ix = (size_t)coat_lambda_bin(C, lam) * C.nt + it;
+            const uint32_t w = bounces > 0 ? ghost_word_ds(P, src, ray, n_ghost++) : coat_word(P, src, ray, S.coat_slot);
+            if (!((unsigned long long)w < __ldg(C.T_thr + ix))) {
+                // reflected backwards (a ghost) with probability R, absorbed otherwise
+                if (ghosts && S.kind != PHOSIM_MIRROR && C.TR_thr && (unsigned long long)w < __ldg(C.TR_thr + ix)) {
+                    const ds dn2 = dot3(dl, Nv) * -2.f;
+                    dl[0] = dfma(dn2, Nv[0], dl[0]);
+                    dl[1] = dfma(dn2, Nv[1], dl[1]);
+                    dl[2] = dfma(dn2, Nv[2], dl[2]);
+                    dir = -dir;
+                    if (++bounces > kMaxGhostBounces) { R.flags = lost(PHOSIM_LOST_MISSED, si); return; }
+                    from_surface_ds(E, flags, p, dl, X, D);
+                    si += dir;
+                    continue;
+                }
+                R.flags = lost(PHOSIM_LOST_COATING, si);
+                return;
+            }
+        }
+        if (S.kind == PHOSIM_MIRROR) {
+            const ds dn2 = dot3(dl, Nv) * -2.f;
+            dl[0] = dfma(dn2, Nv[0], dl[0]);
+            dl[1] = dfma(dn2, Nv[1], dl[1]);
+            dl[2] = dfma(dn2, Nv[2], dl[2]);
+        } else {
+            // the medium beyond the surface in the direction of travel (-1: vacuum)
+            const int mi = dir < 0 ? S.mat_before : S.material;
+            ds n_next = ds_f(1.f), inv_next = ds_f(1.f);
+            if (mi >= 0) {
+                const DMaterial& m = P.mat[mi];
+                if (m.kind == PHOSIM_SELLMEIER) {
+                    if (glass_mat != mi) {
+                        glass_n = sellmeier_ds(m, lam);
+                        glass_inv = ds_rcp(glass_n);
+                        glass_mat = mi;
+                    }
+                    n_next = glass_n;
+                    inv_next = glass_inv;
+                } else if (m.kind == PHOSIM_SILICON) {
+                    n_next = ds_f(silicon_index_f(lam));
+                    inv_next = ds_rcp(n_next);
+                }
+            }
+            if (!refract_ds(dl, Nv, n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
+            n_cur = n_next;
+        }
+        from_surface_ds(E, flags, p, dl, X, D);
+        si += dir;
+    }
+    R.flags = lost(PHOSIM_LOST_MISSED, si < 0 ? 0 : P.n_surf);
 }
 
 // Bilinear screen gradient (Sec. 2.3.2) at a double-single screen position; single-precision weights
@@ -524,19 +569,6 @@ __device__ __forceinline__ void screen_gradient_ds(const DScale& S, ds sx, ds sy
     const float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
     gx += w00 * A.x + w10 * A.z + w01 * B.x + w11 * B.z;
     gy += w00 * A.y + w10 * A.w + w01 * B.y + w11 * B.w;
-}
-
-// The random words the surfaces and the sensor read: blocks 1 (conversion), 2 (diffusion, coatings 0-1),
-// 3 (coatings 2-5) and 4 (back-side reflection), the last two only when the scene uses them; i is the ray.
-__device__ __forceinline__ void optics_words(const TraceParams& P, int src, uint64_t i, uint4& w1, uint4& w2, uint4& w3,
-                                             uint4& w4) {
-    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
-    w1 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 1u), P.k0, P.k1);
-    w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
-    w3 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
-    w4 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.hf_K > 0 || (P.flags & PHOSIM_BACK_REFLECT)) w4 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 4u), P.k0, P.k1);
 }
 
 // Ray i from the top of the atmosphere to the entrance plane of the telescope (Sec. 2.2, 2.3): the sampling
@@ -646,11 +678,12 @@ __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const Sour
     ds X[3], D[3];
     float lam;
     uint4 w1, w2, w3, w4;
-    if (!photon_entry_ds(P, s, src, ray_of(s.bundle, i), R, X, D, lam, w1, w2, w3, w4)) return;
+    const uint64_t ray = ray_of(s.bundle, i);
+    if (!photon_entry_ds(P, s, src, ray, R, X, D, lam, w1, w2, w3, w4)) return;
     MemberDrawS mb;
     const bool bundled = s.bundle > 1;
     if (bundled) mb = member_draw_s(P, s.bsig, src, i);
-    optics_ds(P, X, D, lam, w1, w2, w3, w4, R, bundled ? &mb : nullptr);
+    optics_ds(P, X, D, lam, src, ray, R, bundled ? &mb : nullptr);
 }
 
 }  // namespace phosim

@@ -253,6 +253,10 @@ __device__ __forceinline__ void unit_members(const DSource& s, uint32_t nb, uint
     nm = b > a ? (uint32_t)(b - a) : 0u;
 }
 
+#ifndef PHOSIM_DS_MEMBERS_MIN_BLOCKS
+#define PHOSIM_DS_MEMBERS_MIN_BLOCKS 4
+#endif
+
 __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kernel(const __grid_constant__ TraceParams P,
                                                                                    const DSStage S) {
     __shared__ uint32_t queue_mem[kWarpsPerBlock][64];
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
         if (lane == 0) src_mem[warp] = source_s(s);
         __syncwarp();
         const SourceS& ss = src_mem[warp];
-        const uint32_t nb = ss.bundle;
+        const uint32_t nb = ss.bundle;          // the same for the whole warp (one source per tile)
         TileAcc<true> A = {};
         int queued = 0;
         uint32_t base = 0;
@@ -288,11 +292,16 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                 const uint32_t k = base + lane;
                 const bool valid = k < count;
                 const uint64_t u = ufirst + k;
-                uint64_t lo;
-                uint32_t nm;
-                unit_members(s, nb, u, lo, nm);
-                const unsigned traced = __reduce_add_sync(0xffffffffu, valid ? nm : 0u);
-                if (lane == 0) cnt[0] += traced;
+                if (nb <= 1) {
+                    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                    if (lane == 0) cnt[0] += __popc(vmask);
+                } else {
+                    uint64_t lo;
+                    uint32_t nm;
+                    unit_members(s, nb, u, lo, nm);
+                    const unsigned traced = __reduce_add_sync(0xffffffffu, valid ? nm : 0u);
+                    if (lane == 0) cnt[0] += traced;
+                }
                 bool go_on = valid;
                 if (early) {
                     // stage 1: the early coating decision alone, for every photon of the unit
@@ -301,12 +310,17 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                     if (valid) rej = early_reject_surface_f(P, ss, src, u, lam);
                     go_on = valid && rej < 0;
                     const bool dropped = valid && !go_on;
-                    if (__any_sync(0xffffffffu, dropped)) {
-                        PhotonOutS R;
-                        R.x = R.y = R.xc = R.yc = ds_f(0.f);
-                        R.lam = lam;
-                        R.pix = -1;
-                        R.flags = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
+                    PhotonOutS R;
+                    R.x = R.y = R.xc = R.yc = ds_f(0.f);
+                    R.lam = lam;
+                    R.pix = -1;
+                    R.flags = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
+                    if (nb <= 1) {
+                        consume<true>(P, R, dropped, s.rec_off + (u - s.first), ss.ref_x, ss.ref_y, lane, A, cnt);
+                    } else if (__any_sync(0xffffffffu, dropped)) {
+                        uint64_t lo;
+                        uint32_t nm;
+                        unit_members(s, nb, u, lo, nm);
                         for (uint32_t m = 0; m < nb; ++m)
                             consume<true>(P, R, dropped && m < nm, s.rec_off + (lo + m - s.first), ss.ref_x, ss.ref_y,
                                           lane, A, cnt);
@@ -365,10 +379,60 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
     if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
 }
 
+// Account for one photon per lane of the optics or bundle stage: record, image, counters (cnt: the warp's
+// counters in shared memory, lane 0) and the moment sums about the source's chief-ray position, reduced over
+// the lanes of one source.  Every lane of the warp calls it.
+__device__ __forceinline__ void account_ds(const TraceParams& P, const PhotonOutS& R, bool v, int src, uint64_t i,
+                                           int lane, unsigned long long* cnt) {
+    const DSource& s = P.sources[src];
+    if (v && P.records) {
+        phosim_photon_record rec;
+        rec.x = ds_value(R.x); rec.y = ds_value(R.y); rec.xc = ds_value(R.xc); rec.yc = ds_value(R.yc);
+        rec.lambda = (double)R.lam;
+        rec.flags = R.flags; rec.pix = R.pix;
+        P.records[s.rec_off + (i - s.first)] = rec;
+    }
+    const bool det = v && (R.flags & PHOSIM_F_DETECTED);
+    const unsigned dmask = __ballot_sync(0xffffffffu, det);
+    if (det) {
+        const unsigned same = __match_any_sync(dmask, R.pix);
+        if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
+    }
+    if (lane == 0) cnt[1] += __popc(dmask);
+    const uint32_t reason = v ? ((R.flags >> 8) & 0xffu) : 0u;
+#pragma unroll
+    for (int q = 1; q <= 8; ++q) {
+        const unsigned bq = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
+        if (lane == 0) cnt[1 + q] += __popc(bq);
+    }
+    if (P.moments && dmask) {
+        double mm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (det) {
+            const double fx = (double)(R.x - ds_of(s.ref_x)).hi, fy = (double)(R.y - ds_of(s.ref_y)).hi;
+            mm[0] = 1.0; mm[1] = fx; mm[2] = fy; mm[3] = fx * fx; mm[4] = fx * fy; mm[5] = fy * fy;
+        }
+        const int src0 = __shfl_sync(0xffffffffu, src, __ffs(dmask) - 1);
+        if (__all_sync(0xffffffffu, !det || src == src0)) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) mm[q] = warp_sum(mm[q]);
+            if (lane == 0) {
+                double* M = P.moments + (size_t)src0 * PHOSIM_MOMENT_WORDS;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
+            }
+        } else if (det) {
+            double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256, PHOSIM_DS_OPTICS_MIN_BLOCKS) ds_optics_kernel(const __grid_constant__ TraceParams P,
                                                                                      const DSStage S) {
     __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lanes_below = (1u << lane) - 1u;
     unsigned long long* cnt = cnt_mem[warp];
     if (lane < kNumCounters) cnt[lane] = 0;
     __syncwarp();
@@ -377,84 +441,82 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_OPTICS_MIN_BLOCKS) ds_optics_ke
     for (unsigned long long b = ((unsigned long long)blockIdx.x * kWarpsPerBlock + warp) * 32ull; b < n; b += stride) {
         const unsigned long long e = b + lane;
         const bool v = e < n;
-        // the unit (photon or bundle ray) to the detector surface
-        DetectorHit H;
-        bool hit = false;
-        uint32_t lost_flags = 0;
-        float lam = 0.f;
+        PhotonOutS R;
+        R.flags = 0; R.pix = -1; R.lam = 0.f;
+        R.x = R.y = R.xc = R.yc = ds_f(0.f);
         int src = 0;
         uint64_t u = 0;
-        uint32_t nb = 1;
-        uint4 w1 = make_uint4(0u, 0u, 0u, 0u), w2 = w1, w3 = w1, w4 = w1;
+        DetectorHit H;
         if (v) {
             const DSState st = S.state[e];
             src = st.src;
             u = st.idx;
-            lam = st.lam;
-            nb = P.sources[src].bundle;
+            R.lam = st.lam;
+            const bool bundled = P.sources[src].bundle > 1;
             ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
-            optics_words(P, src, u, w1, w2, w3, w4);
-            hit = optics_to_detector_ds(P, X, D, st.lam, w2, w3, lost_flags, H);
+            optics_ds(P, X, D, st.lam, src, u, R, nullptr, bundled ? &H : nullptr);
         }
-        const DSource& s = P.sources[src];
-        uint64_t lo;
-        uint32_t nm;
-        unit_members(s, nb, u, lo, nm);
-        const uint32_t n_loop = __reduce_max_sync(0xffffffffu, v ? nb : 0u);
-        // then each of its photons through the sensor and into the image
+        // a bundle's ray that reached the detector surface hands its hit over to the bundle stage
+        const bool handed = v && R.flags == kHandedOff;
+        const unsigned hmask = __ballot_sync(0xffffffffu, handed);
+        if (hmask) {
+            unsigned long long slot = 0;
+            if (lane == 0) slot = atomicAdd(S.n_hits, (unsigned long long)__popc(hmask));
+            slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(hmask & lanes_below);
+            if (handed) {
+                DSHit h;
+                h.H = H;
+                h.lam = R.lam;
+                h.src = src;
+                h.ray = u;
+                S.hits[slot] = h;
+            }
+        }
+        // every other unit is one photon, or a bundle's ray lost before the detector (all its photons)
+        const uint32_t nb = v ? P.sources[src].bundle : 1u;
+        uint64_t lo = u;
+        uint32_t nm = 1;
+        if (nb > 1) unit_members(P.sources[src], nb, u, lo, nm);
+        const uint32_t n_loop = __reduce_max_sync(0xffffffffu, v && !handed ? nm : 0u);
+        for (uint32_t m = 0; m < n_loop; ++m) account_ds(P, R, v && !handed && m < nm, src, lo + m, lane, cnt);
+    }
+    __syncwarp();
+    if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
+}
+
+// The photons of the bundles whose ray reached the detector surface: each its own Gaussian offset and its
+// own sensor draws from the shared hit (Sec. 3.2), one hit per thread.
+__global__ void __launch_bounds__(256, PHOSIM_DS_MEMBERS_MIN_BLOCKS) ds_members_kernel(const __grid_constant__ TraceParams P,
+                                                                                       const DSStage S) {
+    __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long* cnt = cnt_mem[warp];
+    if (lane < kNumCounters) cnt[lane] = 0;
+    __syncwarp();
+    const unsigned long long n = *S.n_hits;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kWarpsPerBlock * 32ull;
+    for (unsigned long long b = ((unsigned long long)blockIdx.x * kWarpsPerBlock + warp) * 32ull; b < n; b += stride) {
+        const unsigned long long e = b + lane;
+        const bool v = e < n;
+        DSHit h;
+        h.src = 0; h.ray = 0; h.lam = 0.f;
+        if (v) h = S.hits[e];
+        const DSource& s = P.sources[h.src];
+        const uint32_t nb = v ? s.bundle : 0u;
+        uint64_t lo = 0;
+        uint32_t nm = 0;
+        if (v) unit_members(s, nb, h.ray, lo, nm);
+        const uint32_t n_loop = __reduce_max_sync(0xffffffffu, nm);
         for (uint32_t m = 0; m < n_loop; ++m) {
-            const bool vm = v && m < nm;
-            const uint64_t i = lo + m;
+            const bool vm = m < nm;
             PhotonOutS R;
-            R.flags = hit ? 0u : lost_flags; R.pix = -1; R.lam = lam;
+            R.flags = 0; R.pix = -1; R.lam = h.lam;
             R.x = R.y = R.xc = R.yc = ds_f(0.f);
-            if (vm && hit) {
-                MemberDrawS mb;
-                if (nb > 1) mb = member_draw_s(P, (float)s.bsig, src, i);
-                detect_ds(P, H, lam, w1, w2, w4, R, nb > 1 ? &mb : nullptr);
+            if (vm) {
+                const MemberDrawS mb = member_draw_s(P, (float)s.bsig, h.src, lo + m);
+                detect_ds(P, h.H, h.lam, h.src, h.ray, R, &mb);
             }
-            if (vm && P.records) {
-                phosim_photon_record rec;
-                rec.x = ds_value(R.x); rec.y = ds_value(R.y); rec.xc = ds_value(R.xc); rec.yc = ds_value(R.yc);
-                rec.lambda = (double)R.lam;
-                rec.flags = R.flags; rec.pix = R.pix;
-                P.records[s.rec_off + (i - s.first)] = rec;
-            }
-            const bool det = vm && (R.flags & PHOSIM_F_DETECTED);
-            const unsigned dmask = __ballot_sync(0xffffffffu, det);
-            if (det) {
-                const unsigned same = __match_any_sync(dmask, R.pix);
-                if (lane == __ffs(same) - 1) atomicAdd(P.image + R.pix, (unsigned)__popc(same));
-            }
-            if (lane == 0) cnt[1] += __popc(dmask);
-            const uint32_t reason = vm ? ((R.flags >> 8) & 0xffu) : 0u;
-#pragma unroll
-            for (int q = 1; q <= 8; ++q) {
-                const unsigned bq = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
-                if (lane == 0) cnt[1 + q] += __popc(bq);
-            }
-            // moment sums about the chief-ray position, reduced over the lanes of one source
-            if (P.moments && dmask) {
-                double mm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-                if (det) {
-                    const double fx = (double)(R.x - ds_of(s.ref_x)).hi, fy = (double)(R.y - ds_of(s.ref_y)).hi;
-                    mm[0] = 1.0; mm[1] = fx; mm[2] = fy; mm[3] = fx * fx; mm[4] = fx * fy; mm[5] = fy * fy;
-                }
-                const int src0 = __shfl_sync(0xffffffffu, src, __ffs(dmask) - 1);
-                if (__all_sync(0xffffffffu, !det || src == src0)) {
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) mm[q] = warp_sum(mm[q]);
-                    if (lane == 0) {
-                        double* M = P.moments + (size_t)src0 * PHOSIM_MOMENT_WORDS;
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
-                    }
-                } else if (det) {
-                    double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
-                }
-            }
+            account_ds(P, R, vm, h.src, lo + m, lane, cnt);
         }
     }
     __syncwarp();
@@ -514,10 +576,18 @@ cudaError_t launch_ds_optics(const TraceParams& P, const DSStage& S, int blocks,
     return cudaGetLastError();
 }
 
-cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm) {
+cudaError_t launch_ds_members(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st) {
+    ds_members_kernel<<<blocks, threads, 0, st>>>(P, S);
+    return cudaGetLastError();
+}
+
+const void* ds_members_kernel_ptr() { return (const void*)ds_members_kernel; }
+
+cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm, int* members_per_sm) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(entry_per_sm, ds_entry_kernel, threads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(optics_per_sm, ds_optics_kernel, threads, 0);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(optics_per_sm, ds_optics_kernel, threads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(members_per_sm, ds_members_kernel, threads, 0);
 }
 
 cudaError_t trace_occupancy(int mode, int threads, int* blocks_per_sm) {

@@ -47,13 +47,14 @@ class Material:
 
 @dataclass
 class Coating:
-    """Transmission probability T(lambda, theta), piecewise constant on a uniform grid
-    (the paper's angle/wavelength coating interface, Sec. 2.4.2)."""
+    """Transmission probability T(lambda, theta), and optionally reflection probability R, piecewise constant on
+    a uniform grid (the paper's angle/wavelength coating interface, Sec. 2.4.2)."""
     lam0: float
     dlam: float
     theta0: float
     dtheta: float
     table: np.ndarray            # shape (n_lambda, n_theta), float64 in [0, 1]
+    reflect: np.ndarray = None   # reflection probability R on the same grid (ghosts, Sec. 2.4.2); T + R <= 1
 
 
 @dataclass

@@ -55,7 +55,8 @@ class Material(C.Structure):
 
 class Coating(C.Structure):
     _fields_ = [("lam0", C.c_double), ("dlam", C.c_double), ("theta0", C.c_double), ("dtheta", C.c_double),
-                ("n_lambda", C.c_int32), ("n_theta", C.c_int32), ("table", C.POINTER(C.c_double))]
+                ("n_lambda", C.c_int32), ("n_theta", C.c_int32), ("table", C.POINTER(C.c_double)),
+                ("reflect", C.POINTER(C.c_double))]
 
 
 class ScreenScale(C.Structure):
@@ -212,6 +213,10 @@ class Scene:
             cs[i].lam0, cs[i].dlam, cs[i].theta0, cs[i].dtheta = c.lam0, c.dlam, c.theta0, c.dtheta
             cs[i].n_lambda, cs[i].n_theta = T.shape
             cs[i].table = T.ctypes.data_as(C.POINTER(C.c_double))
+            if getattr(c, "reflect", None) is not None:
+                Rf = np.ascontiguousarray(np.broadcast_to(c.reflect, T.shape), np.float64)
+                keep.append(Rf)
+                cs[i].reflect = Rf.ctypes.data_as(C.POINTER(C.c_double))
         _check("phosim_load_optics", self.L.phosim_load_optics(self.h, ss, n, ms, len(materials), cs, len(coatings)))
 
     def load_screens(self, layers):

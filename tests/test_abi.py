@@ -46,7 +46,7 @@ def test_struct_layout_matches_header():
     checks = {"phosim_scene_desc": (P.SceneDesc, ["seed", "precision", "ell", "n_sigma", "sigma", "dead_layer"]),
               "phosim_surface": (P.Surface, ["R", "alpha", "pert", "zern_rnorm", "zern"]),
               "phosim_material": (P.Material, ["B", "C"]),
-              "phosim_coating": (P.Coating, ["n_lambda", "table"]),
+              "phosim_coating": (P.Coating, ["n_lambda", "table", "reflect"]),
               "phosim_screen_scale": (P.ScreenScale, ["n", "phase"]),
               "phosim_layer": (P.Layer, ["n_scales", "scales"]),
               "phosim_source": (P.Source, ["bundle", "xi", "pa", "bundle_sigma"])}

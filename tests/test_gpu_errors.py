@@ -99,3 +99,15 @@ def test_newton_iteration_cap_is_a_flag_not_a_fault():
     assert gpu["counters"][1 + 3] == (reasons == 3).sum()
     again = G.run_gpu(I.paraboloid_scene(n_photons=1000, screen_n=64), P.PLAIN_FP64, records=False)
     assert again["counters"][0] == 1000
+
+
+def test_grad_refuses_ghosts():
+    """The adjoint follows forward paths only: a scene whose coatings reflect is UNSUPPORTED for phosim_grad."""
+    from tests import gpu_helpers as GH
+    sc = GH.test_system_scene(n_photons=100, atmosphere=False)
+    sc.coatings[0].reflect = 0.5 * (1.0 - sc.coatings[0].table)
+    s = P.Scene(sc)
+    with pytest.raises(P.PhosimError) as e:
+        s.grad(np.zeros((1, 5)), [(0, 0)])
+    assert e.value.code == -4
+    s.close()

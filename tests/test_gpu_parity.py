@@ -267,3 +267,43 @@ def test_background_bundles(oracle_mod, precision):
     sc.sources.bundle_sigma = None
     none = G.run_gpu(sc, precision, early_reject=True, first=first)
     assert np.array_equal(one["rec"], none["rec"])
+
+
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED, P.MIXED_DS])
+def test_ghosts_of_a_coated_plate_match_oracle(oracle_mod, precision):
+    """Ghosts (Sec. 2.4.2) through the C ABI: the tilted beam behind a coated plate (T = 0.5, R = 0.45 on both
+    faces), photon by photon against the oracle; no single-precision step is on this path except the
+    wavelength blur, so every precision meets the FP64 gate."""
+    from tests.test_oracle_pins import _ghost_plate_scene
+    sc = _ghost_plate_scene(0.5, 0.45, n_photons=20000)
+    gpu = G.run_gpu(sc, precision)
+    ora = G.oracle_trace(oracle_mod, sc)
+    r = G.compare_records(sc, gpu, ora)
+    assert r["max_err_px"] < (1e-6 if precision == P.PLAIN_FP64 else 1e-4), r
+    assert r["n_detected"] > 6000
+
+
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED, P.MIXED_DS])
+def test_ghosts_in_the_catadioptric_system(oracle_mod, precision):
+    """The full test system with both filter faces coated and reflecting (R = 0.1 in band, 0.9 out of band):
+    ghosts between the filter faces reach the detector, others leave backwards past the lens and the mirror,
+    through the atmosphere and the sensor; the dynamic transmission test on (only the first coated surface's
+    draw is certain once coatings reflect)."""
+    counts = [5000, 3000, 1000]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=15))
+    sc.surfaces[4].coating = 0
+    c = sc.coatings[0]
+    c.reflect = np.where(c.table > 0, 0.3, 0.9) * np.ones_like(c.table)
+    c.reflect = np.minimum(c.reflect, 1.0 - c.table)
+    gpu = G.run_gpu(sc, precision, early_reject=True)
+    ora = G.oracle_trace(oracle_mod, sc)
+    det_g, det_o = (gpu["rec"]["flags"] & 1) == 1, (ora["flags"] & 1) == 1
+    if precision == P.PLAIN_FP64:
+        assert np.all((det_g == det_o) | G.boundary_mask(ora))
+        both = det_g & det_o
+        err = np.maximum(np.abs(gpu["rec"]["x"][both] - ora["x"][both]), np.abs(gpu["rec"]["y"][both] - ora["y"][both]))
+        assert err.max() / sc.detector.pixel < 1e-6
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
+    else:
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+    assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))

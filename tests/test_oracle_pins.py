@@ -648,3 +648,53 @@ def test_background_bundles_keep_the_mean_image(oracle_mod):
     m = (A + B) > 50
     chi2 = ((A - B)[m] ** 2 / (A + B)[m]).sum() / m.sum()
     assert chi2 < 8.0, chi2
+
+
+def _ghost_plate_scene(T, R, n_photons=40000, xi=0.3, t=5.0):
+    """A coated plane-parallel silica plate (both faces: transmission T, reflection R, the rest absorbed) in a
+    tilted collimated beam, 1 mm pupil, detector 20 mm below, sensor off."""
+    mats = [I.Material(I.VACUUM), I.Material(I.SELLMEIER, I.FUSED_SILICA_B, I.FUSED_SILICA_C), I.Material(I.SILICON)]
+    coat = I.Coating(lam0=400.0, dlam=300.0, theta0=0.0, dtheta=math.pi / 2, table=np.array([[T]]),
+                     reflect=None if R is None else np.array([[R]]))
+    surfaces = [I.Surface(kind=I.REFRACT, R=0.0, z=0.0, r_out=50.0, material=1, coating=0),
+                I.Surface(kind=I.REFRACT, R=0.0, z=-t, r_out=50.0, material=0, coating=0),
+                I.Surface(kind=I.DETECTOR, R=0.0, z=-20.0, material=2)]
+    src = I.point_sources([xi], [0.0], [n_photons])
+    sc = bare_scene(surfaces, materials=mats, coatings=[coat], nx=4096, pixel=0.01, pupil=(0.0, 1.0), sources=src)
+    sc.z_entrance = 10.0
+    return sc
+
+
+def test_ghosts_of_a_coated_plate(oracle_mod):
+    """Sec. 2.4.2 ghosts: a photon reflected by a refracting surface's coating travels back through the surfaces.
+    Behind a coated plate the n-th ghost (n round trips inside the plate) lands 2 n t tan(theta') beyond the
+    direct image, theta' the refraction angle in the glass, with probability T^2 R^(2n); without reflection
+    tables, or with R = 0, nothing changes."""
+    t, xi = 5.0, 0.3
+    Tc, Rc = 0.5, 0.45
+    sc = _ghost_plate_scene(Tc, Rc, t=t, xi=xi)
+    o = oracle_mod.Oracle(sc)
+    rec = o.trace(n_threads=8)
+    pos, d, lam, _ = o.pre_optics(0, 0, 40000)
+    det = (rec["flags"] & 1) == 1
+    # the direct image of every photon: entrance plane -> plate -> detector, with Snell's law at the faces
+    sin_v = np.hypot(d[:, 0], d[:, 1])
+    n_g = np.array([o.index(1, l) for l in lam])
+    sin_g = sin_v / n_g
+    tan_v, tan_g = sin_v / np.sqrt(1 - sin_v ** 2), sin_g / np.sqrt(1 - sin_g ** 2)
+    x_plate = pos[:, 0] + d[:, 0] / -d[:, 2] * (pos[:, 2] - 0.0)
+    x_direct = x_plate + t * tan_g + (20.0 - t) * tan_v
+    step = 2 * t * tan_g
+    k = (rec["x"] - x_direct) / step
+    kr = np.rint(k)
+    assert np.abs(k - kr)[det].max() < 1e-9
+    N = 40000
+    for n in range(3):
+        expect = N * Tc ** 2 * Rc ** (2 * n)
+        got = np.sum(det & (kr == n))
+        assert abs(got - expect) < 5 * math.sqrt(expect) + 2, (n, got, expect)
+    # no reflection table, or R = 0: the plain coating decision
+    plain = oracle_mod.Oracle(_ghost_plate_scene(Tc, None, t=t, xi=xi)).trace(n_threads=8)
+    zero = oracle_mod.Oracle(_ghost_plate_scene(Tc, 0.0, t=t, xi=xi)).trace(n_threads=8)
+    assert np.array_equal(plain["flags"], zero["flags"]) and np.array_equal(plain["x"], zero["x"])
+    assert abs(np.mean((plain["flags"] & 1) == 1) - Tc ** 2) < 5 * math.sqrt(Tc ** 2 / N)
