@@ -253,6 +253,25 @@ __device__ __forceinline__ void unit_members(const DSource& s, uint32_t nb, uint
     nm = b > a ? (uint32_t)(b - a) : 0u;
 }
 
+// Accounting of photons the entry stage stops (the dynamic transmission test): record and loss counters.
+// None is detected there, so unlike consume() it carries no moment partials through the tile.
+__device__ __forceinline__ void account_lost(const TraceParams& P, uint32_t flags, float lam, bool v, uint64_t rec_index,
+                                             int lane, unsigned long long* cnt) {
+    if (v && P.records) {
+        phosim_photon_record rec;
+        rec.x = rec.y = rec.xc = rec.yc = 0.0;
+        rec.lambda = (double)lam;
+        rec.flags = flags; rec.pix = -1;
+        P.records[rec_index] = rec;
+    }
+    const uint32_t reason = v ? ((flags >> 8) & 0xffu) : 0u;
+#pragma unroll
+    for (int q = 1; q <= 8; ++q) {
+        const unsigned b = __ballot_sync(0xffffffffu, reason == (uint32_t)q);
+        if (lane == 0) cnt[1 + q] += __popc(b);
+    }
+}
+
 #ifndef PHOSIM_DS_MEMBERS_MIN_BLOCKS
 #define PHOSIM_DS_MEMBERS_MIN_BLOCKS 4
 #endif
@@ -284,7 +303,6 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
         __syncwarp();
         const SourceS& ss = src_mem[warp];
         const uint32_t nb = ss.bundle;          // the same for the whole warp (one source per tile)
-        TileAcc<true> A = {};
         int queued = 0;
         uint32_t base = 0;
         for (;;) {
@@ -310,20 +328,15 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                     if (valid) rej = early_reject_surface_f(P, ss, src, u, lam);
                     go_on = valid && rej < 0;
                     const bool dropped = valid && !go_on;
-                    PhotonOutS R;
-                    R.x = R.y = R.xc = R.yc = ds_f(0.f);
-                    R.lam = lam;
-                    R.pix = -1;
-                    R.flags = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
+                    const uint32_t fl = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
                     if (nb <= 1) {
-                        consume<true>(P, R, dropped, s.rec_off + (u - s.first), ss.ref_x, ss.ref_y, lane, A, cnt);
+                        account_lost(P, fl, lam, dropped, s.rec_off + (u - s.first), lane, cnt);
                     } else if (__any_sync(0xffffffffu, dropped)) {
                         uint64_t lo;
                         uint32_t nm;
                         unit_members(s, nb, u, lo, nm);
                         for (uint32_t m = 0; m < nb; ++m)
-                            consume<true>(P, R, dropped && m < nm, s.rec_off + (lo + m - s.first), ss.ref_x, ss.ref_y,
-                                          lane, A, cnt);
+                            account_lost(P, fl, lam, dropped && m < nm, s.rec_off + (lo + m - s.first), lane, cnt);
                     }
                 }
                 const unsigned gmask = __ballot_sync(0xffffffffu, go_on);
@@ -367,8 +380,7 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                     uint32_t nm;
                     unit_members(s, nb, u, lo, nm);
                     for (uint32_t m = 0; m < nb; ++m)
-                        consume<true>(P, Q, dropped && m < nm, s.rec_off + (lo + m - s.first), ss.ref_x, ss.ref_y, lane,
-                                      A, cnt);
+                        account_lost(P, Q.flags, Q.lam, dropped && m < nm, s.rec_off + (lo + m - s.first), lane, cnt);
                 }
             }
             if (drained && queued == 0) break;

@@ -111,3 +111,28 @@ def test_grad_refuses_ghosts():
         s.grad(np.zeros((1, 5)), [(0, 0)])
     assert e.value.code == -4
     s.close()
+
+
+def test_stage_timing_reports_each_kernel():
+    """phosim_set_stage_timing / phosim_stage_times: the double-single trace launches the chief-ray, entry and
+    optics kernels, whose event times are positive and add up to the call's own time; a short output array is
+    refused."""
+    import ctypes as C
+    sc = I.paraboloid_scene(n_photons=200_000, screen_n=128)
+    s = P.Scene(sc, P.MIXED_DS, early_reject=True)
+    L = P.lib()
+    img = torch.zeros((256, 256), dtype=torch.int32, device="cuda")
+    assert L.phosim_set_stage_timing(s.h, 1) == 0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    s.trace(img)
+    b.record()
+    ms = (C.c_double * 5)()
+    assert L.phosim_stage_times(s.h, ms, 5) == 0
+    torch.cuda.synchronize()
+    t = list(ms)
+    assert t[0] > 0 and t[1] == 0 and t[2] > 0 and t[3] > 0 and t[4] == 0
+    assert sum(t) <= a.elapsed_time(b) * 1.05 + 0.05
+    assert L.phosim_stage_times(s.h, ms, 4) == -1
+    L.phosim_set_stage_timing(s.h, 0)
+    s.close()
