@@ -136,3 +136,32 @@ def test_stage_timing_reports_each_kernel():
     assert L.phosim_stage_times(s.h, ms, 4) == -1
     L.phosim_set_stage_timing(s.h, 0)
     s.close()
+
+
+def test_bundle_and_reflection_limits():
+    """Background bundles above PHOSIM_MAX_BUNDLE are LIMIT, negative ones or a negative spread INVALID; a
+    reflection table with T + R > 1 or R < 0 is refused at load; the scene stays usable."""
+    sc = I.paraboloid_scene(n_photons=1000, screen_n=64)
+    s = P.Scene(sc)
+    img = torch.zeros((256, 256), dtype=torch.int32, device="cuda")
+    for bundle, sigma, code in ((4097, 0.01, -6), (-1, 0.01, -1), (8, -0.5, -1)):
+        src = sc.sources.subset([0])
+        src.bundle = np.array([bundle], np.int32)
+        src.bundle_sigma = np.array([sigma])
+        s.set_sources(src)
+        with pytest.raises(P.PhosimError) as e:
+            s.trace(img)
+        assert e.value.code == code, (bundle, sigma)
+    s.set_sources(sc.sources)
+    for R in (0.6, -0.1):
+        coat = I.Coating(lam0=400.0, dlam=300.0, theta0=0.0, dtheta=1.6, table=np.array([[0.5]]),
+                         reflect=np.array([[R]]))
+        with pytest.raises(P.PhosimError) as e:
+            s.load_optics(sc.surfaces, sc.materials, [coat])
+        assert e.value.code == -1
+    ref = G.run_gpu(sc, P.PLAIN_FP64, records=False)
+    img.zero_()
+    s.trace(img)
+    torch.cuda.synchronize()
+    assert np.array_equal(img.cpu().numpy().view(np.uint32), ref["image"])
+    s.close()
