@@ -268,6 +268,9 @@ def batched_leg(sc2, args, dev, stream, precision):
     torch.cuda.synchronize(dev)
     ms = a.elapsed_time(b) / steps
     n = int(sc.sources.n_photons.sum())
+    c = scn.counters()
+    if not (int(c[0]) == n and int(c[1]) + int(c[2:].sum()) == n):
+        raise RuntimeError(f"batched trace accounted for {int(c[1]) + int(c[2:].sum())} of {n} photons")
     scn.close()
     kinds = np.bincount(sc.sources.kind, minlength=3)
     return {"workload": f"{kinds[0]} stars + {kinds[1]} Sersic galaxies (counts log-uniform 1e2-1e7) + {kinds[2]} "
@@ -469,6 +472,8 @@ def main():
     other_value = photons * world * args.plain_steps / t_other
     plain_value = photons * world * args.plain_steps / t_plain
     counters = head.counters()
+    if not (int(counters[0]) == photons and int(counters[1]) + int(counters[2:].sum()) == photons):
+        raise RuntimeError(f"headline trace accounted for {int(counters[1]) + int(counters[2:].sum())} of {photons} photons")
 
     if rank != 0:
         if world > 1:

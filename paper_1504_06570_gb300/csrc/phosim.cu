@@ -1017,7 +1017,8 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         if (use_graph && chunk_tiles >= n_tiles) {
             const KernelLaunch L[4] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
                                        {ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, stage_args},
-                                       {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics), block, stage_args},
+                                       {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics),
+                                        dim3((unsigned)ds_optics_threads(sc->threads)), stage_args},
                                        {ds_members_kernel_ptr(), dim3((unsigned)blocks_members), block, stage_args}};
             phosim_status gs = launch_graph(sc, mode, L, bundles ? 4 : 3, st);
             if (gs != PHOSIM_OK) return gs;

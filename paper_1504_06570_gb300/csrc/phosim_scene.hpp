@@ -80,5 +80,6 @@ const void* ds_members_kernel_ptr();
 cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm, int* members_per_sm);
 const void* ds_entry_kernel_ptr();
 const void* ds_optics_kernel_ptr();
+int ds_optics_threads(int threads);      // the optics stage's block size for a schedule's block size
 void free_all(std::vector<void*>& v);
 }  // namespace phosim

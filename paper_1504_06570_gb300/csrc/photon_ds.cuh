@@ -441,112 +441,141 @@ __device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHi
 }
 
 // Surfaces in order (Sec. 2.4.2) and at the detector surface the sensor (detect_ds): the steps of
-// optics<MIXED = true, FULL = true> in photon.cuh.  For a bundle's ray (hand_off given) the hit on the detector
-// surface is handed over for its photons instead, and R.flags = kHandedOff.
+// optics<MIXED = true, FULL = true> in photon.cuh, one surface per call of surface_step_ds.  For a bundle's ray
+// (hand_off given) the hit on the detector surface is handed over for its photons instead, and
+// R.flags = kHandedOff.
 constexpr uint32_t kHandedOff = 0x80000000u;
 
-__device__ __forceinline__ void optics_ds(const TraceParams& P, ds X[3], ds D[3], float lam, int src, uint64_t ray,
-                                          PhotonOutS& R, const MemberDrawS* mb = nullptr,
-                                          DetectorHit* hand_off = nullptr) {
-    const bool ghosts = (P.flags & kGhostFlag) != 0;
-    ds n_cur = ds_f(1.f);
-    int glass_mat = -1;
-    ds glass_n = ds_f(1.f), glass_inv = ds_f(1.f);
-    int si = 0, dir = 1, bounces = 0, n_ghost = 0;
-#pragma unroll 1
-    for (;;) {
-        if (si < 0 || si >= P.n_surf) break;
-        const DSurface& S = P.surf[si];
-        const DSurfaceS& E = P.surf_s[si];
-        const int flags = S.flags;
-        ds p[3], dl[3];
-        to_surface_ds(E, flags, X, D, p, dl);
-        ds l, Nv[3];
-        const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
-        if (why) { R.flags = lost(why, si); return; }
-        if (bounces > 0 && !(l.hi > 0.f)) { R.flags = lost(PHOSIM_LOST_MISSED, si); return; }
-        p[0] = dfma(l, dl[0], p[0]);
-        p[1] = dfma(l, dl[1], p[1]);
-        p[2] = dfma(l, dl[2], p[2]);
-        if (S.kind == PHOSIM_DETECTOR) {
-            // the hit on the detector surface, its direction and the medium in front of it
-            DetectorHit H;
-            H.px = p[0]; H.py = p[1];
-            H.dl[0] = dl[0]; H.dl[1] = dl[1]; H.dl[2] = dl[2];
-            H.N[0] = Nv[0]; H.N[1] = Nv[1]; H.N[2] = Nv[2];
-            H.n_cur = n_cur;
-            H.si = si;
-            if (hand_off) {
-                *hand_off = H;
-                R.flags = kHandedOff;
-                return;
-            }
-            detect_ds(P, H, lam, src, ray, R, mb);
-            return;
-        }
-        // clear aperture
-        const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
-        if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return; }
-        // coating accept-reject at the incidence angle and wavelength
-        if (S.coat_slot >= 0) {
-            const DCoating& C = P.coat[S.coating];
-            int it = 0;
-            if (C.nt > 1) {
-                const float cosi = fabsf(dl[0].hi * Nv[0].hi + dl[1].hi * Nv[1].hi + dl[2].hi * Nv[2].hi);
-                const float th = acosf(fminf(1.f, cosi));
-                it = (int)floorf((th - C.th0f) * C.inv_dthf);
-                it = it < 0 ? 0 : (it > C.nt - 1 ? C.nt - 1 : it);
-            }
-            const size_t ix = (size_t)coat_lambda_bin(C, lam) * C.nt + it;
-            const uint32_t w = bounces > 0 ? ghost_word_ds(P, src, ray, n_ghost++) : coat_word(P, src, ray, S.coat_slot);
-            if (!((unsigned long long)w < __ldg(C.T_thr + ix))) {
-                // reflected backwards (a ghost) with probability R, absorbed otherwise
-                if (ghosts && S.kind != PHOSIM_MIRROR && C.TR_thr && (unsigned long long)w < __ldg(C.TR_thr + ix)) {
-                    const ds dn2 = dot3(dl, Nv) * -2.f;
-                    dl[0] = dfma(dn2, Nv[0], dl[0]);
-                    dl[1] = dfma(dn2, Nv[1], dl[1]);
-                    dl[2] = dfma(dn2, Nv[2], dl[2]);
-                    dir = -dir;
-                    if (++bounces > kMaxGhostBounces) { R.flags = lost(PHOSIM_LOST_MISSED, si); return; }
-                    from_surface_ds(E, flags, p, dl, X, D);
-                    si += dir;
-                    continue;
-                }
-                R.flags = lost(PHOSIM_LOST_COATING, si);
-                return;
-            }
-        }
-        if (S.kind == PHOSIM_MIRROR) {
-            const ds dn2 = dot3(dl, Nv) * -2.f;
-            dl[0] = dfma(dn2, Nv[0], dl[0]);
-            dl[1] = dfma(dn2, Nv[1], dl[1]);
-            dl[2] = dfma(dn2, Nv[2], dl[2]);
-        } else {
-            // the medium beyond the surface in the direction of travel (-1: vacuum)
-            const int mi = dir < 0 ? S.mat_before : S.material;
-            ds n_next = ds_f(1.f), inv_next = ds_f(1.f);
-            if (mi >= 0) {
-                const DMaterial& m = P.mat[mi];
-                if (m.kind == PHOSIM_SELLMEIER) {
-                    if (glass_mat != mi) {
-                        glass_n = sellmeier_ds(m, lam);
-                        glass_inv = ds_rcp(glass_n);
-                        glass_mat = mi;
-                    }
-                    n_next = glass_n;
-                    inv_next = glass_inv;
-                } else if (m.kind == PHOSIM_SILICON) {
-                    n_next = ds_f(silicon_index_f(lam));
-                    inv_next = ds_rcp(n_next);
-                }
-            }
-            if (!refract_ds(dl, Nv, n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return; }
-            n_cur = n_next;
-        }
-        from_surface_ds(E, flags, p, dl, X, D);
-        si += dir;
+// where a ray is in its walk through the surfaces: position and direction in the telescope frame, the surface
+// it meets next and the way it travels (backwards after a ghost reflection), the index of the medium it is in
+// and the last glass index computed
+struct OpticsWalk {
+    ds X[3], D[3];
+    ds n_cur, glass_n, glass_inv;
+    int glass_mat, si, dir, bounces, n_ghost;
+};
+
+__device__ __forceinline__ void walk_start(OpticsWalk& W, const ds X[3], const ds D[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { W.X[k] = X[k]; W.D[k] = D[k]; }
+    W.n_cur = ds_f(1.f);
+    W.glass_n = ds_f(1.f);
+    W.glass_inv = ds_f(1.f);
+    W.glass_mat = -1;
+    W.si = 0; W.dir = 1; W.bounces = 0; W.n_ghost = 0;
+}
+
+// The next surface of the walk; false once the ray has left it (R.flags then says lost, detected or handed off).
+__device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk& W, float lam, int src, uint64_t ray,
+                                                PhotonOutS& R, const MemberDrawS* mb = nullptr,
+                                                DetectorHit* hand_off = nullptr) {
+    const int si = W.si;
+    if (si < 0 || si >= P.n_surf) {
+        R.flags = lost(PHOSIM_LOST_MISSED, si < 0 ? 0 : P.n_surf);
+        return false;
     }
-    R.flags = lost(PHOSIM_LOST_MISSED, si < 0 ? 0 : P.n_surf);
+    const DSurface& S = P.surf[si];
+    const DSurfaceS& E = P.surf_s[si];
+    const int flags = S.flags;
+    ds p[3], dl[3];
+    to_surface_ds(E, flags, W.X, W.D, p, dl);
+    ds l, Nv[3];
+    const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
+    if (why) { R.flags = lost(why, si); return false; }
+    if (W.bounces > 0 && !(l.hi > 0.f)) { R.flags = lost(PHOSIM_LOST_MISSED, si); return false; }
+    p[0] = dfma(l, dl[0], p[0]);
+    p[1] = dfma(l, dl[1], p[1]);
+    p[2] = dfma(l, dl[2], p[2]);
+    if (S.kind == PHOSIM_DETECTOR) {
+        // the hit on the detector surface, its direction and the medium in front of it
+        DetectorHit H;
+        H.px = p[0]; H.py = p[1];
+        H.dl[0] = dl[0]; H.dl[1] = dl[1]; H.dl[2] = dl[2];
+        H.N[0] = Nv[0]; H.N[1] = Nv[1]; H.N[2] = Nv[2];
+        H.n_cur = W.n_cur;
+        H.si = si;
+        if (hand_off) {
+            *hand_off = H;
+            R.flags = kHandedOff;
+            return false;
+        }
+        detect_ds(P, H, lam, src, ray, R, mb);
+        return false;
+    }
+    // clear aperture
+    const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
+    if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return false; }
+    // coating accept-reject at the incidence angle and wavelength
+    if (S.coat_slot >= 0) {
+        const DCoating& C = P.coat[S.coating];
+        int it = 0;
+        if (C.nt > 1) {
+            const float cosi = fabsf(dl[0].hi * Nv[0].hi + dl[1].hi * Nv[1].hi + dl[2].hi * Nv[2].hi);
+            const float th = acosf(fminf(1.f, cosi));
+            it = (int)floorf((th - C.th0f) * C.inv_dthf);
+            it = it < 0 ? 0 : (it > C.nt - 1 ? C.nt - 1 : it);
+        }
+        const size_t ix = (size_t)coat_lambda_bin(C, lam) * C.nt + it;
+        const uint32_t w = W.bounces > 0 ? ghost_word_ds(P, src, ray, W.n_ghost++) : coat_word(P, src, ray, S.coat_slot);
+        if (!((unsigned long long)w < __ldg(C.T_thr + ix))) {
+            // reflected backwards (a ghost) with probability R, absorbed otherwise
+            if ((P.flags & kGhostFlag) && S.kind != PHOSIM_MIRROR && C.TR_thr &&
+                (unsigned long long)w < __ldg(C.TR_thr + ix)) {
+                const ds dn2 = dot3(dl, Nv) * -2.f;
+                dl[0] = dfma(dn2, Nv[0], dl[0]);
+                dl[1] = dfma(dn2, Nv[1], dl[1]);
+                dl[2] = dfma(dn2, Nv[2], dl[2]);
+                W.dir = -W.dir;
+                if (++W.bounces > kMaxGhostBounces) { R.flags = lost(PHOSIM_LOST_MISSED, si); return false; }
+                from_surface_ds(E, flags, p, dl, W.X, W.D);
+                W.si = si + W.dir;
+                return true;
+            }
+            R.flags = lost(PHOSIM_LOST_COATING, si);
+            return false;
+        }
+    }
+    if (S.kind == PHOSIM_MIRROR) {
+        const ds dn2 = dot3(dl, Nv) * -2.f;
+        dl[0] = dfma(dn2, Nv[0], dl[0]);
+        dl[1] = dfma(dn2, Nv[1], dl[1]);
+        dl[2] = dfma(dn2, Nv[2], dl[2]);
+    } else {
+        // the medium beyond the surface in the direction of travel (-1: vacuum)
+        const int mi = W.dir < 0 ? S.mat_before : S.material;
+        ds n_next = ds_f(1.f), inv_next = ds_f(1.f);
+        if (mi >= 0) {
+            const DMaterial& m = P.mat[mi];
+            if (m.kind == PHOSIM_SELLMEIER) {
+                if (W.glass_mat != mi) {
+                    W.glass_n = sellmeier_ds(m, lam);
+                    W.glass_inv = ds_rcp(W.glass_n);
+                    W.glass_mat = mi;
+                }
+                n_next = W.glass_n;
+                inv_next = W.glass_inv;
+            } else if (m.kind == PHOSIM_SILICON) {
+                n_next = ds_f(silicon_index_f(lam));
+                inv_next = ds_rcp(n_next);
+            }
+        }
+        if (!refract_ds(dl, Nv, W.n_cur * inv_next)) { R.flags = lost(PHOSIM_LOST_TIR, si); return false; }
+        W.n_cur = n_next;
+    }
+    from_surface_ds(E, flags, p, dl, W.X, W.D);
+    W.si = si + W.dir;
+    return true;
+}
+
+// the whole walk of one ray
+__device__ __forceinline__ void optics_ds(const TraceParams& P, const ds X[3], const ds D[3], float lam, int src,
+                                          uint64_t ray, PhotonOutS& R, const MemberDrawS* mb = nullptr,
+                                          DetectorHit* hand_off = nullptr) {
+    OpticsWalk W;
+    walk_start(W, X, D);
+#pragma unroll 1
+    while (surface_step_ds(P, W, lam, src, ray, R, mb, hand_off)) {
+    }
 }
 
 // Bilinear screen gradient (Sec. 2.3.2) at a double-single screen position; single-precision weights

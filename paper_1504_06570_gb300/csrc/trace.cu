@@ -234,15 +234,25 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
 // (the staging of wavefront path tracers), each half has a smaller code footprint and fewer live values:
 //   ds_entry_kernel:  early rejection, sampling and the layers for the tiles of one chunk; survivors append
 //                     their entrance-plane state (64 bytes) to a buffer in device memory;
-//   ds_optics_kernel: the surfaces, the sensor and the accounting, one state per thread.
+//   ds_optics_kernel: the surfaces, the sensor and the accounting, one state per thread.  The warps of a
+//                     block take the surfaces in step (a barrier after each surface): warps left to run
+//                     freely spread over the whole surface code and the SM's instruction cache misses.
 // The per-photon arithmetic and its order are those of trace_photon_ds, so both give the same results.
 // ---------------------------------------------------------------------------------------------------------
 #ifndef PHOSIM_DS_ENTRY_MIN_BLOCKS
 #define PHOSIM_DS_ENTRY_MIN_BLOCKS 6
 #endif
 #ifndef PHOSIM_DS_OPTICS_MIN_BLOCKS
-#define PHOSIM_DS_OPTICS_MIN_BLOCKS 8
+#define PHOSIM_DS_OPTICS_MIN_BLOCKS 6
 #endif
+#ifndef PHOSIM_DS_LOCKSTEP
+#define PHOSIM_DS_LOCKSTEP 1
+#endif
+// threads per block of the optics stage (0: the schedule's block size)
+#ifndef PHOSIM_DS_OPTICS_THREADS
+#define PHOSIM_DS_OPTICS_THREADS 0
+#endif
+constexpr int kOpticsMaxThreads = PHOSIM_DS_OPTICS_THREADS ? PHOSIM_DS_OPTICS_THREADS : 256;
 
 // A work unit of the two-kernel path is a photon, or for a bundle of n photons per ray (Sec. 3.2) a ray:
 // the ray is traced once and its photons (those in the call's range) only go through the sensor apart.
@@ -440,17 +450,26 @@ __device__ __forceinline__ void account_ds(const TraceParams& P, const PhotonOut
     }
 }
 
-__global__ void __launch_bounds__(256, PHOSIM_DS_OPTICS_MIN_BLOCKS) ds_optics_kernel(const __grid_constant__ TraceParams P,
-                                                                                     const DSStage S) {
-    __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
+__global__ void __launch_bounds__(kOpticsMaxThreads, PHOSIM_DS_OPTICS_MIN_BLOCKS)
+    ds_optics_kernel(const __grid_constant__ TraceParams P, const DSStage S) {
+    __shared__ unsigned long long cnt_mem[kOpticsMaxThreads / 32][kNumCounters];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lanes_below = (1u << lane) - 1u;
     unsigned long long* cnt = cnt_mem[warp];
     if (lane < kNumCounters) cnt[lane] = 0;
     __syncwarp();
     const unsigned long long n = *S.n_state;
-    const unsigned long long stride = (unsigned long long)gridDim.x * kWarpsPerBlock * 32ull;
-    for (unsigned long long b = ((unsigned long long)blockIdx.x * kWarpsPerBlock + warp) * 32ull; b < n; b += stride) {
+    // any block size up to 256 threads (the schedule's)
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+#if PHOSIM_DS_LOCKSTEP
+    // a block's states at a time, all its warps meeting the surfaces together (a barrier after each), so
+    // that the SM's warps fetch the same stretch of code rather than as many stretches as warps
+    for (unsigned long long b0 = (unsigned long long)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
+        const unsigned long long b = b0 + (unsigned long long)warp * 32ull;
+#else
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (unsigned long long)warp * 32ull; b < n;
+         b += stride) {
+#endif
         const unsigned long long e = b + lane;
         const bool v = e < n;
         PhotonOutS R;
@@ -459,15 +478,33 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_OPTICS_MIN_BLOCKS) ds_optics_ke
         int src = 0;
         uint64_t u = 0;
         DetectorHit H;
+#if PHOSIM_DS_LOCKSTEP
+        OpticsWalk W;
+        bool go = false, bundled = false;
+        if (v) {
+            const DSState st = S.state[e];
+            src = st.src;
+            u = st.idx;
+            R.lam = st.lam;
+            bundled = P.sources[src].bundle > 1;
+            const ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
+            walk_start(W, X, D);
+            go = true;
+        }
+        while (__syncthreads_or(go)) {
+            if (go) go = surface_step_ds(P, W, R.lam, src, u, R, nullptr, bundled ? &H : nullptr);
+        }
+#else
         if (v) {
             const DSState st = S.state[e];
             src = st.src;
             u = st.idx;
             R.lam = st.lam;
             const bool bundled = P.sources[src].bundle > 1;
-            ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
+            const ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
             optics_ds(P, X, D, st.lam, src, u, R, nullptr, bundled ? &H : nullptr);
         }
+#endif
         // a bundle's ray that reached the detector surface hands its hit over to the bundle stage
         const bool handed = v && R.flags == kHandedOff;
         const unsigned hmask = __ballot_sync(0xffffffffu, handed);
@@ -506,8 +543,9 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_MEMBERS_MIN_BLOCKS) ds_members_
     if (lane < kNumCounters) cnt[lane] = 0;
     __syncwarp();
     const unsigned long long n = *S.n_hits;
-    const unsigned long long stride = (unsigned long long)gridDim.x * kWarpsPerBlock * 32ull;
-    for (unsigned long long b = ((unsigned long long)blockIdx.x * kWarpsPerBlock + warp) * 32ull; b < n; b += stride) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (unsigned long long)warp * 32ull; b < n;
+         b += stride) {
         const unsigned long long e = b + lane;
         const bool v = e < n;
         DSHit h;
@@ -583,8 +621,10 @@ cudaError_t launch_ds_entry(const TraceParams& P, const DSStage& S, int blocks, 
     return cudaGetLastError();
 }
 
+int ds_optics_threads(int threads) { return PHOSIM_DS_OPTICS_THREADS ? PHOSIM_DS_OPTICS_THREADS : threads; }
+
 cudaError_t launch_ds_optics(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st) {
-    ds_optics_kernel<<<blocks, threads, 0, st>>>(P, S);
+    ds_optics_kernel<<<blocks, ds_optics_threads(threads), 0, st>>>(P, S);
     return cudaGetLastError();
 }
 
@@ -597,7 +637,8 @@ const void* ds_members_kernel_ptr() { return (const void*)ds_members_kernel; }
 
 cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm, int* members_per_sm) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(entry_per_sm, ds_entry_kernel, threads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(optics_per_sm, ds_optics_kernel, threads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(optics_per_sm, ds_optics_kernel, ds_optics_threads(threads), 0);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(members_per_sm, ds_members_kernel, threads, 0);
 }

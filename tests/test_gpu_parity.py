@@ -106,6 +106,25 @@ def test_schedule_does_not_change_results(oracle_mod, schedule):
     assert np.array_equal(gpu["image"], ref["image"])
 
 
+@pytest.mark.parametrize("schedule", [(32, 32), (64, 96), (128, 0), (256, 1024)])
+def test_schedule_does_not_change_double_single_stages(schedule):
+    """The two-kernel double-single path (entry, optics and bundle stages, each with its own grid) under any
+    block and tile size: every photon is accounted for once and the records and image do not change."""
+    counts = [3, 5000, 12000, 640, 2000]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=19))
+    sc.sources.bundle = np.array([1, 1, 1, 1, 8], np.int32)
+    sc.sources.bundle_sigma = np.array([0.0, 0.0, 0.0, 0.0, 0.004])
+    ref = G.run_gpu(sc, P.MIXED_DS, early_reject=True)
+    gpu = G.run_gpu(sc, P.MIXED_DS, early_reject=True, schedule=schedule)
+    n = int(np.sum(counts))
+    for out in (ref, gpu):
+        c = out["counters"]
+        assert c[0] == n and c[1] + sum(c[2:]) == n, c
+        assert np.count_nonzero(out["rec"]["flags"]) == n
+    assert np.array_equal(gpu["rec"], ref["rec"])
+    assert np.array_equal(gpu["image"], ref["image"])
+
+
 def test_photon_ranges_compose():
     """Tracing photons [0, a) then [a, n) of each source gives the records and image of [0, n)."""
     counts = np.array([700, 1500, 33], np.uint64)
