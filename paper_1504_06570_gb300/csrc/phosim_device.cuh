@@ -97,6 +97,7 @@ struct DSource {
     double xi, eta, zfac, t0, t_exp, a, b, cpa, spa;
     double bsig;                              // sigma of the spread of a ray's photons on the detector, mm
     double ref_x, ref_y;
+    float ref_s[4];                           // ref_x, ref_y as double-single pairs (hi, lo, hi, lo)
     uint64_t first, count, rec_off;           // photons [first, first + count); record index of the first
     uint64_t ufirst, ucount;                  // work units of the two-kernel path: rays of a bundle, else photons
 };

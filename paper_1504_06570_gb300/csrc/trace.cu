@@ -428,24 +428,34 @@ __device__ __forceinline__ void account_ds(const TraceParams& P, const PhotonOut
         if (lane == 0) cnt[1 + q] += __popc(bq);
     }
     if (P.moments && dmask) {
-        double mm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        // Per-source partial sums of the warp: the states arrive in runs of one source (a warp of the entry
+        // stage appends its survivors together), so the lanes of a source are contiguous segments.  An
+        // inclusive segmented scan in double-single (exact products of the single-precision offsets from the
+        // chief ray, sums to ~2^-47) leaves each segment's sums in its last lane, which adds them to the
+        // source's double-precision moments: one set of atomics per segment, not per photon, and the FP64
+        // pipe (a sixty-fourth of the FP32 rate on this GPU) only converts the partials.
+        ds mm[6] = {ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f)};
         if (det) {
-            const double fx = (double)(R.x - ds_of(s.ref_x)).hi, fy = (double)(R.y - ds_of(s.ref_y)).hi;
-            mm[0] = 1.0; mm[1] = fx; mm[2] = fy; mm[3] = fx * fx; mm[4] = fx * fy; mm[5] = fy * fy;
+            const float fx = (R.x - ds{s.ref_s[0], s.ref_s[1]}).hi, fy = (R.y - ds{s.ref_s[2], s.ref_s[3]}).hi;
+            mm[0] = ds_f(1.f); mm[1] = ds_f(fx); mm[2] = ds_f(fy);
+            mm[3] = two_prod(fx, fx); mm[4] = two_prod(fx, fy); mm[5] = two_prod(fy, fy);
         }
-        const int src0 = __shfl_sync(0xffffffffu, src, __ffs(dmask) - 1);
-        if (__all_sync(0xffffffffu, !det || src == src0)) {
+        const int prev = __shfl_up_sync(0xffffffffu, src, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != src);
+        const int first = 31 - __clz(heads & (lane == 31 ? 0xffffffffu : (2u << lane) - 1u));
 #pragma unroll
-            for (int q = 0; q < 6; ++q) mm[q] = warp_sum(mm[q]);
-            if (lane == 0) {
-                double* M = P.moments + (size_t)src0 * PHOSIM_MOMENT_WORDS;
+        for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
+            for (int q = 0; q < 6; ++q) {
+                const ds t = {__shfl_up_sync(0xffffffffu, mm[q].hi, d), __shfl_up_sync(0xffffffffu, mm[q].lo, d)};
+                if (lane - d >= first) mm[q] = mm[q] + t;
             }
-        } else if (det) {
+        }
+        const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (last && mm[0].hi > 0.f) {
             double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) atomicAdd(M + q, mm[q]);
+            for (int q = 0; q < 6; ++q) atomicAdd(M + q, ds_value(mm[q]));
         }
     }
 }
@@ -589,6 +599,8 @@ __global__ void chief_ray_kernel(const __grid_constant__ TraceParams P, DSource*
     const bool ok = (R.flags & PHOSIM_F_DETECTED) != 0;
     S.ref_x = ok ? R.x : 0.0;
     S.ref_y = ok ? R.y : 0.0;
+    const ds rx = ds_of(S.ref_x), ry = ds_of(S.ref_y);
+    S.ref_s[0] = rx.hi; S.ref_s[1] = rx.lo; S.ref_s[2] = ry.hi; S.ref_s[3] = ry.lo;
     if (moments) {
         moments[(size_t)s * PHOSIM_MOMENT_WORDS + 6] = S.ref_x;
         moments[(size_t)s * PHOSIM_MOMENT_WORDS + 7] = S.ref_y;
