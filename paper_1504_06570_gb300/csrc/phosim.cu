@@ -175,6 +175,7 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
     }
     if (!(flags & (SF_CONIC | SF_EVEN | SF_ODD | SF_ZERN))) flags |= SF_FLAT_ONLY;
     if (s.pert[3] != 0.0 || s.pert[4] != 0.0 || s.pert[5] != 0.0) flags |= SF_ROTATED;
+    if (s.pert[0] != 0.0 || s.pert[1] != 0.0) flags |= SF_DECENTERED;
     d.flags = flags;
     rotation(s.pert, d.M);
     d.o[0] = s.pert[0];

@@ -19,7 +19,10 @@ constexpr int kMaxCoatings = 8;
 constexpr int kZPoly = 28;                 // monomials x^a y^b, a + b <= 6
 constexpr int kSedGuide = 256;             // guide-table buckets of the wavelength-bin draw (its top 8 bits)
 
-enum SurfFlags : int { SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FLAT_ONLY = 16, SF_ROTATED = 32 };
+enum SurfFlags : int {
+    SF_CONIC = 1, SF_EVEN = 2, SF_ODD = 4, SF_ZERN = 8, SF_FLAT_ONLY = 16, SF_ROTATED = 32,
+    SF_DECENTERED = 64          // a vertex off the axis (the double-single transforms skip zero x, y offsets)
+};
 
 struct DSurface {
     int kind, material, coating, coat_slot;   // coat_slot: index of this surface's accept draw, -1 none

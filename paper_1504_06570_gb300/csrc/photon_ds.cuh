@@ -199,34 +199,11 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
     return true;
 }
 
-// Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
-// vertex branch, then Newton's method for the aspheric and Zernike terms until the step is below 1e-8 mm.
-// The Newton slope F'(l) only scales the step, so it is taken in single precision.
-static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
-                                                 ds N[3]) {
-    if (flags & SF_FLAT_ONLY) {
-        if (d[2].hi == 0.f) return PHOSIM_LOST_MISSED;
-        l = -(p[2] / d[2]);
-        N[0] = ds_f(0.f); N[1] = ds_f(0.f); N[2] = ds_f(1.f);
-        return 0;
-    }
-    const ds A = dfma(E.kc * d[2], d[2], E.c * dfma(d[0], d[0], d[1] * d[1]));
-    const ds b = dfma(E.kc * p[2], d[2], E.c * dfma(p[0], d[0], p[1] * d[1])) - d[2];
-    const ds C = dfma(E.kc * p[2], p[2], E.c * dfma(p[0], p[0], p[1] * p[1])) - p[2] * 2.f;
-    const ds disc = dfma(b, b, -(A * C));
-    if (disc.hi < 0.f) return PHOSIM_LOST_MISSED;
-    const ds sq = ds_sqrt(disc);
-    const ds q = b.hi >= 0.f ? -(b + sq) : sq - b;
-    if (q.hi == 0.f) return PHOSIM_LOST_MISSED;
-    l = C / q;
-    if (A.hi != 0.f && (ds_f(1.f) - E.kc * dfma(l, d[2], p[2])).hi < 0.f) l = q / A;
-    if (!(flags & (SF_EVEN | SF_ODD | SF_ZERN))) {
-        const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]), z = dfma(l, d[2], p[2]);
-        const ds vx = -(E.c * x), vy = -(E.c * y), vz = ds_f(1.f) - E.kc * z;
-        const ds inv = ds_rsqrt(dfma(vx, vx, dfma(vy, vy, vz * vz)));
-        N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
-        return 0;
-    }
+// Newton's method in double-single on F(l) = p_z + l d_z - S(p_x + l d_x, p_y + l d_y) from l until the step
+// is below 1e-8 mm (the Newton slope F'(l) only scales the step, so it is taken in single precision); the
+// normal from the slopes at the last point
+__device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
+                                              ds N[3]) {
     ds zx = ds_f(0.f), zy = ds_f(0.f);
 #pragma unroll 1
     for (int it = 0; it < 20; ++it) {
@@ -247,6 +224,108 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
     return PHOSIM_LOST_NEWTON;
 }
 
+// Sag and slopes in single precision (the hi parts of the surface's constants), for the first Newton steps
+__device__ __forceinline__ bool sag_f(const DSurfaceS& E, int flags, float x, float y, float& z, float& zx, float& zy) {
+    const float r2 = fmaf(x, x, y * y);
+    float g = 0.f;
+    z = 0.f;
+    if (flags & SF_CONIC) {
+        const float arg = fmaf(-E.k1c2.hi, r2, 1.f);
+        if (arg < 0.f) return false;
+        const float rs = rsqrtf(arg);
+        z = E.c.hi * r2 / fmaf(arg, rs, 1.f);
+        g = E.c.hi * rs;
+    }
+    if (flags & SF_EVEN) {
+        const float u = r2 * E.inv_rn2.hi;
+        const float pe = fmaf(fmaf(fmaf(E.ae[3].hi, u, E.ae[2].hi), u, E.ae[1].hi), u, E.ae[0].hi);
+        z = fmaf(u * u, pe, z);
+        const float pd = fmaf(fmaf(fmaf(E.aed[3].hi, u, E.aed[2].hi), u, E.aed[1].hi), u, E.aed[0].hi);
+        g = fmaf(u * E.inv_rn2.hi, pd, g);
+    }
+    if (flags & SF_ODD) {
+        const float rho = sqrtf(r2) * E.inv_rn.hi;
+        const float u = rho * rho;
+        const float po = fmaf(fmaf(fmaf(E.ao[3].hi, u, E.ao[2].hi), u, E.ao[1].hi), u, E.ao[0].hi);
+        z = fmaf(u * rho, po, z);
+        const float pd = fmaf(fmaf(fmaf(E.aod[3].hi, u, E.aod[2].hi), u, E.aod[1].hi), u, E.aod[0].hi);
+        g = fmaf(rho * E.inv_rn2.hi, pd, g);
+    }
+    zx = x * g;
+    zy = y * g;
+    if (flags & SF_ZERN) {
+        float zz, zu, zv;
+        zern_eval_f(E.zp, x * E.zinv, y * E.zinv, zz, zu, zv);
+        z += zz;
+        zx = fmaf(zu, E.zinv, zx);
+        zy = fmaf(zv, E.zinv, zy);
+    }
+    return true;
+}
+
+// Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
+// vertex branch, then Newton's method for the aspheric and Zernike terms until the step is below 1e-8 mm.
+// Newton converges to the same root from any start close enough to it, so for the aspheric and Zernike
+// surfaces the start (the conic's root, then Newton steps while they exceed 10 um: the asphere moves the root
+// by up to millimetres) is computed in single precision, and the double-single steps only take it from
+// there to the final 1e-8 mm.
+static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
+                                                 ds N[3]) {
+    if (flags & SF_FLAT_ONLY) {
+        if (d[2].hi == 0.f) return PHOSIM_LOST_MISSED;
+        l = -(p[2] / d[2]);
+        N[0] = ds_f(0.f); N[1] = ds_f(0.f); N[2] = ds_f(1.f);
+        return 0;
+    }
+    const bool newton = (flags & (SF_EVEN | SF_ODD | SF_ZERN)) != 0;
+    if (newton) {
+        // the conic's root in single precision; a ray whose discriminant is not clearly positive (grazing or
+        // missing the conic) takes the double-single root below
+        const float c = E.c.hi, kc = E.kc.hi;
+        const float Af = fmaf(kc * d[2].hi, d[2].hi, c * fmaf(d[0].hi, d[0].hi, d[1].hi * d[1].hi));
+        const float bf = fmaf(kc * p[2].hi, d[2].hi, c * fmaf(p[0].hi, d[0].hi, p[1].hi * d[1].hi)) - d[2].hi;
+        const float Cf = fmaf(kc * p[2].hi, p[2].hi, c * fmaf(p[0].hi, p[0].hi, p[1].hi * p[1].hi)) - 2.f * p[2].hi;
+        const float disc = fmaf(bf, bf, -(Af * Cf));
+        if (disc > 1e-6f * bf * bf) {
+            const float sq = sqrtf(disc);
+            const float qf = bf >= 0.f ? -(bf + sq) : sq - bf;
+            float lf = Cf / qf;
+            if (Af != 0.f && fmaf(-kc, fmaf(lf, d[2].hi, p[2].hi), 1.f) < 0.f) lf = qf / Af;
+#pragma unroll 1
+            for (int it = 0; it < 4; ++it) {
+                const float x = fmaf(lf, d[0].hi, p[0].hi), y = fmaf(lf, d[1].hi, p[1].hi);
+                float zs, zxf, zyf;
+                if (!sag_f(E, flags, x, y, zs, zxf, zyf)) break;
+                const float dF = d[2].hi - zxf * d[0].hi - zyf * d[1].hi;
+                const float step = (fmaf(lf, d[2].hi, p[2].hi) - zs) / dF;
+                if (!(fabsf(step) < 1e30f)) break;
+                lf -= step;
+                if (fabsf(step) < 1e-2f) break;
+            }
+            if (fabsf(lf) < 1e30f) {
+                l = ds_f(lf);
+                return newton_ds(E, flags, p, d, l, N);
+            }
+        }
+    }
+    const ds A = dfma(E.kc * d[2], d[2], E.c * dfma(d[0], d[0], d[1] * d[1]));
+    const ds b = dfma(E.kc * p[2], d[2], E.c * dfma(p[0], d[0], p[1] * d[1])) - d[2];
+    const ds C = dfma(E.kc * p[2], p[2], E.c * dfma(p[0], p[0], p[1] * p[1])) - p[2] * 2.f;
+    const ds disc = dfma(b, b, -(A * C));
+    if (disc.hi < 0.f) return PHOSIM_LOST_MISSED;
+    const ds sq = ds_sqrt(disc);
+    const ds q = b.hi >= 0.f ? -(b + sq) : sq - b;
+    if (q.hi == 0.f) return PHOSIM_LOST_MISSED;
+    l = C / q;
+    if (A.hi != 0.f && (ds_f(1.f) - E.kc * dfma(l, d[2], p[2])).hi < 0.f) l = q / A;
+    if (newton) return newton_ds(E, flags, p, d, l, N);
+    const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]), z = dfma(l, d[2], p[2]);
+    const ds vx = -(E.c * x), vy = -(E.c * y), vz = ds_f(1.f) - E.kc * z;
+    const ds inv = ds_rsqrt(dfma(vx, vx, dfma(vy, vy, vz * vz)));
+    N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
+    return 0;
+}
+
 __device__ __forceinline__ ds dot3(const ds a[3], const ds b[3]) { return dfma(a[0], b[0], dfma(a[1], b[1], a[2] * b[2])); }
 
 // Snell's law in vector form (Sec. 2.4.2), mu = n1 / n2; false on total internal reflection
@@ -265,6 +344,11 @@ static __device__ PHOSIM_DS_STEP bool refract_ds(ds d[3], ds N[3], ds mu) {
 
 __device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, const ds x[3], const ds d[3], ds p[3],
                                               ds dl[3]) {
+    if (!(flags & (SF_ROTATED | SF_DECENTERED))) {     // a vertex on the axis: x - 0 is x
+        p[0] = x[0]; p[1] = x[1]; p[2] = x[2] - E.o[2];
+        dl[0] = d[0]; dl[1] = d[1]; dl[2] = d[2];
+        return;
+    }
     const ds rx = x[0] - E.o[0], ry = x[1] - E.o[1], rz = x[2] - E.o[2];
     if (!(flags & SF_ROTATED)) {
         p[0] = rx; p[1] = ry; p[2] = rz;
@@ -281,7 +365,12 @@ __device__ __forceinline__ void to_surface_ds(const DSurfaceS& E, int flags, con
 __device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, const ds p[3], const ds dl[3], ds x[3],
                                                 ds d[3]) {
     if (!(flags & SF_ROTATED)) {
-        x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1]; x[2] = p[2] + E.o[2];
+        if (flags & SF_DECENTERED) {
+            x[0] = p[0] + E.o[0]; x[1] = p[1] + E.o[1];
+        } else {
+            x[0] = p[0]; x[1] = p[1];
+        }
+        x[2] = p[2] + E.o[2];
         d[0] = dl[0]; d[1] = dl[1]; d[2] = dl[2];
         return;
     }
