@@ -26,8 +26,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "photons/s end-to-end on 1 GB300 vs plain FP64 path; PSF-moment error vs oracle"
-WORKLOAD = ("three-mirror 8.4 m telescope + 3-lens camera + 550-700 nm filter, 7 von Karman layers "
-            "(4096^2@1cm + 1024^2@64cm), 1000 stars, 1e8 photons, 4096^2 chip")
+def workload_name(photons=1e8, fine_n=4096, coarse_n=1024):
+    return ("three-mirror 8.4 m telescope + 3-lens camera + 550-700 nm filter, 7 von Karman layers "
+            f"({fine_n}^2@1cm + {coarse_n}^2@64cm), 1000 stars, {photons:.0e} photons, 4096^2 chip").replace("e+0", "e")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -35,7 +36,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--photons", type=float, default=1e8, help="photons per step per GPU")
@@ -52,7 +53,8 @@ def parse():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; only the samples that arrive between
+    mark() and stop() (the timed region) are kept."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -61,20 +63,27 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 5.0
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
 
+    def mark(self):
+        self.t0 = time.time()
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def stop(self):
         if not self.proc:
@@ -86,7 +95,9 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for t, l in self.lines:
+            if self.t0 is not None and t < self.t0:
+                continue
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -126,6 +137,23 @@ def recorded_traffic(photons, kernel):
     except OSError:
         return None
     for m in re.finditer(r"traffic_record: kernel=(\S+) bytes=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text):
+        if m.group(1) == kernel and m.group(4) == kernel_source_hash():
+            return int(m.group(2)) * photons / int(m.group(3))
+    return None
+
+
+INST_PROFILE = os.path.join(ROOT, "profiles", "ds_stages_three_mirror_2e7.md")
+
+
+def recorded_instructions(photons, kernel):
+    """Thread instructions one launch of a kernel executes (ncu smsp__inst_executed x threads per instruction on
+    the committed capture), scaled to this launch's photons, or None when the kernel sources changed since."""
+    import re
+    try:
+        text = open(INST_PROFILE).read()
+    except OSError:
+        return None
+    for m in re.finditer(r"inst_record: kernel=(\S+) thread_inst=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text):
         if m.group(1) == kernel and m.group(4) == kernel_source_hash():
             return int(m.group(2)) * photons / int(m.group(3))
     return None
@@ -353,7 +381,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "photons/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "oracle_sample": cpu["sample"]},
+            "config": {"workload": workload_name(args.photons, args.fine_n, args.coarse_n), "oracle_sample": cpu["sample"]},
             "cpu_baseline": {**cpu, "value": v},
             "e2e": {"value": v, "unit": "photons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -401,11 +429,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(scene, steps, warmup):
+    def timed(scene, steps, warmup, on_start=None):
         for _ in range(warmup):
             scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
+        if on_start:
+            on_start()
         for a, b in ev:
             a.record(stream)
             scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
@@ -444,7 +474,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    per_head = timed(head, args.steps, args.warmup)
+    per_head = timed(head, args.steps, args.warmup, on_start=clocks.mark)
     clock_rec = clocks.stop()
     per_other = timed(other, args.plain_steps, 1)
     per_plain = timed(plain, args.plain_steps, 1)
@@ -489,7 +519,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_head / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f32" if head_prec == P.MIXED_DS else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "photons_per_step_per_gpu": photons, "sources": n_src,
+            "config": {"workload": workload_name(args.photons, args.fine_n, args.coarse_n),
+                       "photons_per_step_per_gpu": photons, "sources": n_src,
                        "precision": descr[head_prec],
                        "l2": "inputs larger than L2 (gradient screens 2.8 GB, read in both precisions' forms)",
                        "setup_s": round(setup_s, 1)},
@@ -521,21 +552,32 @@ def main():
                               f"here) over the kernel's time (CUDA events around its launches on the stream); peak = "
                               + ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)"))}
         fp64_roof["frac"] = fp64_roof["achieved"] / peak64
-        # double-single kernel: the same optics operations as FP32 instructions of the double-single
-        # algorithms, against the FP32 instruction issue rate (FMA rate / 2)
-        ds_inst = sum(ops["optics"][k] * c for k, c in DS_INSTRUCTIONS.items())
+        # double-single kernel: bound by FP32 instruction issue.  achieved = the thread instructions the optics
+        # stage executes per launch (committed ncu capture, per sampled photon) over its time; peak = the SMs'
+        # issue rate (measured FP32 FMA rate / 2: one FMA a lane a cycle).  The oracle's FP64 operations over
+        # the same time give the emulated FP64 rate, against the native FP64 FMA rate.
         peak32 = fp32_rate / 2 if fp32_rate else None
+        t_opt = float(kt_ds[3]) / 1e3
+        inst = recorded_instructions(photons, "ds_optics_kernel")
+        ds_inst = sum(ops["optics"][k] * c for k, c in DS_INSTRUCTIONS.items())
+        emulated = fl_opt * photons / t_opt / 1e12
         ds_roof = {"bound": "alu", "kernel": "ds_optics_kernel", "kernel_ms": float(kt_ds[3]),
                    "entry_kernel_ms": float(kt_ds[2]),
-                   "achieved": ds_inst * photons / (float(kt_ds[3]) / 1e3) / 1e12,
+                   "achieved": inst / t_opt / 1e12 if inst else None,
                    "peak": peak32, "unit": "Tinst/s", "traffic": recorded_traffic(photons, "ds_optics_kernel"),
-                   "note": (f"the oracle's FP64 optics operations per sampled photon ({ops['optics']['add']:.0f} add, "
-                            f"{ops['optics']['mul']:.0f} mul, {ops['optics']['div']:.0f} div, "
-                            f"{ops['optics']['sqrt']:.0f} sqrt) costed as FP32 instructions of the double-single "
-                            f"primitives {DS_INSTRUCTIONS} = {ds_inst:.0f} per photon (surfaces and sensor, the "
-                            "optics stage's work), over the optics stage's time (CUDA events around its launches on "
-                            "the stream); peak = measured FP32 FMA rate / 2 (one instruction per FMA)")}
-        ds_roof["frac"] = ds_roof["achieved"] / peak32 if peak32 else None
+                   "instructions_per_photon": inst / photons if inst else None,
+                   "note": ("thread instructions of the optics stage per sampled photon (ncu smsp__inst_executed x "
+                            "threads per instruction on the committed 2e7-photon capture of the same kernel "
+                            "sources, profiles/ds_stages_three_mirror_2e7.md) x photons over the stage's time (CUDA "
+                            "events around its launches on the stream); peak = measured FP32 FMA rate / 2, the issue "
+                            "rate of one instruction a lane a cycle"),
+                   "emulated_fp64": {"tflops": emulated, "vs_measured_fp64_peak": emulated / peak64,
+                                     "note": (f"the oracle's FP64 optics operations per sampled photon ({fl_opt:.0f}: "
+                                              f"{ops['optics']['add']:.0f} add, {ops['optics']['mul']:.0f} mul, "
+                                              f"{ops['optics']['div']:.0f} div, {ops['optics']['sqrt']:.0f} sqrt; "
+                                              f"{ds_inst:.0f} FP32 instructions as double-single primitives "
+                                              f"{DS_INSTRUCTIONS}) over the optics stage's time")}}
+        ds_roof["frac"] = ds_roof["achieved"] / peak32 if (peak32 and inst) else None
         head_roof, other_roof = (ds_roof, fp64_roof) if head_prec == P.MIXED_DS else (fp64_roof, ds_roof)
         head_roof["algorithmic_gather_bytes"] = gather_bytes_per_launch(sc, ops, photons)
         head_roof["traffic_unit"] = "DRAM bytes per launch (ncu, committed summary)"
