@@ -265,14 +265,20 @@ __device__ __forceinline__ void unit_members(const DSource& s, uint32_t nb, uint
 
 // Accounting of photons the entry stage stops (the dynamic transmission test): record and loss counters.
 // None is detected there, so unlike consume() it carries no moment partials through the tile.
+// (only_reason > 0: every lane with v was lost for that reason, one ballot counts them)
 __device__ __forceinline__ void account_lost(const TraceParams& P, uint32_t flags, float lam, bool v, uint64_t rec_index,
-                                             int lane, unsigned long long* cnt) {
+                                             int lane, unsigned long long* cnt, int only_reason = 0) {
     if (v && P.records) {
         phosim_photon_record rec;
         rec.x = rec.y = rec.xc = rec.yc = 0.0;
         rec.lambda = (double)lam;
         rec.flags = flags; rec.pix = -1;
         P.records[rec_index] = rec;
+    }
+    if (only_reason > 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) cnt[1 + only_reason] += __popc(b);
+        return;
     }
     const uint32_t reason = v ? ((flags >> 8) & 0xffu) : 0u;
 #pragma unroll
@@ -340,13 +346,14 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                     const bool dropped = valid && !go_on;
                     const uint32_t fl = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
                     if (nb <= 1) {
-                        account_lost(P, fl, lam, dropped, s.rec_off + (u - s.first), lane, cnt);
+                        account_lost(P, fl, lam, dropped, s.rec_off + (u - s.first), lane, cnt, PHOSIM_LOST_COATING);
                     } else if (__any_sync(0xffffffffu, dropped)) {
                         uint64_t lo;
                         uint32_t nm;
                         unit_members(s, nb, u, lo, nm);
                         for (uint32_t m = 0; m < nb; ++m)
-                            account_lost(P, fl, lam, dropped && m < nm, s.rec_off + (lo + m - s.first), lane, cnt);
+                            account_lost(P, fl, lam, dropped && m < nm, s.rec_off + (lo + m - s.first), lane, cnt,
+                                         PHOSIM_LOST_COATING);
                     }
                 }
                 const unsigned gmask = __ballot_sync(0xffffffffu, go_on);
