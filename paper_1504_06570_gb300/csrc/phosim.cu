@@ -51,7 +51,8 @@ bool is_finite(double v) { return std::isfinite(v); }
 // and bundle-hit counts of the two-kernel double-single path
 constexpr int kStateCountWord = 1 + kNumCounters;
 constexpr int kHitCountWord = kStateCountWord + 1;
-constexpr int kCounterWords = kHitCountWord + 1;
+constexpr int kBatchWord = kHitCountWord + 1;      // next batch of states for the optics stage's blocks
+constexpr int kCounterWords = kBatchWord + 1;
 // photons per chunk of the two-kernel path: its state buffer holds one chunk (64 bytes a photon, 8.6 GB)
 constexpr uint64_t kStateChunk = 1ull << 27;
 
@@ -1010,6 +1011,7 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         S.n_state = sc->d_counters + kStateCountWord;
         S.hits = sc->d_hits;
         S.n_hits = sc->d_counters + kHitCountWord;
+        S.batch = sc->d_counters + kBatchWord;
         S.tile_begin = 0;
         S.tile_end = std::min(n_tiles, chunk_tiles);
         void* stage_args[2] = {&P, &S};
@@ -1031,7 +1033,7 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
                 S.tile_end = std::min(n_tiles, t0 + chunk_tiles);
                 if (t0 > 0) {
                     CU(cudaMemsetAsync(sc->d_counters, 0, sizeof(unsigned long long), st));
-                    CU(cudaMemsetAsync(sc->d_counters + kStateCountWord, 0, 2 * sizeof(unsigned long long), st));
+                    CU(cudaMemsetAsync(sc->d_counters + kStateCountWord, 0, 3 * sizeof(unsigned long long), st));
                 }
                 ls = timed(2, [&] { return launch_ds_entry(P, S, blocks, sc->threads, st); });
                 if (ls == PHOSIM_OK) ls = timed(3, [&] { return launch_ds_optics(P, S, blocks_optics, sc->threads, st); });

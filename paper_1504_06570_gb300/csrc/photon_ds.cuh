@@ -67,6 +67,7 @@ struct DSStage {
     unsigned long long* n_state;
     DSHit* hits;
     unsigned long long* n_hits;
+    unsigned long long* batch;    // the optics stage's blocks claim batches of states from this count
     uint64_t tile_begin, tile_end;
 };
 

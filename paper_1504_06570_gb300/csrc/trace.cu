@@ -243,10 +243,13 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
 #define PHOSIM_DS_ENTRY_MIN_BLOCKS 6
 #endif
 #ifndef PHOSIM_DS_OPTICS_MIN_BLOCKS
-#define PHOSIM_DS_OPTICS_MIN_BLOCKS 6
+#define PHOSIM_DS_OPTICS_MIN_BLOCKS 5
 #endif
 #ifndef PHOSIM_DS_LOCKSTEP
 #define PHOSIM_DS_LOCKSTEP 1
+#endif
+#ifndef PHOSIM_DS_DYNAMIC_BATCHES
+#define PHOSIM_DS_DYNAMIC_BATCHES 1
 #endif
 // threads per block of the optics stage (0: the schedule's block size)
 #ifndef PHOSIM_DS_OPTICS_THREADS
@@ -480,8 +483,19 @@ __global__ void __launch_bounds__(kOpticsMaxThreads, PHOSIM_DS_OPTICS_MIN_BLOCKS
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
 #if PHOSIM_DS_LOCKSTEP
     // a block's states at a time, all its warps meeting the surfaces together (a barrier after each), so
-    // that the SM's warps fetch the same stretch of code rather than as many stretches as warps
+    // that the SM's warps fetch the same stretch of code rather than as many stretches as warps; the
+    // blocks claim batches as they finish (a block is as slow as its slowest ray at every surface)
+#if PHOSIM_DS_DYNAMIC_BATCHES
+    __shared__ unsigned long long next_batch;
+    (void)stride;
+    for (;;) {
+        if (threadIdx.x == 0) next_batch = atomicAdd(S.batch, 1ull) * blockDim.x;
+        __syncthreads();
+        const unsigned long long b0 = next_batch;
+        if (b0 >= n) break;
+#else
     for (unsigned long long b0 = (unsigned long long)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
+#endif
         const unsigned long long b = b0 + (unsigned long long)warp * 32ull;
 #else
     for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (unsigned long long)warp * 32ull; b < n;
