@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
 #define PHOSIM_DS_ENTRY_MIN_BLOCKS 6
 #endif
 #ifndef PHOSIM_DS_OPTICS_MIN_BLOCKS
-#define PHOSIM_DS_OPTICS_MIN_BLOCKS 5
+#define PHOSIM_DS_OPTICS_MIN_BLOCKS 4
 #endif
 #ifndef PHOSIM_DS_LOCKSTEP
 #define PHOSIM_DS_LOCKSTEP 1
