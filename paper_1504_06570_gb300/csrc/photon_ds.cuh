@@ -407,16 +407,27 @@ __device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, floa
     return -1;
 }
 
-// i is the photon, or for a bundle the ray
-__device__ __forceinline__ int early_reject_surface_f(const TraceParams& P, const SourceS& s, int src, uint64_t i,
-                                                      float& lam) {
-    const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
-    const uint4 w0 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
+// The first stage of the dynamic transmission test (Sec. 3.2) of the double-single path, for every photon:
+// the wavelength, and the coated surfaces whose worst-case transmission there is 0 (lost whatever its draw)
+// or 1 (passed whatever its draw).  Returns the surface that certainly loses the photon, or -1: the photon
+// goes on to the full test (early_coating_reject_f, with its draws) at the start of its propagation, which
+// decides the photons a draw decides exactly as a one-stage test would, so fates, records and counts do not
+// change; the coating words (a generator call) are drawn only for the photons that get that far.
+// i is the photon, or for a bundle the ray.
+__device__ __forceinline__ int early_reject_certain_f(const TraceParams& P, const SourceS& s, int src, uint64_t i,
+                                                     float& lam) {
+    const uint4 w0 = philox_ds(make_uint4((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)src, 0u), P.k0, P.k1);
     lam = sample_wavelength_f(P, s, w0);
-    const uint4 w2 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 2u), P.k0, P.k1);
-    uint4 w3 = make_uint4(0u, 0u, 0u, 0u);
-    if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
-    return early_coating_reject_f(P, lam, w2, w3);
+    const int nk = (P.flags & kGhostFlag) ? min(1, P.n_coated) : P.n_coated;   // see early_coating_reject
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {
+        const int si = P.coated_surface[k];
+        const DCoating& C = P.coat[P.surf[si].coating];
+        const unsigned long long thr = __ldg(C.Tmax_thr + coat_lambda_bin(C, lam));
+        if (thr == 0ull) return si;               // no draw passes: lost here whatever the draw
+        if (thr < (1ull << 32)) return -1;        // a draw decides: the full test with the photon's words
+    }
+    return -1;
 }
 
 // A bundle's photon (member_draw in photon.cuh) with a single-precision spread

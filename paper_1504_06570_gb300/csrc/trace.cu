@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
                     int rej = -1;
                     if constexpr (DS) {
                         float lam = 0.f;
-                        if (valid) rej = early_reject_surface_f(P, ss, src, ray_of(ss.bundle, first + k), lam);
+                        if (valid) rej = early_reject_certain_f(P, ss, src, ray_of(ss.bundle, first + k), lam);
                         R.x = R.y = R.xc = R.yc = ds_f(0.f);
                         R.lam = lam;
                     } else {
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                     // stage 1: the early coating decision alone, for every photon of the unit
                     int rej = -1;
                     float lam = 0.f;
-                    if (valid) rej = early_reject_surface_f(P, ss, src, u, lam);
+                    if (valid) rej = early_reject_certain_f(P, ss, src, u, lam);
                     go_on = valid && rej < 0;
                     const bool dropped = valid && !go_on;
                     const uint32_t fl = dropped ? lost(PHOSIM_LOST_COATING, rej) : 0u;
