@@ -61,3 +61,32 @@ def test_full_size_sampled_parity(oracle_mod, scene, precision):
         assert np.array_equal(sample["pix"][okpix], ora["pix"][okpix])
     else:
         assert np.mean(err < 1e-2) > 0.999, np.percentile(err, [50, 99, 100])
+
+
+def test_double_single_chunks_compose():
+    """A double-single launch larger than one chunk of the state buffer (2^27 photons) runs the entry and optics
+    stages chunk after chunk, each with its own state and batch counts: 1.5e8 photons in one call must give
+    exactly the image and counts of two calls over complementary photon ranges of every source, each of which
+    fits one chunk, and every photon is counted once."""
+    sc = I.three_mirror_scene(n_total=150_000_000, fine_n=256, coarse_n=64)
+    counts = sc.sources.n_photons.astype(np.uint64)
+    n = int(counts.sum())
+    assert n > (1 << 27)
+    s = P.Scene(sc, P.MIXED_DS, early_reject=True)
+    d = sc.detector
+
+    def run(cnt, first=None):
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        s.trace(img, None, None, n_photons=cnt, first=first)
+        torch.cuda.synchronize()
+        return img.cpu().numpy().view(np.uint32), s.counters()
+
+    full, c_full = run(counts)
+    a = counts // np.uint64(2)
+    part1, c1 = run(a)
+    part2, c2 = run(counts - a, first=a)
+    s.close()
+    assert int(c_full[0]) == n and int(c_full[1]) + int(c_full[2:].sum()) == n
+    assert np.array_equal(c_full, c1 + c2)
+    assert np.array_equal(full, part1 + part2)
+    assert int(full.sum()) == int(c_full[1])
