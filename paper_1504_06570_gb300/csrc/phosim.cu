@@ -200,6 +200,7 @@ void build_surface_s(const phosim_surface& s, const DSurface& d, DSurfaceS& e) {
     e.c = ds_of(d.c);
     e.k1c2 = ds_of(d.k1c2);
     e.kc = ds_of(d.kc);
+    e.kmc = ds_of(d.kc - d.c);
     const double rn = (s.r_out > 0.0 && s.r_out < 1e6) ? s.r_out : 1000.0;
     for (int k = 0; k < 4; ++k) {
         const double ae = d.ae[k] * std::pow(rn, 2 * k + 4), ao = d.ao[k] * std::pow(rn, 2 * k + 3);

@@ -46,6 +46,7 @@ struct DSurface {
 // odd part   z = rho^3 sum_k ao[k] u^k;             (1/r) dz/dr = inv_rn2 rho sum_k aod[k] u^k
 struct DSurfaceS {
     ds c, k1c2, kc;
+    ds kmc;                                   // kc - c = kappa c: the quadric's d_z^2 term for a unit direction
     ds ae[4], aed[4], ao[4], aod[4];
     ds M[9], o[3];
     ds r_in2, r_out2;

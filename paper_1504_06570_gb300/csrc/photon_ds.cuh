@@ -283,7 +283,7 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
         // the conic's root in single precision; a ray whose discriminant is not clearly positive (grazing or
         // missing the conic) takes the double-single root below
         const float c = E.c.hi, kc = E.kc.hi;
-        const float Af = fmaf(kc * d[2].hi, d[2].hi, c * fmaf(d[0].hi, d[0].hi, d[1].hi * d[1].hi));
+        const float Af = fmaf(E.kmc.hi * d[2].hi, d[2].hi, c);
         const float bf = fmaf(kc * p[2].hi, d[2].hi, c * fmaf(p[0].hi, d[0].hi, p[1].hi * d[1].hi)) - d[2].hi;
         const float Cf = fmaf(kc * p[2].hi, p[2].hi, c * fmaf(p[0].hi, p[0].hi, p[1].hi * p[1].hi)) - 2.f * p[2].hi;
         const float disc = fmaf(bf, bf, -(Af * Cf));
@@ -309,7 +309,8 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
             }
         }
     }
-    const ds A = dfma(E.kc * d[2], d[2], E.c * dfma(d[0], d[0], d[1] * d[1]));
+    // the quadric's l^2 coefficient c (d_x^2 + d_y^2) + kc d_z^2, which for the unit direction is c + (kc - c) d_z^2
+    const ds A = dfma(E.kmc * d[2], d[2], E.c);
     const ds b = dfma(E.kc * p[2], d[2], E.c * dfma(p[0], d[0], p[1] * d[1])) - d[2];
     const ds C = dfma(E.kc * p[2], p[2], E.c * dfma(p[0], p[0], p[1] * p[1])) - p[2] * 2.f;
     const ds disc = dfma(b, b, -(A * C));

@@ -444,28 +444,32 @@ __device__ __forceinline__ void account_ds(const TraceParams& P, const PhotonOut
         // chief ray, sums to ~2^-47) leaves each segment's sums in its last lane, which adds them to the
         // source's double-precision moments: one set of atomics per segment, not per photon, and the FP64
         // pipe (a sixty-fourth of the FP32 rate on this GPU) only converts the partials.
-        ds mm[6] = {ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f)};
+        ds mm[5] = {ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f), ds_f(0.f)};
         if (det) {
             const float fx = (R.x - ds{s.ref_s[0], s.ref_s[1]}).hi, fy = (R.y - ds{s.ref_s[2], s.ref_s[3]}).hi;
-            mm[0] = ds_f(1.f); mm[1] = ds_f(fx); mm[2] = ds_f(fy);
-            mm[3] = two_prod(fx, fx); mm[4] = two_prod(fx, fy); mm[5] = two_prod(fy, fy);
+            mm[0] = ds_f(fx); mm[1] = ds_f(fy);
+            mm[2] = two_prod(fx, fx); mm[3] = two_prod(fx, fy); mm[4] = two_prod(fy, fy);
         }
         const int prev = __shfl_up_sync(0xffffffffu, src, 1);
         const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != src);
-        const int first = 31 - __clz(heads & (lane == 31 ? 0xffffffffu : (2u << lane) - 1u));
+        const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;
+        const int first = 31 - __clz(heads & upto);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
+            for (int q = 0; q < 5; ++q) {
                 const ds t = {__shfl_up_sync(0xffffffffu, mm[q].hi, d), __shfl_up_sync(0xffffffffu, mm[q].lo, d)};
                 if (lane - d >= first) mm[q] = mm[q] + t;
             }
         }
         const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
-        if (last && mm[0].hi > 0.f) {
+        // the segment's detected photons, counted from the ballot
+        const unsigned n_det = __popc(dmask & upto & ~((1u << first) - 1u));
+        if (last && n_det > 0) {
             double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
+            atomicAdd(M, (double)n_det);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) atomicAdd(M + q, ds_value(mm[q]));
+            for (int q = 0; q < 5; ++q) atomicAdd(M + 1 + q, ds_value(mm[q]));
         }
     }
 }
