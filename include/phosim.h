@@ -258,7 +258,9 @@ phosim_status phosim_grad(phosim_scene* scene, const phosim_source* sources, int
                           const int32_t* param_field, int n_params, double* grad, double* moments_out,
                           void* stream);
 
-/* Launch shape of the trace kernel: threads per block and photons per warp tile (0 = keep current). */
+/* Launch shape of the trace kernel: threads per block and photons per warp tile (0 = keep current).  In the
+   two-kernel double-single path it applies to the entry and bundle stages; the optics stage keeps blocks of
+   256 threads, whose warps take the surfaces together. */
 phosim_status phosim_set_schedule(phosim_scene* scene, int threads_per_block, int tile_photons);
 
 /* Autotuner of the trace launch: traces a sample of the workload (about sample_photons photons, spread
