@@ -531,7 +531,9 @@ def main():
             "detected_fraction": float(counters[1] / max(1, counters[0])),
             "e2e": {"value": photons * world / e2e_s, "unit": "photons/s", "h2d_bytes_per_step": img_bytes + src_bytes,
                     "d2h_bytes_per_step": img_bytes},
-            "gpu_launches": (3 if head_prec == P.MIXED_DS else 2) * args.steps, "clocks": clock_rec,
+            # per step: chief rays, then the entry and optics stages and the moment-stripe sum (double-single)
+            # or the one trace kernel
+            "gpu_launches": (4 if head_prec == P.MIXED_DS else 2) * args.steps, "clocks": clock_rec,
             "fma_peaks_measured_tflops": {"fp64": fp64_rate, "fp32": fp32_rate}}
 
     if not args.no_oracle:

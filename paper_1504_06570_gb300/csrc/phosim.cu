@@ -322,7 +322,10 @@ struct KernelLaunch {
 // replayed on the caller's stream with this call's kernel parameters and launch shapes.
 phosim_status launch_graph(phosim_scene* sc, int slot, const KernelLaunch* L, int n, cudaStream_t st) {
     TraceGraph& g = sc->graphs[slot];
-    if (g.exec && g.n != n) destroy_graph(g);
+    if (n > kMaxGraphNodes) return PHOSIM_ERR_LIMIT;
+    bool same = g.exec && g.n == n;
+    for (int i = 0; same && i < n; ++i) same = g.func[i] == L[i].func;
+    if (g.exec && !same) destroy_graph(g);
     if (!g.exec) {
         if (!sc->capture_stream) CU(cudaStreamCreateWithFlags(&sc->capture_stream, cudaStreamNonBlocking));
         CU(cudaStreamBeginCapture(sc->capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -338,6 +341,7 @@ phosim_status launch_graph(phosim_scene* sc, int slot, const KernelLaunch* L, in
         }
         g.graph = graph;
         g.n = n;
+        for (int i = 0; i < n; ++i) g.func[i] = L[i].func;
         if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
         size_t cnt = 0;
         cudaGraphGetNodes(g.graph, nullptr, &cnt);
@@ -475,6 +479,7 @@ void phosim_destroy_scene(phosim_scene* sc) {
     cudaFree(sc->d_stage);
     cudaFree(sc->d_state);
     cudaFree(sc->d_hits);
+    cudaFree(sc->d_mom_stripes);
     cudaFree(sc->d_grad_scratch);
     cudaFree(sc->d_mom_scratch);
     for (TraceGraph& g : sc->graphs) destroy_graph(g);
@@ -965,7 +970,22 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         }
     }
     CU(cudaMemsetAsync(sc->d_counters, 0, kCounterWords * sizeof(unsigned long long), st));
+    // the two-kernel path's striped moment accumulators, added into the caller's sums after the last stage
+    const bool striped = staged && moments && n_src > 0;
+    const size_t stripe_stride = (size_t)n_src * PHOSIM_MOMENT_WORDS;
+    if (striped) {
+        const size_t need = (size_t)kMomStripes * stripe_stride;
+        if (sc->cap_mom_stripes < need) {
+            cudaFree(sc->d_mom_stripes);
+            sc->d_mom_stripes = nullptr; sc->cap_mom_stripes = 0;
+            CU(cudaMalloc(&sc->d_mom_stripes, need * sizeof(double)));
+            sc->cap_mom_stripes = need;
+        }
+        CU(cudaMemsetAsync(sc->d_mom_stripes, 0, need * sizeof(double), st));
+    }
     TraceParams P = sc->base;
+    P.mom_stripes = striped ? sc->d_mom_stripes : nullptr;
+    P.mom_stripe_stride = striped ? stripe_stride : 0;
     P.sources = sc->d_src;
     P.tile_prefix = sc->d_prefix;
     P.n_src = n_src;
@@ -1018,13 +1038,19 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         void* stage_args[2] = {&P, &S};
         const dim3 block((unsigned)sc->threads);
         const bool bundles = bundled_units > 0;
+        void* reduce_args[1] = {&P};
+        const KernelLaunch reduce = {moment_stripes_kernel_ptr(), dim3((unsigned)((n_src * 6 + 255) / 256)), dim3(256),
+                                     reduce_args};
         if (use_graph && chunk_tiles >= n_tiles) {
-            const KernelLaunch L[4] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
-                                       {ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, stage_args},
-                                       {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics),
-                                        dim3((unsigned)ds_optics_threads(sc->threads)), stage_args},
-                                       {ds_members_kernel_ptr(), dim3((unsigned)blocks_members), block, stage_args}};
-            phosim_status gs = launch_graph(sc, mode, L, bundles ? 4 : 3, st);
+            KernelLaunch L[5] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
+                                 {ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, stage_args},
+                                 {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics),
+                                  dim3((unsigned)ds_optics_threads(sc->threads)), stage_args},
+                                 {ds_members_kernel_ptr(), dim3((unsigned)blocks_members), block, stage_args},
+                                 reduce};
+            int n_nodes = bundles ? 4 : 3;
+            if (striped) L[n_nodes++] = reduce;
+            phosim_status gs = launch_graph(sc, mode, L, n_nodes, st);
             if (gs != PHOSIM_OK) return gs;
         } else {
             phosim_status ls = timed(0, [&] { return launch_chief_rays(P, sc->d_src, n_src, moments, st); });
@@ -1040,6 +1066,10 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
                 if (ls == PHOSIM_OK) ls = timed(3, [&] { return launch_ds_optics(P, S, blocks_optics, sc->threads, st); });
                 if (ls == PHOSIM_OK && bundles)
                     ls = timed(4, [&] { return launch_ds_members(P, S, blocks_members, sc->threads, st); });
+                if (ls != PHOSIM_OK) return ls;
+            }
+            if (striped) {
+                ls = timed(3, [&] { return launch_moment_stripes(P, st); });
                 if (ls != PHOSIM_OK) return ls;
             }
         }

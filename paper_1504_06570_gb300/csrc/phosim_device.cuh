@@ -158,7 +158,13 @@ struct TraceParams {
     uint32_t* image;
     double* moments;
     phosim_photon_record* records;
+    // the two-kernel double-single path's moment accumulators: kMomStripes copies of the per-source sums
+    // (PHOSIM_MOMENT_WORDS a source, mom_stripe_stride doubles a copy), a block adding to copy blockIdx %
+    // kMomStripes so that a bright source's atomics spread over several cache lines; null: add to moments
+    double* mom_stripes;
+    unsigned long long mom_stripe_stride;
 };
+constexpr int kMomStripes = 16;
 
 // ------------------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two 32x32 multiplications per round.

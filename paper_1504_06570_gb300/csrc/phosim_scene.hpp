@@ -9,11 +9,12 @@
 // One captured [chief rays, trace] launch pair, replayed with updated kernel parameters.
 // One captured sequence of kernel launches ([chief rays, trace] or [chief rays, entry, optics(, bundles)]), replayed
 // with each call's kernel parameters and launch shapes.
-constexpr int kMaxGraphNodes = 4;
+constexpr int kMaxGraphNodes = 6;
 struct TraceGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int n = 0;
+    const void* func[kMaxGraphNodes] = {};      // the kernels the graph was captured with, in order
     cudaGraphNode_t node[kMaxGraphNodes] = {};
 };
 
@@ -46,6 +47,8 @@ struct phosim_scene {
     size_t cap_state = 0;
     phosim::DSHit* d_hits = nullptr;            // detector hits of its bundle rays
     size_t cap_hits = 0;
+    double* d_mom_stripes = nullptr;            // its striped per-source moment accumulators
+    size_t cap_mom_stripes = 0;
     size_t cap_stage = 0;
     cudaStream_t last_stream = nullptr;
     // adjoint: Zernike monomial table (owned with the optics) and per-call scratch
@@ -80,6 +83,8 @@ const void* ds_members_kernel_ptr();
 cudaError_t ds_stage_occupancy(int threads, int* entry_per_sm, int* optics_per_sm, int* members_per_sm);
 const void* ds_entry_kernel_ptr();
 const void* ds_optics_kernel_ptr();
+const void* moment_stripes_kernel_ptr();
+cudaError_t launch_moment_stripes(const TraceParams& P, cudaStream_t st);
 int ds_optics_threads(int threads);      // the optics stage's block size for a schedule's block size
 void free_all(std::vector<void*>& v);
 }  // namespace phosim

@@ -468,7 +468,8 @@ __device__ __forceinline__ void account_ds(const TraceParams& P, const PhotonOut
         // the segment's detected photons, counted from the ballot
         const unsigned n_det = __popc(dmask & upto & ~((1u << first) - 1u));
         if (last && n_det > 0) {
-            double* M = P.moments + (size_t)src * PHOSIM_MOMENT_WORDS;
+            double* M = (P.mom_stripes ? P.mom_stripes + (size_t)(blockIdx.x % kMomStripes) * P.mom_stripe_stride
+                                       : P.moments) + (size_t)src * PHOSIM_MOMENT_WORDS;
             atomicAdd(M, (double)n_det);
 #pragma unroll
             for (int q = 0; q < 5; ++q) atomicAdd(M + 1 + q, ds_value(mm[q]));
@@ -610,6 +611,18 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_MEMBERS_MIN_BLOCKS) ds_members_
     if (lane < kNumCounters && cnt[lane]) atomicAdd(P.counters + lane, cnt[lane]);
 }
 
+// The striped moment accumulators of the two-kernel path added into the caller's moment sums (one thread a
+// source and word)
+__global__ void moment_stripes_kernel(const __grid_constant__ TraceParams P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n_src * 6) return;
+    const size_t w = (size_t)(i / 6) * PHOSIM_MOMENT_WORDS + (size_t)(i % 6);
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMomStripes; ++k) sum += P.mom_stripes[(size_t)k * P.mom_stripe_stride + w];
+    P.moments[w] += sum;
+}
+
 // Chief ray of each source (pupil centre, source centre direction, lambda_ref, no apertures): the
 // reference point of the moment sums.
 __global__ void chief_ray_kernel(const __grid_constant__ TraceParams P, DSource* sources, int n_src, double* moments) {
@@ -654,6 +667,13 @@ const void* trace_kernel_ptr(int mode) {
 const void* chief_kernel_ptr() { return (const void*)chief_ray_kernel; }
 const void* ds_entry_kernel_ptr() { return (const void*)ds_entry_kernel; }
 const void* ds_optics_kernel_ptr() { return (const void*)ds_optics_kernel; }
+const void* moment_stripes_kernel_ptr() { return (const void*)moment_stripes_kernel; }
+
+cudaError_t launch_moment_stripes(const TraceParams& P, cudaStream_t st) {
+    if (P.n_src <= 0 || !P.moments || !P.mom_stripes) return cudaSuccess;
+    moment_stripes_kernel<<<(P.n_src * 6 + 255) / 256, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ds_entry(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st) {
     ds_entry_kernel<<<blocks, threads, 0, st>>>(P, S);
