@@ -207,6 +207,41 @@ def test_graph_replay_matches_direct_launches(precision):
     gr.close()
 
 
+def test_graph_follows_the_kernel_list():
+    """In the double-single path the captured graph holds 3 to 5 kernels (chief rays, entry and optics stages,
+    the bundle stage when a source is bundled, the moment-stripe sum when moment sums are asked for); a scene
+    that alternates between those lists in graph mode re-captures and gives, every time, the images, records and
+    moment sums of the same calls launched directly."""
+    import torch
+    counts = np.array([900, 2500, 60], np.uint64)
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=31))
+    bundled = G.test_system_scene(sources=G.mixed_sources(counts, seed=31))
+    bundled.sources.bundle = np.array([1, 4, 1], np.int32)
+    bundled.sources.bundle_sigma = np.array([0.0, 0.003, 0.0])
+    ref = P.Scene(sc, P.MIXED_DS, early_reject=True)
+    gr = P.Scene(sc, P.MIXED_DS, early_reject=True, graph=True)
+    d = sc.detector
+    n = int(counts.sum())
+    for sources, with_moments in ((sc.sources, True), (sc.sources, False), (bundled.sources, True),
+                                  (bundled.sources, False), (sc.sources, True)):
+        outs = []
+        for s in (ref, gr):
+            s.set_sources(sources)
+            img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+            rec = torch.zeros(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+            mom = torch.zeros((len(counts), P.MOMENT_WORDS), dtype=torch.float64, device="cuda") if with_moments else None
+            s.trace(img, rec, mom)
+            torch.cuda.synchronize()
+            outs.append((img.cpu().numpy(), P.records_to_numpy(rec), None if mom is None else mom.cpu().numpy()))
+        assert np.array_equal(outs[0][0], outs[1][0])
+        assert np.array_equal(outs[0][1], outs[1][1])
+        if with_moments:
+            np.testing.assert_allclose(outs[1][2], outs[0][2], rtol=1e-12, atol=1e-15)
+            assert outs[1][2][:, 0].sum() == int((outs[1][1]["flags"] & 1).sum())
+    ref.close()
+    gr.close()
+
+
 @pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED, P.MIXED_DS])
 def test_sensor_extensions(oracle_mod, precision):
     """Dead layer, back-side reflection and a depth-dependent diffusion sigma from the field model."""
