@@ -27,9 +27,10 @@ def build(force=False):
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", LIB + ".tmp", SRC]
+    tmp = f"{LIB}.{os.getpid()}.tmp"     # concurrent builders each write their own file; the replace is atomic
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", tmp, SRC]
     subprocess.check_call(cmd)
-    os.replace(LIB + ".tmp", LIB)
+    os.replace(tmp, LIB)
     return LIB
 
 

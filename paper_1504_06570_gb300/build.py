@@ -49,6 +49,20 @@ def build(force=False, verbose=False, ptxas_info=False):
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    # one build at a time (the ranks of a multi-GPU run all call this): the first compiles, the others find
+    # the library up to date once they hold the lock
+    import fcntl
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB
+            return _build_locked(verbose, ptxas_info)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, ptxas_info):
     objs = []
 
     def compile_one(src):
