@@ -191,7 +191,11 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 //            spread a, spread b, conversion, diffusion a; diffusion b, back-side reflection
 //   blocks 7, 8, ... (ghosts): the coating decisions after the first reflection, one word each, in order
 __device__ __forceinline__ double u64of(uint32_t w) { return ((double)w + 0.5) * 2.3283064365386963e-10; }
-__device__ __forceinline__ float u32of(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+// the uniform (w + 1/2) 2^-32 of a word in single precision: the whole word converts (exactly below 2^24), so
+// the small values that the -log u of the conversion depth and of Box-Muller reach keep 24 significant bits
+__device__ __forceinline__ float u32of(uint32_t w) {
+    return __fadd_rn(__fmul_rn((float)w, 2.3283064365386963e-10f), 1.1641532182693481e-10f);
+}
 
 // ------------------------------------------------------------------------------------------------------
 // surface shape (Sec. 2.4.1)
