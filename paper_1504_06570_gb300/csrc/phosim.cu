@@ -574,6 +574,7 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
         C.lam0 = coats[k].lam0; C.inv_dlam = 1.0 / coats[k].dlam;
         C.th0 = coats[k].theta0; C.inv_dth = 1.0 / coats[k].dtheta;
         C.lam0f = (float)C.lam0; C.inv_dlamf = (float)C.inv_dlam; C.th0f = (float)C.th0; C.inv_dthf = (float)C.inv_dth;
+        C.lam0_s = ds_of(C.lam0); C.inv_dlam_s = ds_of(C.inv_dlam);
         C.T_thr = dthr;
         C.Tmax_thr = dmax_thr;
         C.TR = dtr;
@@ -716,6 +717,8 @@ phosim_status phosim_load_seds(phosim_scene* sc, const double* flux, int n_sed, 
     sc->base.sed_dlam = dlam;
     sc->base.sed_lam0f = (float)lam0;
     sc->base.sed_dlamf = (float)dlam;
+    sc->base.sed_lam0_s = ds_of(lam0);
+    sc->base.sed_dlam_s = ds_of(dlam);
     sc->n_sed = n_sed;
     sc->seds_loaded = true;
     return PHOSIM_OK;

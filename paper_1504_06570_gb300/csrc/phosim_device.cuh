@@ -64,6 +64,7 @@ struct DMaterial {
 struct DCoating {
     double lam0, inv_dlam, th0, inv_dth;
     float lam0f, inv_dlamf, th0f, inv_dthf;
+    ds lam0_s, inv_dlam_s;                    // the wavelength grid as double-single pairs (its bins)
     int nl, nt, pad0, pad1;
     const double* T;                          // nl x nt
     const double* Tmax;                       // nl: the largest transmission over angles at each wavelength
@@ -139,6 +140,7 @@ struct TraceParams {
     // spectra, shapes
     int n_bins, sersic_K;
     double sed_lam0, sed_dlam;
+    ds sed_lam0_s, sed_dlam_s;
     const unsigned long long* thr;            // n_sed x (n_bins - 1) integer thresholds on the bin draw
     const int* sed_guide;                     // n_sed x (kSedGuide + 1): first threshold above j 2^24
     const double* sersic;

@@ -38,7 +38,9 @@ struct PhotonOutS {
 // A photon's state on the entrance plane of the telescope, passed from the entry stage to the optics stage
 // of the two-kernel double-single path (64 bytes)
 struct __align__(16) DSState {
-    ds x, y, z, nx, ny, nz;
+    ds x, y;                      // on the entrance plane (z is the plane's)
+    float lam_lo, pad;            // the low word of the double-single wavelength (lam + lam_lo)
+    ds nx, ny, nz;
     float lam;
     int src;
     unsigned long long idx;       // photon index within its source's stream
@@ -75,6 +77,7 @@ struct DSStage {
 struct SourceS {
     ds xi, eta, t0, t_exp, ref_x, ref_y;
     float zfac, a, b, cpa, spa, bsig;
+    ds zfac_s;
     int kind, sed, table;
     uint32_t bundle;
 };
@@ -83,7 +86,7 @@ __device__ __forceinline__ SourceS source_s(const DSource& s) {
     SourceS r;
     r.xi = ds_of(s.xi); r.eta = ds_of(s.eta); r.t0 = ds_of(s.t0); r.t_exp = ds_of(s.t_exp);
     r.ref_x = ds_of(s.ref_x); r.ref_y = ds_of(s.ref_y);
-    r.zfac = (float)s.zfac; r.a = (float)s.a; r.b = (float)s.b; r.cpa = (float)s.cpa; r.spa = (float)s.spa;
+    r.zfac = (float)s.zfac; r.zfac_s = ds_of(s.zfac); r.a = (float)s.a; r.b = (float)s.b; r.cpa = (float)s.cpa; r.spa = (float)s.spa;
     r.kind = s.kind; r.sed = s.sed; r.table = s.table;
     r.bundle = s.bundle; r.bsig = (float)s.bsig;
     return r;
@@ -384,19 +387,25 @@ __device__ __forceinline__ void from_surface_ds(const DSurfaceS& E, int flags, c
 }
 
 // the coating accept-reject: the draw (w + 1/2) 2^-32 < T exactly when w < ceil(T 2^32 - 1/2)
-__device__ __forceinline__ int coat_lambda_bin(const DCoating& C, float lam) {
-    int il = (int)floorf((lam - C.lam0f) * C.inv_dlamf);
+// The coating's wavelength bin of a photon, from its double-single wavelength: the FP64 paths' bin except within
+// ~1e-14 of an edge (a single-precision wavelength would move about one photon in 5e6 across a band edge of
+// the filter, and with it the photon's fate and its star's moments)
+__device__ __forceinline__ int coat_lambda_bin(const DCoating& C, ds lam) {
+    const int il = (int)ds_floor((lam - C.lam0_s) * C.inv_dlam_s);
     return il < 0 ? 0 : (il > C.nl - 1 ? C.nl - 1 : il);
 }
-
-__device__ __forceinline__ float sample_wavelength_f(const TraceParams& P, const SourceS& s, const uint4& w0) {
-    const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.sed_guide + (size_t)s.sed * (kSedGuide + 1), w0.z);
-    const float lo = fmaf((float)bin, P.sed_dlamf, P.sed_lam0f);
-    return fmaf(u32of(w0.w), P.sed_dlamf, lo) * s.zfac;
+// The wavelength of a photon (Sec. 2.2): (bin + u) dlam + lam0, redshifted, with the bin from the SED's
+// thresholds and u = (w + 1/2) 2^-32 exact from word w of block 0, as a double-single pair (the FP64 paths'
+// value to ~1e-14); its high word is the single-precision wavelength of the FP32 steps.
+__device__ __forceinline__ int sed_bin_of(const TraceParams& P, int sed, const uint4& w0) {
+    return sed_bin(P.thr + (size_t)sed * (P.n_bins - 1), P.sed_guide + (size_t)sed * (kSedGuide + 1), w0.z);
 }
-
+__device__ __forceinline__ ds sample_wavelength_ds(const TraceParams& P, const SourceS& s, const uint4& w0) {
+    const ds lo = P.sed_lam0_s + P.sed_dlam_s * (float)sed_bin_of(P, s.sed, w0);
+    return dfma(ds_uniform(w0.w), P.sed_dlam_s, lo) * s.zfac_s;
+}
 // dynamic transmission (Sec. 3.2) on the single-precision wavelength, as early_coating_reject
-__device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, float lam, const uint4& w2, const uint4& w3) {
+__device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, ds lam, const uint4& w2, const uint4& w3) {
     const int nk = (P.flags & kGhostFlag) ? min(1, P.n_coated) : P.n_coated;   // see early_coating_reject
 #pragma unroll 1
     for (int k = 0; k < nk; ++k) {
@@ -418,13 +427,21 @@ __device__ __forceinline__ int early_coating_reject_f(const TraceParams& P, floa
 __device__ __forceinline__ int early_reject_certain_f(const TraceParams& P, const SourceS& s, int src, uint64_t i,
                                                      float& lam) {
     const uint4 w0 = philox_ds(make_uint4((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)src, 0u), P.k0, P.k1);
-    lam = sample_wavelength_f(P, s, w0);
+    // the wavelength in single precision, within ~2.5e-7 of the double-single value (relative): a bin taken
+    // from it is the exact bin unless it lies that close to a bin edge, and such a photon is left to the full
+    // test, which bins the double-single wavelength
+    const float bin = (float)sed_bin_of(P, s.sed, w0);
+    lam = fmaf(u32of(w0.w), P.sed_dlamf, fmaf(bin, P.sed_dlamf, P.sed_lam0f)) * s.zfac;
     const int nk = (P.flags & kGhostFlag) ? min(1, P.n_coated) : P.n_coated;   // see early_coating_reject
 #pragma unroll 1
     for (int k = 0; k < nk; ++k) {
         const int si = P.coated_surface[k];
         const DCoating& C = P.coat[P.surf[si].coating];
-        const unsigned long long thr = __ldg(C.Tmax_thr + coat_lambda_bin(C, lam));
+        const float t = (lam - C.lam0f) * C.inv_dlamf, f = floorf(t), margin = 1e-6f * fabsf(lam) * C.inv_dlamf + 1e-6f;
+        if (!(t - f > margin && t - f < 1.f - margin)) return -1;
+        int il = (int)f;
+        il = il < 0 ? 0 : (il > C.nl - 1 ? C.nl - 1 : il);
+        const unsigned long long thr = __ldg(C.Tmax_thr + il);
         if (thr == 0ull) return si;               // no draw passes: lost here whatever the draw
         if (thr < (1ull << 32)) return -1;        // a draw decides: the full test with the photon's words
     }
@@ -568,7 +585,7 @@ __device__ __forceinline__ void walk_start(OpticsWalk& W, const ds X[3], const d
 }
 
 // The next surface of the walk; false once the ray has left it (R.flags then says lost, detected or handed off).
-__device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk& W, float lam, int src, uint64_t ray,
+__device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk& W, ds lam, int src, uint64_t ray,
                                                 PhotonOutS& R, const MemberDrawS* mb = nullptr,
                                                 DetectorHit* hand_off = nullptr) {
     const int si = W.si;
@@ -601,7 +618,7 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
             R.flags = kHandedOff;
             return false;
         }
-        detect_ds(P, H, lam, src, ray, R, mb);
+        detect_ds(P, H, lam.hi, src, ray, R, mb);
         return false;
     }
     // clear aperture
@@ -650,14 +667,14 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
             const DMaterial& m = P.mat[mi];
             if (m.kind == PHOSIM_SELLMEIER) {
                 if (W.glass_mat != mi) {
-                    W.glass_n = sellmeier_ds(m, lam);
+                    W.glass_n = sellmeier_ds(m, lam.hi);
                     W.glass_inv = ds_rcp(W.glass_n);
                     W.glass_mat = mi;
                 }
                 n_next = W.glass_n;
                 inv_next = W.glass_inv;
             } else if (m.kind == PHOSIM_SILICON) {
-                n_next = ds_f(silicon_index_f(lam));
+                n_next = ds_f(silicon_index_f(lam.hi));
                 inv_next = ds_rcp(n_next);
             }
         }
@@ -670,7 +687,7 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
 }
 
 // the whole walk of one ray
-__device__ __forceinline__ void optics_ds(const TraceParams& P, const ds X[3], const ds D[3], float lam, int src,
+__device__ __forceinline__ void optics_ds(const TraceParams& P, const ds X[3], const ds D[3], ds lam, int src,
                                           uint64_t ray, PhotonOutS& R, const MemberDrawS* mb = nullptr,
                                           DetectorHit* hand_off = nullptr) {
     OpticsWalk W;
@@ -707,7 +724,7 @@ __device__ __forceinline__ void screen_gradient_ds(const DScale& S, ds sx, ds sy
 // dynamic transmission test drops it (R.flags says where); otherwise X, D are its position and direction on
 // the entrance plane.
 __device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
-                                                PhotonOutS& R, ds X[3], ds D[3], float& lam_out, uint4& w1,
+                                                PhotonOutS& R, ds X[3], ds D[3], float& lam_out, float& lam_lo, uint4& w1,
                                                 uint4& w2, uint4& w3, uint4& w4) {
     const uint32_t clo = (uint32_t)i, chi = (uint32_t)(i >> 32);
     const uint4 w0 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 0u), P.k0, P.k1);
@@ -716,7 +733,9 @@ __device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const Sour
     R.x = R.y = R.xc = R.yc = ds_f(0.f);
     // time stamp, wavelength (Sec. 2.2)
     const ds t = dfma(s.t_exp, ds_uniform(w1.x), s.t0);
-    const float lam = sample_wavelength_f(P, s, w0);
+    const ds lamd = sample_wavelength_ds(P, s, w0);
+    const float lam = lamd.hi;
+    lam_lo = lamd.lo;           // stored at once: the caller may keep it out of the registers of the layer loop
     R.lam = lam;
     // direction with the paraxial shape offset (Sec. 2.2, 2.2.1)
     ds nx = s.xi, ny = s.eta;
@@ -741,7 +760,7 @@ __device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const Sour
     w3 = make_uint4(0u, 0u, 0u, 0u);
     if (P.n_coated > 2) w3 = philox_ds(make_uint4(clo, chi, (uint32_t)src, 3u), P.k0, P.k1);
     if (P.flags & PHOSIM_EARLY_REJECT) {
-        const int si = early_coating_reject_f(P, lam, w2, w3);
+        const int si = early_coating_reject_f(P, lamd, w2, w3);
         if (si >= 0) { R.flags = lost(PHOSIM_LOST_COATING, si); return false; }
     }
     // pupil point on the annulus, on the nominal first surface, moved back to the top of the atmosphere
@@ -807,14 +826,14 @@ __device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const Sour
 __device__ __forceinline__ void trace_photon_ds(const TraceParams& P, const SourceS& s, int src, uint64_t i,
                                                 PhotonOutS& R) {
     ds X[3], D[3];
-    float lam;
+    float lam, lam_lo;
     uint4 w1, w2, w3, w4;
     const uint64_t ray = ray_of(s.bundle, i);
-    if (!photon_entry_ds(P, s, src, ray, R, X, D, lam, w1, w2, w3, w4)) return;
+    if (!photon_entry_ds(P, s, src, ray, R, X, D, lam, lam_lo, w1, w2, w3, w4)) return;
     MemberDrawS mb;
     const bool bundled = s.bundle > 1;
     if (bundled) mb = member_draw_s(P, s.bsig, src, i);
-    optics_ds(P, X, D, lam, src, ray, R, bundled ? &mb : nullptr);
+    optics_ds(P, X, D, ds{lam, lam_lo}, src, ray, R, bundled ? &mb : nullptr);
 }
 
 }  // namespace phosim

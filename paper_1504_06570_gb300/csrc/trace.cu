@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
     __shared__ uint32_t queue_mem[kWarpsPerBlock][64];
     __shared__ unsigned long long cnt_mem[kWarpsPerBlock][kNumCounters];
     __shared__ SourceS src_mem[kWarpsPerBlock];
+    __shared__ float lam_lo_mem[kWarpsPerBlock * 32];   // a photon's wavelength low word, out of the registers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* queue = queue_mem[warp];
     unsigned long long* cnt = cnt_mem[warp];
@@ -378,9 +379,10 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                 Q.flags = 0; Q.pix = -1;
                 ds X[3], D[3];
                 float lam = 0.f;
+                float& lam_lo = lam_lo_mem[threadIdx.x];
                 uint4 w1, w2, w3, w4;
                 const uint64_t u = ufirst + kk;
-                const bool go = v && photon_entry_ds(P, ss, src, u, Q, X, D, lam, w1, w2, w3, w4);
+                const bool go = v && photon_entry_ds(P, ss, src, u, Q, X, D, lam, lam_lo, w1, w2, w3, w4);
                 // survivors append their state, a warp at a time
                 const unsigned amask = __ballot_sync(0xffffffffu, go);
                 unsigned long long slot = 0;
@@ -388,7 +390,8 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
                 slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(amask & lanes_below);
                 if (go) {
                     DSState e;
-                    e.x = X[0]; e.y = X[1]; e.z = X[2];
+                    e.x = X[0]; e.y = X[1];                 // X[2] is the entrance plane's z
+                    e.lam_lo = lam_lo; e.pad = 0.f;
                     e.nx = D[0]; e.ny = D[1]; e.nz = D[2];
                     e.lam = lam;
                     e.src = src;
@@ -518,19 +521,21 @@ __global__ void __launch_bounds__(kOpticsMaxThreads, PHOSIM_DS_OPTICS_MIN_BLOCKS
         DetectorHit H;
 #if PHOSIM_DS_LOCKSTEP
         OpticsWalk W;
+        ds lam = ds_f(0.f);
         bool go = false, bundled = false;
         if (v) {
             const DSState st = S.state[e];
             src = st.src;
             u = st.idx;
             R.lam = st.lam;
+            lam = ds{st.lam, st.lam_lo};
             bundled = P.sources[src].bundle > 1;
-            const ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
+            const ds X[3] = {st.x, st.y, P.z_ent_s}, D[3] = {st.nx, st.ny, st.nz};
             walk_start(W, X, D);
             go = true;
         }
         while (__syncthreads_or(go)) {
-            if (go) go = surface_step_ds(P, W, R.lam, src, u, R, nullptr, bundled ? &H : nullptr);
+            if (go) go = surface_step_ds(P, W, lam, src, u, R, nullptr, bundled ? &H : nullptr);
         }
 #else
         if (v) {
@@ -539,8 +544,8 @@ __global__ void __launch_bounds__(kOpticsMaxThreads, PHOSIM_DS_OPTICS_MIN_BLOCKS
             u = st.idx;
             R.lam = st.lam;
             const bool bundled = P.sources[src].bundle > 1;
-            const ds X[3] = {st.x, st.y, st.z}, D[3] = {st.nx, st.ny, st.nz};
-            optics_ds(P, X, D, st.lam, src, u, R, nullptr, bundled ? &H : nullptr);
+            const ds X[3] = {st.x, st.y, P.z_ent_s}, D[3] = {st.nx, st.ny, st.nz};
+            optics_ds(P, X, D, ds{st.lam, st.lam_lo}, src, u, R, nullptr, bundled ? &H : nullptr);
         }
 #endif
         // a bundle's ray that reached the detector surface hands its hit over to the bundle stage
