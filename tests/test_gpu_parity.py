@@ -60,6 +60,26 @@ def test_tiny_paraboloid_mixed(oracle_mod, precision):
     G.compare_moments(gpu["moments"], G.oracle_moments(ora, 1), rel=1e-3)
 
 
+def test_double_single_fates_and_moments_at_fp64_level(oracle_mod):
+    """The double-single path's coating decisions use its double-single wavelength (the FP64 paths' bins), so
+    with the atmosphere, the sensor, every source kind and the dynamic transmission test on it gives every photon
+    the oracle's fate except at flagged accept boundaries, and its moments agree with the oracle far inside the
+    mixed gate: centroids within 1e-5 of the PSF size and second moments within 1e-5 relative (the remaining
+    differences are the single-precision deflections, diffusion draws and wavelength of the FP32 steps)."""
+    counts = [0, 1, 31, 33, 1000, 4097, 20000, 7, 2500]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts), hf=True)
+    gpu = G.run_gpu(sc, P.MIXED_DS)
+    ora = G.oracle_trace(oracle_mod, sc)
+    rec = gpu["rec"]
+    bnd = G.boundary_mask(ora)
+    assert np.all((rec["flags"] == ora["flags"]) | bnd), np.sum((rec["flags"] != ora["flags"]) & ~bnd)
+    G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-5)
+    both = ((rec["flags"] & 1) == 1) & ((ora["flags"] & 1) == 1)
+    err = np.maximum(np.abs(rec["x"][both] - ora["x"][both]), np.abs(rec["y"][both] - ora["y"][both])) / sc.detector.pixel
+    assert np.percentile(err, 99.9) < 1e-3, np.percentile(err, [50, 99.9, 100])
+    assert np.max(np.abs(rec["lam"] - ora["lam"]) / ora["lam"]) < 1e-7
+
+
 @pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED, P.MIXED_DS])
 def test_catadioptric_system_all_surface_features(oracle_mod, precision):
     """Annular paraboloid with Zernike figure and tilt, decentred aspheric lens, coated filter, silicon;
