@@ -512,9 +512,9 @@ def main():
         return
 
     names = {P.MIXED_DS: "mixed_ds", P.MIXED: "mixed_fp64_optics"}
-    descr = {P.MIXED_DS: "mixed, double-single (FP32-pair) positions/directions/transforms/intersections, FP32 "
-                         "deflections/SED blur/sensor",
-             P.MIXED: "mixed, FP64 positions/directions/transforms/intersections, FP32 deflections/SED blur/sensor"}
+    descr = {P.MIXED_DS: "mixed, double-single (FP32-pair) positions/directions/transforms/intersections/wavelength, "
+                         "FP32 deflections/sensor",
+             P.MIXED: "mixed, FP64 positions/directions/transforms/intersections/wavelength, FP32 deflections/sensor"}
     line = {"metric": METRIC, "value": value, "unit": "photons/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_head / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f32" if head_prec == P.MIXED_DS else "f64+f32",

@@ -319,16 +319,14 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
     R.flags = lost(PHOSIM_LOST_MISSED, si < 0 ? 0 : P.n_surf);
 }
 
-// Wavelength (Sec. 2.2): cumulative photon-number table, blur within the bin, redshift.
+// Wavelength (Sec. 2.2): cumulative photon-number table, blur within the bin, redshift.  FP64 in both FP64-optics
+// paths: the coating decisions bin it, and a single-precision wavelength would move about one photon in 5e6
+// across a band edge of a filter (a form that blurred in FP32 took as many FP64-pipe operations, in its
+// conversions, as this one).
 template <bool MIXED>
 __device__ __forceinline__ double sample_wavelength(const TraceParams& P, const DSource& s, const uint4& w0) {
     const int bin = sed_bin(P.thr + (size_t)s.sed * (P.n_bins - 1), P.sed_guide + (size_t)s.sed * (kSedGuide + 1), w0.z);
-    if constexpr (MIXED) {
-        const float lo = (float)(P.sed_lam0 + bin * P.sed_dlam);
-        return (double)(fmaf(u32of(w0.w), (float)P.sed_dlam, lo) * (float)s.zfac);
-    } else {
-        return fma(u64of(w0.w), P.sed_dlam, P.sed_lam0 + bin * P.sed_dlam) * s.zfac;
-    }
+    return fma(u64of(w0.w), P.sed_dlam, P.sed_lam0 + bin * P.sed_dlam) * s.zfac;
 }
 
 // Dynamic transmission (Sec. 3.2): the index of the first coated surface whose accept draw is not below the
