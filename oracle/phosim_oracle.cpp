@@ -319,7 +319,7 @@ bool surface_sag(const SurfT<T>& st, T x, T y, T& z, T& zx, T& zy) {
     }
     if (!st.zern.empty() && s.rnorm > 0.0) {
         T xr = x, yr = y;
-        if (val(r2) == 0.0) xr = T(1e-300);
+        if (val(r2) == 0.0) xr = T(1e-150);     // its square stays a normal number
         T rr = sqrt(xr * xr + yr * yr);
         T rho = rr / T(s.rnorm);
         T th = atan2(yr, xr);

@@ -698,3 +698,180 @@ def test_ghosts_of_a_coated_plate(oracle_mod):
     zero = oracle_mod.Oracle(_ghost_plate_scene(Tc, 0.0, t=t, xi=xi)).trace(n_threads=8)
     assert np.array_equal(plain["flags"], zero["flags"]) and np.array_equal(plain["x"], zero["x"])
     assert abs(np.mean((plain["flags"] & 1) == 1) - Tc ** 2) < 5 * math.sqrt(Tc ** 2 / N)
+
+
+# ---------------------------------------------------------------------------------------------- misalignments, figure, sources, coatings
+def _flat_mirror_scene(pert=(0.0,) * 6, zern=(), rnorm=0.0, L=500.0, coating=-1, coatings=None, sources=None,
+                       nx=512, pixel=4.0):
+    """A flat mirror at z = 0 (optionally tilted / figured) reflecting a downward beam onto a flat detector at
+    z = L above it; the chip is nx * pixel wide so that a beam turned by a few tenths of a radian stays on it."""
+    surfaces = [I.Surface(kind=I.MIRROR, R=0.0, z=0.0, r_out=1e4, pert=tuple(pert), zern=tuple(zern),
+                          zern_rnorm=rnorm, coating=coating),
+                I.Surface(kind=I.DETECTOR, R=0.0, z=L, material=1)]
+    return bare_scene(surfaces, coatings=coatings, nx=nx, pixel=pixel, sources=sources)
+
+
+def test_tilted_flat_mirror_turns_the_beam_by_twice_the_tilt(oracle_mod):
+    """Sec. 2.4.1 misalignments, with the header's convention R = Rz(tz) Ry(ty) Rx(tx) taking surface-frame
+    vectors to the telescope frame: a flat mirror tilted by tx has the normal (0, -sin tx, cos tx), so a beam
+    travelling down (0, 0, -1) leaves along (0, -sin 2tx, cos 2tx); one hitting at (x0, y0) meets the tilted
+    plane at z = y0 tan tx and reaches the detector plane z = L at y = y0 - tan 2tx (L - y0 tan tx).  A tilt ty
+    gives the normal (sin ty, 0, cos ty), the hit at z = -x0 tan ty and x = x0 + tan 2ty (L + x0 tan ty)."""
+    L = 500.0
+    rng = np.random.default_rng(11)
+    n = 64
+    x0, y0 = rng.uniform(-300, 300, n), rng.uniform(-300, 300, n)
+    pos = np.c_[x0, y0, np.full(n, 3000.0)]
+    dirs = np.tile([0.0, 0.0, -1.0], (n, 1))
+    for t in (2e-3, -7e-3, 0.05):
+        o = oracle_mod.Oracle(_flat_mirror_scene(pert=(0, 0, 0, t, 0, 0), L=L))
+        x, y, fl = o.trace_rays(pos, dirs, 600.0)
+        assert np.all(fl & 1)
+        np.testing.assert_allclose(x, x0, atol=1e-9)
+        np.testing.assert_allclose(y, y0 - math.tan(2 * t) * (L - y0 * math.tan(t)), atol=1e-9)
+        o = oracle_mod.Oracle(_flat_mirror_scene(pert=(0, 0, 0, 0, t, 0), L=L))
+        x, y, fl = o.trace_rays(pos, dirs, 600.0)
+        assert np.all(fl & 1)
+        np.testing.assert_allclose(y, y0, atol=1e-9)
+        np.testing.assert_allclose(x, x0 + math.tan(2 * t) * (L + x0 * math.tan(t)), atol=1e-9)
+    # small angles: a mirror tilted by theta moves the spot of a ray through its vertex by 2 theta L
+    o = oracle_mod.Oracle(_flat_mirror_scene(pert=(0, 0, 0, 1e-5, 0, 0), L=L))
+    x, y, fl = o.trace_rays(np.array([[0.0, 0.0, 3000.0]]), np.array([[0.0, 0.0, -1.0]]), 600.0)
+    assert abs(y[0] - (-2e-5 * L)) < 1e-9
+
+
+def test_zernike_tilt_term_rotated_by_tz(oracle_mod):
+    """Sec. 2.4.1 Zernike figure and the rotation about the optical axis: Noll Z2 = 2 rho cos(theta) with
+    coefficient c over radius rho_n is the plane z = g x, g = 2 c / rho_n, in the surface frame.  Rotated by tz
+    its telescope-frame normal is (-g cos tz, -g sin tz, 1) / sqrt(1 + g^2); a downward ray at (x0, y0) hits at
+    z = g (x0 cos tz + y0 sin tz) and leaves along (-2 g cos tz, -2 g sin tz, 1 - g^2) / (1 + g^2), so at
+    z = L it is displaced by (L - z) times that direction's slope."""
+    L, c, rn = 500.0, 0.4, 1000.0
+    g = 2 * c / rn
+    rng = np.random.default_rng(12)
+    n = 64
+    x0, y0 = rng.uniform(-300, 300, n), rng.uniform(-300, 300, n)
+    pos = np.c_[x0, y0, np.full(n, 3000.0)]
+    dirs = np.tile([0.0, 0.0, -1.0], (n, 1))
+    for tz in (0.0, 0.4, math.pi / 2, -2.0):
+        o = oracle_mod.Oracle(_flat_mirror_scene(pert=(0, 0, 0, 0, 0, tz), zern=(0.0, c), rnorm=rn, L=L))
+        x, y, fl = o.trace_rays(pos, dirs, 600.0)
+        assert np.all(fl & 1)
+        zh = g * (x0 * math.cos(tz) + y0 * math.sin(tz))
+        s = -2 * g / (1 - g * g)
+        np.testing.assert_allclose(x, x0 + (L - zh) * s * math.cos(tz), atol=1e-9)
+        np.testing.assert_allclose(y, y0 + (L - zh) * s * math.sin(tz), atol=1e-9)
+
+
+def test_zernike_figure_slopes_against_central_differences(oracle_mod):
+    """Sec. 2.4.1: the sag slopes of a conic + asphere + Zernike surface (all Noll terms up to j = 28, polar
+    derivatives turned into x and y slopes) agree with central differences of the sag itself, including at the
+    vertex, where the polar form is singular but the polynomial is smooth."""
+    rng = np.random.default_rng(13)
+    zern = tuple(rng.normal(0, 2e-4, 28))
+    alpha = [0.0, 3e-12, 0.0, -2e-18, 0.0, 0.0, 0.0, 0.0]
+    surfaces = [I.Surface(kind=I.MIRROR, R=7000.0, kappa=-0.7, alpha=alpha, zern_rnorm=900.0, zern=zern),
+                I.Surface(kind=I.MIRROR, R=0.0, zern_rnorm=500.0, zern=zern, pert=(3.0, -2.0, 0, 1e-3, 2e-3, 0.7)),
+                I.Surface(kind=I.DETECTOR, z=1.0, material=1)]
+    o = oracle_mod.Oracle(bare_scene(surfaces))
+    x = np.r_[0.0, 0.5, rng.uniform(-850, 850, 400)]
+    y = np.r_[0.0, -0.3, rng.uniform(-850, 850, 400)]
+    h = 1e-3
+    for s in (0, 1):
+        z, zx, zy = o.sag(s, x, y)
+        zp, _, _ = o.sag(s, x + h, y); zm, _, _ = o.sag(s, x - h, y)
+        np.testing.assert_allclose(zx, (zp - zm) / (2 * h), rtol=1e-6, atol=1e-9)
+        zp, _, _ = o.sag(s, x, y + h); zm, _, _ = o.sag(s, x, y - h)
+        np.testing.assert_allclose(zy, (zp - zm) / (2 * h), rtol=1e-6, atol=1e-9)
+    # and the value itself is the Noll sum of the pinned polynomials (figure-only flat surface, rho = r / 500)
+    z, _, _ = o.sag(1, x, y)
+    r, th = np.hypot(x, y) / 500.0, np.arctan2(y, x)
+    expect = sum(zern[j] * oracle_mod.zernike(j + 1, r, th) for j in range(28))
+    np.testing.assert_allclose(z, expect, rtol=1e-12, atol=1e-12)
+
+
+def test_gaussian_source_offsets_are_normal(oracle_mod):
+    """Sec. 2.2.2 background sources: a Gaussian source of width a offsets each photon's tangent-plane
+    direction by independent N(0, a^2) components (KS per axis), so |offset|^2 / a^2 is chi-square with two
+    degrees of freedom, and the direction stays a unit vector travelling down."""
+    n, a = 20000, 3e-4
+    src = I.point_sources([0.01], [-0.02], [n])
+    src.kind[:] = I.GAUSS
+    src.a[:] = a
+    sc = mirror_scene(20000.0, -1.0, 10000.0, sources=src)
+    o, (pos, d, lam, t) = _pre(oracle_mod, sc, n)
+    gx, gy = (d[:, 0] - 0.01) / a, (d[:, 1] + 0.02) / a
+    assert stats.kstest(gx, "norm").pvalue > 1e-3
+    assert stats.kstest(gy, "norm").pvalue > 1e-3
+    assert stats.kstest(gx * gx + gy * gy, "chi2", args=(2,)).pvalue > 1e-3
+    assert abs(np.corrcoef(gx, gy)[0, 1]) < 4 / math.sqrt(n)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-15)
+    assert np.all(d[:, 2] < 0)
+
+
+def test_redshift_scales_every_wavelength(oracle_mod):
+    """Sec. 2.2: a source at redshift z emits the rest-frame wavelength times (1 + z).  Under common random
+    numbers (same seed, source index and photon index) each photon of a z = 0.1 source has exactly 1.1 times
+    the wavelength of the z = 0 source's photon, and the same pupil point and direction."""
+    n = 5000
+    out = []
+    for z in (0.0, 0.1):
+        src = I.point_sources([0.0], [0.0], [n])
+        src.redshift[:] = z
+        out.append(_pre(oracle_mod, mirror_scene(20000.0, -1.0, 10000.0, sources=src), n)[1])
+    (p0, d0, l0, t0), (p1, d1, l1, t1) = out
+    np.testing.assert_allclose(l1, 1.1 * l0, rtol=2e-16, atol=0)
+    np.testing.assert_array_equal(p0, p1)
+    np.testing.assert_array_equal(d0, d1)
+    np.testing.assert_array_equal(t0, t1)
+
+
+def test_coating_angle_bins_on_a_tilted_beam(oracle_mod):
+    """Sec. 2.4.2 coatings are tables in wavelength and incidence angle.  A mirror coating with T = 1 on
+    [0.05, 0.15) rad, 0 on [0.15, 0.25) and 1 from 0.25 on (angles below the first bin take the first bin,
+    above the last the last) reflects every photon or none.  The incidence angle of an on-axis beam on a flat
+    mirror tilted by t about x or y is |t| (closed form), and that of a beam from field angle alpha on an
+    untilted mirror is alpha = asin(xi)."""
+    table = np.array([[1.0, 0.0, 1.0]])
+    coat = [I.Coating(lam0=300.0, dlam=1000.0, theta0=0.05, dtheta=0.1, table=table)]
+    expect = lambda th: table[0, min(2, max(0, int(math.floor((th - 0.05) / 0.1))))]
+    n = 400
+    for t in (0.02, 0.1, 0.14, 0.16, -0.2, 0.24, 0.26, -0.3):
+        for axis in (3, 4):
+            pert = [0.0] * 6
+            pert[axis] = t
+            sc = _flat_mirror_scene(pert=pert, coating=0, coatings=coat, nx=1024, pixel=4.0, L=300.0,
+                                    sources=I.point_sources([0.0], [0.0], [n]))
+            rec = oracle_mod.Oracle(sc).trace(image=False)
+            reason = (rec["flags"] >> 8) & 0xFF
+            if expect(abs(t)) == 1.0:
+                assert np.all(rec["flags"] & 1), (t, axis)
+            else:
+                assert np.all(reason == 5) and not np.any(rec["flags"] & 1), (t, axis)
+    for alpha in (0.12, 0.18, 0.27):
+        sc = _flat_mirror_scene(coating=0, coatings=coat, nx=1024, pixel=4.0, L=300.0,
+                                sources=I.point_sources([math.sin(alpha)], [0.0], [n]))
+        rec = oracle_mod.Oracle(sc).trace(image=False)
+        assert bool(np.all(rec["flags"] & 1)) == (expect(alpha) == 1.0), alpha
+        assert bool(np.all(((rec["flags"] >> 8) & 0xFF) == 5)) == (expect(alpha) == 0.0), alpha
+
+
+def test_bleeding_hand_worked_rows(oracle_mod):
+    """Sec. 2.5 bleeding on hand-worked rows of 8 pixels (halves [0, 4) and [4, 8) meet at the implant), full
+    well 10 (rows 0, 1) and 5 (row 2).  Row 0, left: pixel 1 holds 25, its 15 extra electrons go one at a time
+    to the closest pixels with room, left before right at equal distance: pixel 0 (3) and pixel 2 (9) take one
+    each, pixel 2 is then full, pixel 0 takes six more (to 10); distance 2 has only pixel 3 (0 -> 7).  Right:
+    pixel 4 (12) finds pixels 5 and 6 full and gives its 2 to pixel 7 (4 -> 6).  Row 1: pixel 1 (30) finds its
+    whole half-row full; the implant stops it, so 20 electrons are removed and the right half stays empty.
+    Row 2 (well 5): pixel 2 (14) gives alternately to pixel 1 (0) and pixel 3 (4), which fills after one; pixel
+    1 takes four more, then pixel 0 the last three."""
+    img = np.array([[3, 25, 9, 0, 12, 10, 10, 4],
+                    [10, 30, 10, 10, 0, 0, 0, 0]], np.uint32)
+    out, removed = oracle_mod.bleed(img, 10)
+    np.testing.assert_array_equal(out, [[10, 10, 10, 7, 10, 10, 10, 6],
+                                        [10, 10, 10, 10, 0, 0, 0, 0]])
+    assert removed == 20
+    out, removed = oracle_mod.bleed(np.array([[0, 0, 14, 4, 0, 0, 16, 0]], np.uint32), 5)
+    # right half: pixel 6 (16) gives 11: pixel 5 and 7 alternate (5, 5 after 10), pixel 4 takes the last one
+    np.testing.assert_array_equal(out, [[3, 5, 5, 5, 1, 5, 5, 5]])
+    assert removed == 0
