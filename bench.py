@@ -1,12 +1,15 @@
 """Benchmark: photons/s of the photon Monte Carlo path on one GB300 (and N GPUs by weak scaling).
 
-Workload: 1000 stars, 1e8 source photons per step (300-1200 nm blackbodies) through seven frozen-flow von
-Karman layers (4096^2 at 1 cm + 1024^2 at 64 cm each), the synthetic 8.4 m three-mirror telescope with a
-three-lens camera and a 550-700 nm filter, and 100 um of silicon, onto one 4096 x 4096 chip.  A step is one
-phosim_trace call over all photons.  The headline is the mixed-precision path with its FP64 parts in
-double-single arithmetic (--mode ds, the default) or in native FP64 (--mode mixed); the other mixed form and
-the plain all-FP64 path are timed beside it, and the moments of all three are compared with the CPU oracle on
-a photon sample.
+Headline workload (the batched persistent launch): 10^4 sources (70 % stars, 30 % Sersic galaxies with index
+0.5-4, half-light radius 0.2-3 arcsec, |e| < 0.6), photon counts log-uniform 1e2-1e7 (~8.8e9 photons), plus a
+uniform sky of 1e9 photons on 15 arcsec Gaussian nodes traced as rays of 8 photons (Sec. 3.2), through seven
+frozen-flow von Karman layers (4096^2 at 1 cm + 1024^2 at 64 cm each), the synthetic 8.4 m three-mirror
+telescope with a three-lens camera and a 550-700 nm filter, and 100 um of silicon, onto one 4096 x 4096 chip.
+A step is one phosim_trace call over all sources (autotuned schedule, dynamic transmission).  The headline is
+the mixed-precision path with its FP64 parts in double-single arithmetic; the native-FP64 mixed path and the
+plain all-FP64 path trace the same workload beside it, every source's moments are compared with the all-FP64
+path's, and the moments of all three with the CPU oracle on a photon sample.  Extras: the 1000-star 1e8-photon
+workload with the per-photon precision split, the background bundles and the adjoint.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -26,9 +29,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "photons/s end-to-end on 1 GB300 vs plain FP64 path; PSF-moment error vs oracle"
+
+
+def batched_name(scale=1.0, fine_n=4096, coarse_n=1024):
+    return ("batched: 7000 stars + 3000 Sersic galaxies (counts log-uniform 1e2-1e7) + 1e9 sky photons on 15 arcsec "
+            f"nodes in rays of 8, x{scale:g} photons; three-mirror 8.4 m telescope + 3-lens camera + 550-700 nm "
+            f"filter, 7 von Karman layers ({fine_n}^2@1cm + {coarse_n}^2@64cm), 4096^2 chip")
+
+
 def workload_name(photons=1e8, fine_n=4096, coarse_n=1024):
     return ("three-mirror 8.4 m telescope + 3-lens camera + 550-700 nm filter, 7 von Karman layers "
             f"({fine_n}^2@1cm + {coarse_n}^2@64cm), 1000 stars, {photons:.0e} photons, 4096^2 chip").replace("e+0", "e")
+
+
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -36,17 +49,16 @@ FP64_NOMINAL_TFLOPS = 1.25
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--photons", type=float, default=1e8, help="photons per step per GPU")
-    ap.add_argument("--mode", default="ds", choices=["ds", "mixed"], help="headline mixed-precision form")
-    ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain FP64 path and of the "
-                                                                  "other mixed form")
-    ap.add_argument("--sample", type=int, default=8000, help="oracle photons per star for the CPU leg")
+    ap.add_argument("--scale", type=float, default=1.0, help="photon scale of the batched workload (per GPU)")
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 path and of the "
+                                                                  "native-FP64 mixed path")
+    ap.add_argument("--sample", type=int, default=2000, help="oracle photons per source for the CPU leg")
     ap.add_argument("--no-oracle", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the precision-split, batched and adjoint legs")
-    ap.add_argument("--batched-scale", type=float, default=1.0, help="photon scale of the batched workload")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 1e8-star, background and adjoint legs")
+    ap.add_argument("--stars-photons", type=float, default=1e8, help="photons of the 1000-star extra leg")
     ap.add_argument("--fine-n", type=int, default=4096, help="fine screen size (smaller: profiling case)")
     ap.add_argument("--coarse-n", type=int, default=1024, help="coarse screen size (smaller: profiling case)")
     return ap.parse_args()
@@ -113,6 +125,7 @@ class ClockSampler:
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "launches_three_mirror_1e8.md")
+INST_PROFILE = os.path.join(ROOT, "profiles", "ds_stages_three_mirror_2e7.md")
 KERNEL_SOURCES = ("paper_1504_06570_gb300/csrc/photon.cuh", "paper_1504_06570_gb300/csrc/trace.cu",
                   "paper_1504_06570_gb300/csrc/phosim_device.cuh", "paper_1504_06570_gb300/csrc/photon_ds.cuh",
                   "paper_1504_06570_gb300/csrc/ds.cuh")
@@ -127,42 +140,27 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(photons, kernel):
-    """DRAM bytes per launch of a trace kernel (trace_kernel<1> native-FP64 mixed, ds_optics_kernel the
-    double-single optics stage) from the committed ncu summary, scaled to this launch's photons, or None when
-    the kernel sources changed since that capture."""
+def _profile_records(path, tag):
+    """(kernel, workload, value, photons, sources hash) of the `tag` lines of a committed ncu summary; lines
+    without a workload field belong to the 1000-star workload."""
     import re
     try:
-        text = open(TRAFFIC_PROFILE).read()
+        text = open(os.path.join(ROOT, "profiles", path) if not os.path.isabs(path) else path).read()
     except OSError:
-        return None
-    for m in re.finditer(r"traffic_record: kernel=(\S+) bytes=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text):
-        if m.group(1) == kernel and m.group(4) == kernel_source_hash():
-            return int(m.group(2)) * photons / int(m.group(3))
+        return []
+    pat = tag + r": kernel=(\S+)(?: workload=(\S+))? \w+=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)"
+    return [(m.group(1), m.group(2) or "stars", int(m.group(3)), int(m.group(4)), m.group(5))
+            for m in re.finditer(pat, text)]
+
+
+def recorded(path, tag, photons, kernel, wl):
+    """A per-launch figure of a kernel (DRAM bytes or thread instructions) from a committed ncu summary, scaled
+    to this launch's photons, or None when the kernel sources changed since that capture."""
+    h = kernel_source_hash()
+    for k, w, v, n, src in _profile_records(path, tag):
+        if k == kernel and w == wl and src == h:
+            return v * photons / n
     return None
-
-
-INST_PROFILE = os.path.join(ROOT, "profiles", "ds_stages_three_mirror_2e7.md")
-
-
-def recorded_instructions(photons, kernel):
-    """Thread instructions one launch of a kernel executes (ncu smsp__inst_executed x threads per instruction on
-    the committed capture), scaled to this launch's photons, or None when the kernel sources changed since."""
-    import re
-    try:
-        text = open(INST_PROFILE).read()
-    except OSError:
-        return None
-    for m in re.finditer(r"inst_record: kernel=(\S+) thread_inst=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)", text):
-        if m.group(1) == kernel and m.group(4) == kernel_source_hash():
-            return int(m.group(2)) * photons / int(m.group(3))
-    return None
-
-
-# FP32 instructions of each double-single primitive of ds.cuh (sum: TwoSum 6 + 2 + Fast2Sum 3; product:
-# 1 multiply + 3 FMAs + Fast2Sum 3; quotient: reciprocal estimate, product, ds x float product 6, ds sum 11,
-# correction and Fast2Sum; square root: reciprocal-root estimate, product, exact square, ds sum, correction)
-DS_INSTRUCTIONS = {"add": 11, "mul": 7, "div": 23, "sqrt": 20}
 
 
 def measured_peaks():
@@ -173,54 +171,113 @@ def measured_peaks():
         return {}
 
 
-def workload(photons_per_gpu, rank, fine_n=4096, coarse_n=1024):
+def stars_workload(photons, fine_n=4096, coarse_n=1024):
     from paper_1504_06570_gb300 import inputs as I
-    return I.three_mirror_scene(n_total=int(photons_per_gpu), fine_n=fine_n, coarse_n=coarse_n)
+    return I.three_mirror_scene(n_total=int(photons), fine_n=fine_n, coarse_n=coarse_n)
 
 
-def cpu_leg(scene, sample):
+def batched_workload(scale=1.0, fine_n=4096, coarse_n=1024):
+    from paper_1504_06570_gb300 import inputs as I
+    return I.batched_scene(fine_n=fine_n, coarse_n=coarse_n, photon_scale=scale)
+
+
+def cpu_leg(scene, sample, n_threads=None, o=None):
     """The oracle as it stands on the host cores over a bounded sample: the first `sample` photons of every
-    star (all threads).  Returns its rate and its records for the moment comparison."""
+    source (all threads).  Returns its rate, its records and the per-source counts."""
     from oracle import oracle as O
     cnt = np.minimum(scene.sources.n_photons, np.uint64(sample))
-    o = O.Oracle(scene)
-    cores = os.cpu_count() or 1
+    o = o or O.Oracle(scene)
+    cores = n_threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     rec = o.trace(count=cnt, n_threads=cores, image=False)
     dt = time.perf_counter() - t0
     return {"value": float(cnt.sum() / dt), "unit": "photons/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} photons of each of {len(cnt)} stars ({int(cnt.sum())} photons, {dt:.1f} s)"}, rec, cnt
+            "sample": f"first {sample} photons of each of {len(cnt)} sources ({int(cnt.sum())} photons, {dt:.1f} s)"}, rec, cnt
 
 
 def moment_errors(gpu_m, ora_rec, n_src):
-    """Per-star centroid / size / ellipticity differences between the GPU sample and the oracle sample."""
+    """Per-source centroid / size / ellipticity differences between the GPU sample and the oracle sample."""
     from paper_1504_06570_gb300 import phosim as P
     g = P.derived_moments(gpu_m)
     det = (ora_rec["flags"] & 1) == 1
-    out = []
-    for s in range(n_src):
-        m = det & (ora_rec["source"] == s)
-        if m.sum() < 50:
-            continue
-        x, y = ora_rec["x"][m], ora_rec["y"][m]
-        mx, my = x.mean(), y.mean()
-        ixx, ixy, iyy = ((x - mx) ** 2).mean(), ((x - mx) * (y - my)).mean(), ((y - my) ** 2).mean()
-        T = ixx + iyy
-        gT = g[s, 3] + g[s, 5]
-        out.append([abs(g[s, 1] - mx) / np.sqrt(T), abs(gT / T - 1), abs((g[s, 3] - g[s, 5]) / gT - (ixx - iyy) / T),
-                    abs(2 * g[s, 4] / gT - 2 * ixy / T), abs(g[s, 0] - m.sum()) / m.sum()])
-    a = np.array(out)
-    return {"stars": len(a), "max_centroid_over_size": float(a[:, 0].max()), "max_rel_T": float(a[:, 1].max()),
+    src = ora_rec["source"][det]
+    x, y = ora_rec["x"][det], ora_rec["y"][det]
+    # two-pass moments of the oracle's detected photons, per source
+    n = np.bincount(src, minlength=n_src).astype(np.float64)
+    ok = n >= 50
+    nn = np.maximum(n, 1)
+    mx, my = np.bincount(src, x, n_src) / nn, np.bincount(src, y, n_src) / nn
+    dx, dy = x - mx[src], y - my[src]
+    ixx, ixy, iyy = (np.bincount(src, dx * dx, n_src) / nn, np.bincount(src, dx * dy, n_src) / nn,
+                     np.bincount(src, dy * dy, n_src) / nn)
+    T = ixx + iyy
+    gT = g[:, 3] + g[:, 5]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        a = np.stack([np.hypot(g[:, 1] - mx, g[:, 2] - my) / np.sqrt(T), np.abs(gT / T - 1),
+                      np.abs((g[:, 3] - g[:, 5]) / gT - (ixx - iyy) / T), np.abs(2 * g[:, 4] / gT - 2 * ixy / T),
+                      np.abs(g[:, 0] - n) / nn], 1)[ok]
+    return {"sources": int(ok.sum()), "max_centroid_over_size": float(a[:, 0].max()), "max_rel_T": float(a[:, 1].max()),
             "max_de1": float(a[:, 2].max()), "max_de2": float(a[:, 3].max()), "max_rel_count": float(a[:, 4].max())}
 
 
-def gather_bytes_per_launch(sc, ops, photons):
-    """Algorithmic screen bytes: one 32-byte 2 x 2 gradient block per scale and layer for every photon that
-    survives the dynamic transmission test (fraction from the oracle's count, photons with no work)."""
+def moments_vs_fp64(sums, sums_fp64, min_count=100):
+    """Every source's moments of one path against the all-FP64 path's on the same photons: worst centroid
+    shift over the PSF size, relative size, e1 / e2 differences, relative detected count."""
+    from paper_1504_06570_gb300 import phosim as P
+    g, p = P.derived_moments(sums), P.derived_moments(sums_fp64)
+    ok = p[:, 0] > min_count
+    T, Tp = g[:, 3] + g[:, 5], p[:, 3] + p[:, 5]
+    return {"sources": int(ok.sum()),
+            "max_centroid_over_size": float((np.hypot(g[:, 1] - p[:, 1], g[:, 2] - p[:, 2]) / np.sqrt(Tp))[ok].max()),
+            "max_rel_T": float(np.abs(T / Tp - 1)[ok].max()),
+            "max_de1": float(np.abs((g[:, 3] - g[:, 5]) / T - (p[:, 3] - p[:, 5]) / Tp)[ok].max()),
+            "max_de2": float(np.abs(2 * g[:, 4] / T - 2 * p[:, 4] / Tp)[ok].max()),
+            "max_rel_count": float((np.abs(g[:, 0] - p[:, 0]) / np.maximum(p[:, 0], 1))[ok].max()),
+            "within_0.1%": bool(np.all(np.abs(T / Tp - 1)[ok] < 1e-3))}
+
+
+def algorithmic_work(sc, counts, sample=50):
+    """The oracle's operation count (sums, products, quotients, roots of the FP64 program, counted by its
+    operation-counting scalar on the first `sample` photons of every source, with the dynamic transmission
+    test) scaled to a launch of `counts` photons.  A background bundle's ray is traced once for its photons
+    (Sec. 3.2), so a bundled source's optics operations count once per ray; the entry stage's screen lookups
+    are one 32-byte 2 x 2 gradient block per scale and layer for every surviving ray."""
+    from oracle import oracle as O
+    o = O.Oracle(sc)
+    src = sc.sources
+    bundle = np.ones(len(src)) if src.bundle is None else np.maximum(1, src.bundle).astype(np.float64)
+    work = {"pre": {}, "optics": {}, "units": 0.0, "photons": float(np.sum(counts))}
     n_scales = sum(len(L.scales) for L in sc.layers)
-    surv = ops.get("survivors", None)
-    frac = surv if surv is not None else 1.0
-    return int(32 * n_scales * frac * photons)
+    gathers = 0.0
+    for b in np.unique(bundle):
+        sel = bundle == b
+        cnt = np.where(sel, np.minimum(counts, np.uint64(sample)), 0).astype(np.uint64)
+        if cnt.sum() == 0:
+            continue
+        ops = o.count_ops(count=cnt, early_reject=True)
+        units = float(np.sum(np.asarray(counts, np.float64)[sel]) / b)        # rays
+        for part in ("pre", "optics"):
+            for k, v in ops[part].items():
+                work[part][k] = work[part].get(k, 0.0) + v * units
+        work["units"] += units
+        gathers += 32.0 * n_scales * ops["survivors"] * units
+    work["gather_bytes"] = gathers
+    return work
+
+
+def ds_mix_peak(lib, stream, work):
+    """The operation rate (Tops/s) of a path doing every one of the oracle's FP64-level operations as one
+    double-single primitive, from the measured rate of each primitive (phosim_ds_rate) and the work's mix."""
+    import ctypes as C
+    r = C.c_double()
+    rates = {}
+    for name, op, it in (("add", 0, 20000), ("mul", 1, 20000), ("fma", 2, 20000), ("div", 3, 5000), ("sqrt", 4, 5000)):
+        if lib.phosim_ds_rate(op, it, 4, C.c_void_p(stream), C.byref(r)) != 0:
+            return None, None
+        rates[name] = r.value
+    mix = {k: work["optics"].get(k, 0.0) for k in ("add", "mul", "div", "sqrt")}
+    t = sum(mix[k] / rates[k] for k in mix)
+    return sum(mix.values()) / t, rates
 
 
 def precision_split(sc, mixed, plain, counts, dev):
@@ -256,58 +313,66 @@ def precision_split(sc, mixed, plain, counts, dev):
     out["fate_agreement"] = float((fa == fb).double().mean().item())
     out["position_error_px"] = {"p50": q(0.5), "p90": q(0.9), "p99": q(0.99), "p99.9": q(0.999),
                                 "p99.999": q(0.99999), "max": float(err[-1].item())}
-    gm, gp = P.derived_moments(moms[0]), P.derived_moments(moms[1])
-    T = gp[:, 3] + gp[:, 5]
-    ok = gp[:, 0] > 100
-    e1m = (gm[:, 3] - gm[:, 5]) / (gm[:, 3] + gm[:, 5]); e1p = (gp[:, 3] - gp[:, 5]) / T
-    e2m = 2 * gm[:, 4] / (gm[:, 3] + gm[:, 5]); e2p = 2 * gp[:, 4] / T
-    out["per_star_vs_fp64"] = {"stars": int(ok.sum()), "max_de1": float(np.abs(e1m - e1p)[ok].max()),
-                               "max_de2": float(np.abs(e2m - e2p)[ok].max()),
-                               "max_rel_size": float(np.abs((gm[:, 3] + gm[:, 5]) / T - 1)[ok].max()),
-                               "max_centroid_px": float(np.hypot(gm[:, 1] - gp[:, 1], gm[:, 2] - gp[:, 2])[ok].max() / d.pixel)}
+    out["per_star_vs_fp64"] = moments_vs_fp64(moms[0], moms[1])
     del recs, a, b
     torch.cuda.empty_cache()
     return out
 
 
-def batched_leg(sc2, args, dev, stream, precision):
-    """10^4 stars and Sersic galaxies with counts log-uniform 1e2-1e7 plus 1e9 sky photons on 15 arcsec
-    Gaussian nodes (rays of 8 photons, Sec. 3.2), one persistent launch per step with the autotuned schedule
-    (same optics and atmosphere)."""
+def stars_leg(args, dev, stream):
+    """The 1000-star workload (1e8 photons, the configuration of the per-photon precision split): each path
+    timed, the double-single stages timed, and every photon's fate and position compared with the all-FP64
+    path's."""
     import torch
-    from paper_1504_06570_gb300 import inputs as I
     from paper_1504_06570_gb300 import phosim as P
-    t0 = time.perf_counter()
-    sc = I.batched_scene(fine_n=16, coarse_n=16, photon_scale=args.batched_scale)
-    sc.layers = sc2.layers
-    scn = P.Scene(sc, precision, early_reject=True)
-    threads, tile = scn.autotune(sample_photons=20_000_000)
+    sc = stars_workload(args.stars_photons, args.fine_n, args.coarse_n)
+    counts = sc.sources.n_photons
+    n = int(counts.sum())
     d = sc.detector
     img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
-    mom = torch.zeros((len(sc.sources), P.MOMENT_WORDS), dtype=torch.float64, device=dev)
-    scn.trace(img, None, mom, stream=stream.cuda_stream)
-    torch.cuda.synchronize(dev)
-    steps = 2
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
+    out = {"workload": workload_name(args.stars_photons, args.fine_n, args.coarse_n), "photons_per_step": n}
+    scenes = {"mixed_ds": P.Scene(sc, P.MIXED_DS, early_reject=True, graph=True),
+              "mixed_fp64_optics": P.Scene(sc, P.MIXED, early_reject=True, graph=True),
+              "plain_fp64": P.Scene(sc, P.PLAIN_FP64, early_reject=True)}
+    for name, scn in scenes.items():
+        steps = 5 if name == "mixed_ds" else 2
+        scn.trace(img, None, None, stream=stream.cuda_stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            scn.trace(img, None, None, stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"value": n / (ms / 1e3), "unit": "photons/s", "ms_per_step": ms}
+    out["stage_ms"] = stage_times(scenes["mixed_ds"], img, None, None, None, stream, 3)
+    out["precision_split"] = {"mixed_ds": precision_split(sc, scenes["mixed_ds"], scenes["plain_fp64"], counts, dev),
+                              "mixed_fp64_optics": precision_split(sc, scenes["mixed_fp64_optics"],
+                                                                   scenes["plain_fp64"], counts, dev)}
+    for scn in scenes.values():
+        scn.close()
+    return out, sc
+
+
+def stage_times(scene, img, mom, counts, first, stream, steps):
+    """Mean milliseconds per kernel kind over `steps` traces launched kernel by kernel with CUDA events on the
+    stream (the library's stage timing): chief rays, one-kernel trace, entry, optics and bundle stages."""
+    import ctypes as C
+    from paper_1504_06570_gb300 import phosim as P
+    L = P.lib()
+    L.phosim_set_stage_timing(scene.h, 1)
+    acc = np.zeros(5)
+    ms = (C.c_double * 5)()
     for _ in range(steps):
-        scn.trace(img, None, mom, stream=stream.cuda_stream)
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b) / steps
-    n = int(sc.sources.n_photons.sum())
-    c = scn.counters()
-    if not (int(c[0]) == n and int(c[1]) + int(c[2:].sum()) == n):
-        raise RuntimeError(f"batched trace accounted for {int(c[1]) + int(c[2:].sum())} of {n} photons")
-    scn.close()
-    kinds = np.bincount(sc.sources.kind, minlength=3)
-    return {"workload": f"{kinds[0]} stars + {kinds[1]} Sersic galaxies (counts log-uniform 1e2-1e7) + {kinds[2]} "
-                        f"sky nodes (1e9 photons in rays of 8), x{args.batched_scale} photons", "photons_per_step": n,
-            "value": n / (ms / 1e3), "unit": "photons/s", "ms_per_step": ms, "autotuned": {"threads": threads, "tile": tile},
-            "setup_s": round(time.perf_counter() - t0, 1)}
+        scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
+        if L.phosim_stage_times(scene.h, ms, 5) != 0:
+            raise RuntimeError("phosim_stage_times failed")
+        acc += np.array(ms[:])
+    L.phosim_set_stage_timing(scene.h, 0)
+    return dict(zip(("chief", "one_kernel", "entry", "optics", "bundle"), (acc / steps).tolist()))
 
 
-def background_leg(sc2, dev, stream, precision):
+def background_leg(layers, dev, stream, precision):
     """Sec. 3.2 background optimisation on the batched workload's sky alone (1e9 photons on 15 arcsec Gaussian
     nodes): rays of 8 photons spread by 5 arcsec on the detector against one photon per ray, timed per step,
     and the reduced chi^2 of the two images (pixel counts, (a - b)^2 / (a + b) averaged over pixels with
@@ -319,7 +384,7 @@ def background_leg(sc2, dev, stream, precision):
     imgs = {}
     for n in (1, 8):
         sc = I.batched_scene(fine_n=16, coarse_n=16, sky_bundle=n)
-        sc.layers = sc2.layers
+        sc.layers = layers
         sky = np.nonzero(sc.sources.kind == I.GAUSS)[0]
         sc.sources = sc.sources.subset(sky[sc.sources.n_photons[sky] > 0])
         scn = P.Scene(sc, precision, early_reject=True)
@@ -347,7 +412,8 @@ def background_leg(sc2, dev, stream, precision):
 
 def adjoint_leg(dev, stream):
     """Adjoint raytrace on 64 stars on an 8 x 8 grid, 1e6 photons each, no atmosphere, 97 per-surface
-    parameters (M2 and each camera surface dx, dy, tx, ty; Z4-Z22 of the three mirrors)."""
+    parameters (M2 and each camera surface dx, dy, tx, ty; Z4-Z22 of the three mirrors), from which the 65
+    enumerated ones (the camera as one rigid body) follow by a fixed Jacobian."""
     import torch
     from paper_1504_06570_gb300 import inputs as I
     from paper_1504_06570_gb300 import phosim as P
@@ -371,17 +437,19 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = workload(args.photons, 0, args.fine_n, args.coarse_n)
+    from oracle import oracle as O
+    sc = batched_workload(args.scale, args.fine_n, args.coarse_n)
+    o = O.Oracle(sc)
     steps = []
     cpu = None
     for _ in range(args.warmup + args.steps):
-        cpu, _, _ = cpu_leg(sc, max(1, args.sample // 4))
+        cpu, _, _ = cpu_leg(sc, max(1, args.sample // 4), o=o)
         steps.append(cpu["value"])
     v = float(np.median(steps[args.warmup:]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "photons/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.photons, args.fine_n, args.coarse_n), "oracle_sample": cpu["sample"]},
+            "config": {"workload": batched_name(args.scale, args.fine_n, args.coarse_n), "oracle_sample": cpu["sample"]},
             "cpu_baseline": {**cpu, "value": v},
             "e2e": {"value": v, "unit": "photons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -391,11 +459,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    import ctypes as C
     import torch
     import torch.distributed as dist
     from paper_1504_06570_gb300 import build as B
     B.build()
     from paper_1504_06570_gb300 import phosim as P
+    from paper_1504_06570_gb300 import sharding
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -405,31 +475,32 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    L = P.lib()
 
     t_setup = time.perf_counter()
-    sc = workload(args.photons, rank, args.fine_n, args.coarse_n)
+    sc = batched_workload(args.scale, args.fine_n, args.coarse_n)
     n_src = len(sc.sources)
-    # weak scaling: rank r traces photons [r N, (r + 1) N) of every star (a longer exposure per GPU)
-    from paper_1504_06570_gb300 import sharding
+    # weak scaling: rank r traces photons [r N, (r + 1) N) of every source (a longer exposure per GPU)
     first, counts = sharding.rank_photon_range(sc.sources.n_photons, rank, world)
     photons = int(counts.sum())
     # every path with the paper's dynamic transmission (early coating rejection), which leaves the detected
-    # photons unchanged; the headline form as a CUDA graph
-    head_prec, other_prec = (P.MIXED_DS, P.MIXED) if args.mode == "ds" else (P.MIXED, P.MIXED_DS)
-    head = P.Scene(sc, head_prec, early_reject=True, graph=True)
-    other = P.Scene(sc, other_prec, early_reject=True, graph=True)
+    # photons unchanged, and its launch shape picked by the autotuner on a sample of this workload
+    head = P.Scene(sc, P.MIXED_DS, early_reject=True, graph=True)
+    other = P.Scene(sc, P.MIXED, early_reject=True, graph=True)
     plain = P.Scene(sc, P.PLAIN_FP64, early_reject=True)
+    tuned = {}
+    for name, scn in (("mixed_ds", head), ("mixed_fp64_optics", other), ("plain_fp64", plain)):
+        tuned[name] = scn.autotune(sample_photons=20_000_000, n_photons=counts, stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t_setup
     d = sc.detector
     img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
-    mom = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(scene, steps, warmup, on_start=None):
+    def timed(scene, steps, warmup, mom, on_start=None):
         for _ in range(warmup):
             scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -441,50 +512,31 @@ def main():
             scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
             b.record(stream)
         barrier()
-        per = np.array([a.elapsed_time(b) for a, b in ev])
-        return per
+        return np.array([a.elapsed_time(b) for a, b in ev])
 
-    # peaks of the arithmetic roofline (FMA issue rate), measured on this device
+    # peaks of the arithmetic roofline, measured on this device: FP64 and FP32 FMA rates
     fp64_rate = fp32_rate = None
-    try:
-        import ctypes as C
-        r = C.c_double()
-        if P.lib().phosim_fma_rate(1, 2000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
-            fp64_rate = r.value
-        if P.lib().phosim_fma_rate(0, 20000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
-            fp32_rate = r.value
-    except Exception:
-        pass
+    r = C.c_double()
+    if L.phosim_fma_rate(1, 2000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
+        fp64_rate = r.value
+    if L.phosim_fma_rate(0, 20000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
+        fp32_rate = r.value
 
-    def kernel_times(scene, steps):
-        """Mean milliseconds per kernel kind (chief rays, one-kernel trace, entry stage, optics stage) over
-        `steps` traces launched kernel by kernel with CUDA events on the stream (the library's stage timing)."""
-        import ctypes as C
-        L = P.lib()
-        L.phosim_set_stage_timing(scene.h, 1)
-        acc = np.zeros(5)
-        ms = (C.c_double * 5)()
-        for _ in range(steps):
-            scene.trace(img, None, mom, n_photons=counts, first=first, stream=stream.cuda_stream)
-            if L.phosim_stage_times(scene.h, ms, 5) != 0:
-                raise RuntimeError("phosim_stage_times failed")
-            acc += np.array(ms[:])
-        L.phosim_set_stage_timing(scene.h, 0)
-        return acc / steps
-
+    # moment sums of each path over all its runs (warm-up and timed): the derived moments do not depend on
+    # how many identical runs were added
+    moms = {k: torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+            for k in ("mixed_ds", "mixed_fp64_optics", "plain_fp64")}
     clocks = ClockSampler(local)
     clocks.start()
-    per_head = timed(head, args.steps, args.warmup, on_start=clocks.mark)
+    per_head = timed(head, args.steps, args.warmup, moms["mixed_ds"], on_start=clocks.mark)
     clock_rec = clocks.stop()
-    per_other = timed(other, args.plain_steps, 1)
-    per_plain = timed(plain, args.plain_steps, 1)
-    kt_head = kernel_times(head, 3)
-    kt_other = kernel_times(other, 2)
+    per_other = timed(other, args.plain_steps, 1, moms["mixed_fp64_optics"])
+    per_plain = timed(plain, args.plain_steps, 1, moms["plain_fp64"])
+    kt = stage_times(head, img, None, counts, first, stream, 2)
 
-    # e2e through the C ABI with host buffers: pinned host image in, result image out, every step
+    # e2e through the C ABI with host buffers: a pinned host image in and the result image out, every step
     himg = torch.zeros((d.ny, d.nx), dtype=torch.int32, pin_memory=True)
-    for _ in range(1):
-        head.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+    head.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -492,7 +544,7 @@ def main():
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
     img_bytes = d.nx * d.ny * 4
-    src_bytes = n_src * (P.C.sizeof(P.Source) if hasattr(P, "C") else 80) + n_src * 16
+    src_bytes = n_src * (C.sizeof(P.Source) + 16)
 
     t_head = float(per_head.sum()) / 1e3
     t_other = float(per_other.sum()) / 1e3
@@ -505,110 +557,122 @@ def main():
     if not (int(counters[0]) == photons and int(counters[1]) + int(counters[2:].sum()) == photons):
         raise RuntimeError(f"headline trace accounted for {int(counters[1]) + int(counters[2:].sum())} of {photons} photons")
 
+    # the job's image and moment sums: one sum-reduce over the ranks (photon ranges are disjoint), checked
+    # against the detected counts of every rank
+    img.zero_()
+    job_mom = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+    head.trace(img, None, job_mom, n_photons=counts, first=first, stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    det = torch.tensor([float(head.counters()[1])], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(img, op=dist.ReduceOp.SUM)
+        dist.all_reduce(job_mom, op=dist.ReduceOp.SUM)
+        dist.all_reduce(det, op=dist.ReduceOp.SUM)
+    job = {"ranks": world, "detected": int(det.item()), "image_sum": int(img.to(torch.int64).sum().item()),
+           "moment_count_sum": float(job_mom[:, 0].sum().item())}
+    job["consistent"] = job["image_sum"] == job["detected"] and job["moment_count_sum"] == float(job["detected"])
+
     if rank != 0:
+        head.close(); other.close(); plain.close()
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    names = {P.MIXED_DS: "mixed_ds", P.MIXED: "mixed_fp64_optics"}
-    descr = {P.MIXED_DS: "mixed, double-single (FP32-pair) positions/directions/transforms/intersections/wavelength, "
-                         "FP32 deflections/sensor",
-             P.MIXED: "mixed, FP64 positions/directions/transforms/intersections/wavelength, FP32 deflections/sensor"}
+    sums = {k: v.cpu().numpy() for k, v in moms.items()}
     line = {"metric": METRIC, "value": value, "unit": "photons/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_head / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f32" if head_prec == P.MIXED_DS else "f64+f32",
-            "data": "synthetic",
-            "config": {"workload": workload_name(args.photons, args.fine_n, args.coarse_n),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f32", "data": "synthetic",
+            "config": {"workload": batched_name(args.scale, args.fine_n, args.coarse_n),
                        "photons_per_step_per_gpu": photons, "sources": n_src,
-                       "precision": descr[head_prec],
-                       "l2": "inputs larger than L2 (gradient screens 2.8 GB, read in both precisions' forms)",
+                       "precision": "mixed, double-single (FP32-pair) positions/directions/transforms/intersections/"
+                                    "wavelength, FP32 deflections/sensor",
+                       "schedule": {"autotuned": tuned}, "parallelism": f"photon ranges x{world}",
+                       "l2": "inputs larger than L2 (gradient screens 3.8 GB single precision, swept by the wind)",
                        "setup_s": round(setup_s, 1)},
-            names[other_prec]: {"value": other_value, "unit": "photons/s",
-                                "ms_per_step": t_other / args.plain_steps * 1e3, "precision": descr[other_prec]},
+            "mixed_fp64_optics": {"value": other_value, "unit": "photons/s",
+                                  "ms_per_step": t_other / args.plain_steps * 1e3,
+                                  "precision": "mixed, FP64 positions/directions/transforms/intersections/wavelength, "
+                                               "FP32 deflections/sensor"},
             "plain_fp64": {"value": plain_value, "unit": "photons/s", "ms_per_step": t_plain / args.plain_steps * 1e3,
                            "speedup_of_headline": value / plain_value},
+            "moments_vs_plain_fp64": {"mixed_ds": moments_vs_fp64(sums["mixed_ds"], sums["plain_fp64"]),
+                                      "mixed_fp64_optics": moments_vs_fp64(sums["mixed_fp64_optics"], sums["plain_fp64"])},
             "detected_fraction": float(counters[1] / max(1, counters[0])),
             "e2e": {"value": photons * world / e2e_s, "unit": "photons/s", "h2d_bytes_per_step": img_bytes + src_bytes,
                     "d2h_bytes_per_step": img_bytes},
-            # per step: chief rays, then the entry and optics stages and the moment-stripe sum (double-single)
-            # or the one trace kernel
-            "gpu_launches": (4 if head_prec == P.MIXED_DS else 2) * args.steps, "clocks": clock_rec,
+            "job_reduce": job,
+            "stage_ms": kt,
+            "clocks": clock_rec,
             "fma_peaks_measured_tflops": {"fp64": fp64_rate, "fp32": fp32_rate}}
+    # kernels per step: chief rays, then per chunk of 2^27 photons the entry, optics and bundle stages, and
+    # the moment-stripe sum
+    import math
+    bundle = np.ones(n_src, np.uint64) if sc.sources.bundle is None else np.maximum(1, sc.sources.bundle).astype(np.uint64)
+    units = int(np.sum((counts + bundle - np.uint64(1)) // bundle))
+    chunks = max(1, math.ceil(units / (1 << 27)))
+    line["gpu_launches"] = (2 + 3 * chunks) * args.steps
 
     if not args.no_oracle:
-        from oracle import oracle as O
-        o = O.Oracle(sc)
-        ops = o.count_ops(count=np.minimum(counts, np.uint64(50)), early_reject=True)
-        fl_pre = sum(v for k, v in ops["pre"].items() if k != "transcendental")
-        fl_opt = sum(v for k, v in ops["optics"].items() if k != "transcendental")
-        kt_mixed = kt_head if head_prec == P.MIXED else kt_other
-        kt_ds = kt_head if head_prec == P.MIXED_DS else kt_other
+        work = algorithmic_work(sc, counts)
+        fl_opt = sum(v for k, v in work["optics"].items() if k != "transcendental")
+        fl_pre = sum(v for k, v in work["pre"].items() if k != "transcendental")
+        t_opt = kt["optics"] / 1e3
+        achieved = fl_opt / t_opt / 1e12
+        mix_peak, ds_rates = ds_mix_peak(L, stream.cuda_stream, work)
+        peak32 = fp32_rate or None
+        inst = recorded(INST_PROFILE, "inst_record", photons, "ds_optics_kernel", "batched")
+        line["roofline"] = {
+            "bound": "alu", "kernel": "ds_optics_kernel", "kernel_ms": kt["optics"], "entry_kernel_ms": kt["entry"],
+            "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32 if peak32 else None,
+            "traffic": recorded(TRAFFIC_PROFILE, "traffic_record", photons, "ds_optics_kernel", "batched"),
+            "algorithmic_ops_per_launch": fl_opt,
+            "note": ("achieved = the oracle's FP64-level operations of the optics and sensor (sums, products, "
+                     "quotients, roots counted by its operation-counting scalar on the first 50 photons of every "
+                     "source, dynamic transmission applied, a background ray counted once for its 8 photons) per "
+                     "launch over the optics stage's time (CUDA events around its launches on the stream); peak = "
+                     "measured FP32 FMA rate of this GPU (2 operations per instruction on the pipe the stage runs "
+                     "on), the ceiling of any implementation of those operations on it"),
+            "vs_double_single_emulation": {"peak_tops": mix_peak, "frac": achieved / mix_peak if mix_peak else None,
+                                           "primitive_tops": ds_rates,
+                                           "note": "the rate if every one of those operations were one double-single "
+                                                   "primitive (measured rates, the workload's mix); above 1: the "
+                                                   "stage does part of them in single precision where the error "
+                                                   "budget allows"},
+            "issue_frac": (inst / t_opt / 1e12) / (fp32_rate / 2) if (inst and fp32_rate) else None,
+            "algorithmic_gather_bytes": work["gather_bytes"],
+            "entry_gather_gbs": work["gather_bytes"] / (kt["entry"] / 1e3) / 1e9 if kt["entry"] else None,
+            "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}
+        # native-FP64 mixed kernel: the same operations against the FP64 FMA rate
+        kt_other = stage_times(other, img, None, counts, first, stream, 1)
         peak64 = fp64_rate or FP64_NOMINAL_TFLOPS
-        # native-FP64 mixed kernel (one kernel): the oracle's FP64 optics flops against the FP64 FMA rate
-        fp64_roof = {"bound": "alu", "kernel": "trace_kernel<1>", "kernel_ms": float(kt_mixed[1]),
-                     "achieved": fl_opt * photons / (float(kt_mixed[1]) / 1e3) / 1e12,
-                     "peak": peak64, "unit": "TFLOP/s", "traffic": recorded_traffic(photons, "trace_kernel<1>"),
-                     "note": (f"FP64 optics flops {fl_opt:.0f} per sampled photon (oracle op count with the dynamic "
-                              f"transmission rejection; +{fl_pre:.0f} sampling and atmosphere flops, mostly FP32 "
-                              f"here) over the kernel's time (CUDA events around its launches on the stream); peak = "
-                              + ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)"))}
-        fp64_roof["frac"] = fp64_roof["achieved"] / peak64
-        # double-single kernel: bound by FP32 instruction issue.  achieved = the thread instructions the optics
-        # stage executes per launch (committed ncu capture, per sampled photon) over its time; peak = the SMs'
-        # issue rate (measured FP32 FMA rate / 2: one FMA a lane a cycle).  The oracle's FP64 operations over
-        # the same time give the emulated FP64 rate, against the native FP64 FMA rate.
-        peak32 = fp32_rate / 2 if fp32_rate else None
-        t_opt = float(kt_ds[3]) / 1e3
-        inst = recorded_instructions(photons, "ds_optics_kernel")
-        ds_inst = sum(ops["optics"][k] * c for k, c in DS_INSTRUCTIONS.items())
-        emulated = fl_opt * photons / t_opt / 1e12
-        ds_roof = {"bound": "alu", "kernel": "ds_optics_kernel", "kernel_ms": float(kt_ds[3]),
-                   "entry_kernel_ms": float(kt_ds[2]),
-                   "achieved": inst / t_opt / 1e12 if inst else None,
-                   "peak": peak32, "unit": "Tinst/s", "traffic": recorded_traffic(photons, "ds_optics_kernel"),
-                   "instructions_per_photon": inst / photons if inst else None,
-                   "note": ("thread instructions of the optics stage per sampled photon (ncu smsp__inst_executed x "
-                            "threads per instruction on the committed 2e7-photon capture of the same kernel "
-                            "sources, profiles/ds_stages_three_mirror_2e7.md) x photons over the stage's time (CUDA "
-                            "events around its launches on the stream); peak = measured FP32 FMA rate / 2, the issue "
-                            "rate of one instruction a lane a cycle"),
-                   "emulated_fp64": {"tflops": emulated, "vs_measured_fp64_peak": emulated / peak64,
-                                     "note": (f"the oracle's FP64 optics operations per sampled photon ({fl_opt:.0f}: "
-                                              f"{ops['optics']['add']:.0f} add, {ops['optics']['mul']:.0f} mul, "
-                                              f"{ops['optics']['div']:.0f} div, {ops['optics']['sqrt']:.0f} sqrt; "
-                                              f"{ds_inst:.0f} FP32 instructions as double-single primitives "
-                                              f"{DS_INSTRUCTIONS}) over the optics stage's time")}}
-        ds_roof["frac"] = ds_roof["achieved"] / peak32 if (peak32 and inst) else None
-        head_roof, other_roof = (ds_roof, fp64_roof) if head_prec == P.MIXED_DS else (fp64_roof, ds_roof)
-        head_roof["algorithmic_gather_bytes"] = gather_bytes_per_launch(sc, ops, photons)
-        head_roof["traffic_unit"] = "DRAM bytes per launch (ncu, committed summary)"
-        line["roofline"] = head_roof
-        line["roofline_" + names[other_prec]] = other_roof
-        line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) * photons / (float(np.mean(per_plain)) / 1e3) / 1e12,
+        line["roofline_mixed_fp64_optics"] = {
+            "bound": "alu", "kernel": "trace_kernel<1>", "kernel_ms": kt_other["one_kernel"],
+            "achieved": fl_opt / (kt_other["one_kernel"] / 1e3) / 1e12, "peak": peak64, "unit": "TFLOP/s",
+            "note": "the oracle's optics operations per launch over the kernel's time; peak = " +
+                    ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)")}
+        line["roofline_mixed_fp64_optics"]["frac"] = line["roofline_mixed_fp64_optics"]["achieved"] / peak64
+        line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) / (t_plain / args.plain_steps) / 1e12,
                                        "peak": peak64, "unit": "TFLOP/s"}
         line["roofline_plain_fp64"]["frac"] = line["roofline_plain_fp64"]["achieved"] / peak64
-        if rank == 0:
-            cpu, rec, cnt = cpu_leg(sc, args.sample)
-            line["cpu_baseline"] = cpu
-            errs = {}
-            for name, scn in ((names[head_prec], head), (names[other_prec], other), ("plain_fp64", plain)):
-                m2 = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
-                i2 = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
-                scn.trace(i2, None, m2, n_photons=cnt)
-                torch.cuda.synchronize(dev)
-                errs[name] = moment_errors(m2.cpu().numpy(), rec, n_src)
-            line["moment_error_vs_oracle"] = errs
-    if not args.no_extras and rank == 0:
-        line["precision_split"] = {names[head_prec]: precision_split(sc, head, plain, counts, dev),
-                                   names[other_prec]: precision_split(sc, other, plain, counts, dev)}
-        line["batched"] = batched_leg(sc, args, dev, stream, head_prec)
-        line["background_bundles"] = background_leg(sc, dev, stream, head_prec)
-        line["adjoint"] = adjoint_leg(dev, stream)
-    print(json.dumps(line))
+        cpu, rec, cnt = cpu_leg(sc, args.sample)
+        line["cpu_baseline"] = cpu
+        errs = {}
+        for name, scn in (("mixed_ds", head), ("mixed_fp64_optics", other), ("plain_fp64", plain)):
+            m2 = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+            i2 = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
+            scn.trace(i2, None, m2, n_photons=cnt)
+            torch.cuda.synchronize(dev)
+            errs[name] = moment_errors(m2.cpu().numpy(), rec, n_src)
+        line["moment_error_vs_oracle"] = errs
     head.close()
     other.close()
     plain.close()
+    if not args.no_extras:
+        line["stars_1e8"], sc_stars = stars_leg(args, dev, stream)
+        line["background_bundles"] = background_leg(sc_stars.layers, dev, stream, P.MIXED_DS)
+        line["adjoint"] = adjoint_leg(dev, stream)
+    print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

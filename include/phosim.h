@@ -16,6 +16,8 @@
  *     (vignetting, total internal reflection, a non-converged intersection, leaving the chip) are not
  *     errors: such photons are dropped and counted (phosim_get_counters).
  *   - Thread safety: calls on different scenes may run concurrently; calls on one scene must not overlap.
+   - Devices: a scene lives on the CUDA device that was current when it was created; every call on it must be
+     made with that device current (else INVALID_ARGUMENT), and device buffers passed to it must be on it.
  */
 #ifndef PHOSIM_H
 #define PHOSIM_H
@@ -237,9 +239,12 @@ phosim_status phosim_load_hf_kick(phosim_scene* scene, const double* quantiles, 
    sources, n_photons and first are host arrays.  Photon i of source s always draws the same random
    numbers (counter = (i, s, block), key = seed), whatever the batching.
    image: nx * ny uint32 counts, ADDED to (device or host pointer; a host pointer is staged through a
-          scene-owned device buffer and the call returns after the copy back).
+          scene-owned device buffer and the call returns after the copy back; another device's memory is
+          INVALID_ARGUMENT).
    records: NULL or a device array of sum(n_photons) records in source order.
    moments: NULL or a device array of n_src * PHOSIM_MOMENT_WORDS doubles; sums are added.
+   records and moments must be device (or managed) memory of the scene's device: a host pointer returns
+   INVALID_ARGUMENT before anything is launched.
    stream: a cudaStream_t (NULL = legacy default stream); all device work is ordered on it.
    Errors: INVALID_ARGUMENT, NOT_READY, LIMIT, OUT_OF_MEMORY, CUDA. */
 phosim_status phosim_trace(phosim_scene* scene, const phosim_source* sources, int n_src,
@@ -262,6 +267,18 @@ phosim_status phosim_grad(phosim_scene* scene, const phosim_source* sources, int
    two-kernel double-single path it applies to the entry and bundle stages; the optics stage keeps blocks of
    256 threads, whose warps take the surfaces together. */
 phosim_status phosim_set_schedule(phosim_scene* scene, int threads_per_block, int tile_photons);
+
+/* The launch shape phosim_trace uses now (after phosim_set_schedule or phosim_autotune): threads per block
+   and photons per warp tile (0 = chosen per call from the workload).  Errors: INVALID_ARGUMENT (null). */
+phosim_status phosim_get_schedule(const phosim_scene* scene, int* threads_per_block, int* tile_photons);
+
+/* Per-source detected count, centroid and central second moments from the additive sums phosim_trace writes
+   (the number of photons detected from every source and their mean coordinate, Sec. 3.1, and the second
+   moments the image-quality comparisons use): out[6 s + 0] = n, [1] = ref_x + sum dx / n, [2] = ref_y +
+   sum dy / n, [3] = sum dx^2 / n - (sum dx / n)^2, [4] = sum dx dy / n - (sum dx / n)(sum dy / n),
+   [5] = sum dy^2 / n - (sum dy / n)^2; NaN for a source with no detected photon.  sums: host, n_src *
+   PHOSIM_MOMENT_WORDS doubles; out: host, n_src * 6.  Pure host arithmetic.  Errors: INVALID_ARGUMENT. */
+phosim_status phosim_moments_derive(const double* sums, int n_src, double* out);
 
 /* Autotuner of the trace launch: traces a sample of the workload (about sample_photons photons, spread
    over the sources in proportion to their counts) with each candidate (threads per block in {64, 128, 256},
@@ -289,10 +306,14 @@ phosim_status phosim_get_counters(phosim_scene* scene, uint64_t* out, int n);
      (else PHOSIM_ERR_INVALID_ARGUMENT: a host image would need a staging buffer);
    - the first call on a device looks up the array's device address on that device (set-up, once per
      device, with that device current); make that first call before any stream capture;
+   - the call copies its source list and tile prefix from host memory that it frees on return, so on a
+     stream that is being captured it returns PHOSIM_ERR_INVALID_ARGUMENT and enqueues nothing;
    - every call shares the array and leaves its contents behind; each call clears the counters it needs.
      Calls whose GPU work overlaps (different streams, or different threads on one device) race on the
      array and must be serialised by the caller;
-   - phosim_get_counters does not report its photons.
+   - records and moments, like image, must be device memory of the scene's device (else INVALID_ARGUMENT);
+   - phosim_get_counters does not report its photons, and per-kernel stage timing does not cover it (after
+     it, phosim_stage_times reads zero).
    Errors: as phosim_trace, plus LIMIT above. */
 #define PHOSIM_NOALLOC_MAX_SOURCES 4096
 #define PHOSIM_NOALLOC_SCRATCH_BYTES (1u << 20)

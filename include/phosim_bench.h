@@ -20,6 +20,15 @@ extern "C" {
    Errors: INVALID_ARGUMENT (null output, iterations < 1), CUDA. */
 phosim_status phosim_fma_rate(int fp64, int iterations, int blocks_per_sm, void* stream, double* tflops);
 
+/* Sustained throughput of one double-single primitive of the PHOSIM_MIXED_DS path on the current device, in
+   tera-operations per second: every thread of a grid of blocks_per_sm x SM-count blocks of 256 threads runs 8
+   independent dependent chains of `iterations` operations.  op: 0 sum, 1 product, 2 fused multiply-add
+   (a b + c, one normalisation), 3 quotient, 4 square root.  With the FP64-level operation mix of a workload
+   (the oracle's count of its sums, products, quotients and roots), these rates give the operation rate an
+   implementation doing every such operation in double-single could reach.  Blocks on `stream` and
+   synchronises it.  Errors: INVALID_ARGUMENT (unknown op, null output, iterations < 1), OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_ds_rate(int op, int iterations, int blocks_per_sm, void* stream, double* tops);
+
 /* The device Philox4x32-10 the trace kernel draws from (Salmon et al., SC'11), applied to n counters with
    one key, for known-answer checks.  ctr: host, 4 n words; key: host, 2 words; out: host, 4 n words.
    Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */

@@ -57,6 +57,69 @@ extern "C" phosim_status phosim_fma_rate(int fp64, int iterations, int blocks_pe
 }
 
 namespace {
+
+// Eight independent dependent chains of one double-single primitive per thread (op: 0 sum, 1 product, 2 fused
+// multiply-add, 3 quotient, 4 square root); the constants keep every chain finite and normal.
+template <int OP>
+__global__ void ds_chains(int iterations, float seed, float* sink) {
+    using namespace phosim;
+    ds a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = ds_of(1.0 + 1e-3 * (double)(threadIdx.x + k) + (double)seed);
+    const ds m = ds_of(0.99999988079071045), c = ds_of(1.000000059604645e-7), q = ds_of(1.0000001192092896);
+    for (int i = 0; i < iterations; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (OP == 0) a[k] = a[k] + c;
+            else if (OP == 1) a[k] = a[k] * m;
+            else if (OP == 2) a[k] = dfma(a[k], m, c);
+            else if (OP == 3) a[k] = a[k] / q;
+            else a[k] = ds_sqrt(a[k]);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k].hi + a[k].lo;
+    if (s == -1.f) sink[threadIdx.x] = s;      // never true; keeps the chains alive
+}
+
+}  // namespace
+
+extern "C" phosim_status phosim_ds_rate(int op, int iterations, int blocks_per_sm, void* stream, double* tops) {
+    if (!tops || op < 0 || op > 4 || iterations < 1 || blocks_per_sm < 1) return PHOSIM_ERR_INVALID_ARGUMENT;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PHOSIM_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* sink = nullptr;
+    if (cudaMalloc(&sink, 256 * sizeof(float)) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_OUT_OF_MEMORY; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * blocks_per_sm;
+    for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, st);
+        switch (op) {
+            case 0: ds_chains<0><<<blocks, 256, 0, st>>>(iterations, 0.f, sink); break;
+            case 1: ds_chains<1><<<blocks, 256, 0, st>>>(iterations, 0.f, sink); break;
+            case 2: ds_chains<2><<<blocks, 256, 0, st>>>(iterations, 0.f, sink); break;
+            case 3: ds_chains<3><<<blocks, 256, 0, st>>>(iterations, 0.f, sink); break;
+            default: ds_chains<4><<<blocks, 256, 0, st>>>(iterations, 0.f, sink); break;
+        }
+    }
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess || ms <= 0.f) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    *tops = 8.0 * (double)iterations * blocks * 256.0 / (ms * 1e-3) / 1e12;
+    return PHOSIM_OK;
+}
+
+namespace {
 __global__ void philox_kernel(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = phosim::philox(ctr[i], k0, k1);

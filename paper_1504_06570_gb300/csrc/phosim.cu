@@ -372,7 +372,45 @@ phosim_status launch_graph(phosim_scene* sc, int slot, const KernelLaunch* L, in
 
 }  // namespace
 
-// =========================================================================================================
+namespace phosim {
+
+phosim_status check_scene_device(const phosim_scene* sc) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    return dev == sc->device ? PHOSIM_OK : PHOSIM_ERR_INVALID_ARGUMENT;
+}
+
+phosim_status check_device_buffer(const void* p, int device) {
+    if (!p) return PHOSIM_OK;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_INVALID_ARGUMENT; }
+    if (attr.type == cudaMemoryTypeManaged) return PHOSIM_OK;
+    if (attr.type == cudaMemoryTypeDevice && attr.device == device) return PHOSIM_OK;
+    return PHOSIM_ERR_INVALID_ARGUMENT;
+}
+
+// Sec. 3.1 (the number of detected photons of every source and their mean coordinate) and the second moments
+// of the image-quality gates: the sums are about a reference point (ref_x, ref_y), so the centroid is
+// ref + sum(d) / n and the central moments sum(d d') / n - mean(d) mean(d'), with d = x - ref small.
+void derive_moments(const double* sums, int n_src, double* out6) {
+    for (int s = 0; s < n_src; ++s) {
+        const double* M = sums + (size_t)s * PHOSIM_MOMENT_WORDS;
+        double* o = out6 + (size_t)s * 6;
+        const double n = M[0];
+        o[0] = n;
+        if (n > 0) {
+            const double ux = M[1] / n, uy = M[2] / n;
+            o[1] = M[6] + ux; o[2] = M[7] + uy;
+            o[3] = M[3] / n - ux * ux; o[4] = M[4] / n - ux * uy; o[5] = M[5] / n - uy * uy;
+        } else {
+            for (int k = 1; k < 6; ++k) o[k] = std::nan("");
+        }
+    }
+}
+
+}  // namespace phosim
+
+// =================================================================================================
 extern "C" {
 
 const char* phosim_status_string(phosim_status s) {
@@ -443,6 +481,7 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
         delete sc;
         return PHOSIM_ERR_CUDA;
     }
+    sc->device = dev;
     if ((st = upload(sc->table_mem, d->ell, (size_t)d->n_ell, &pd)) != PHOSIM_OK) goto fail;
     P.ell = pd;
     if ((st = upload(sc->table_mem, f.data(), f.size(), &pf)) != PHOSIM_OK) goto fail;
@@ -493,6 +532,7 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
                                  int n_mat, const phosim_coating* coats, int n_coat) {
     if (!sc || !surf || n_surf < 1 || (n_mat > 0 && !mats) || (n_coat > 0 && !coats) || n_mat < 1 || n_coat < 0)
         return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (check_scene_device(sc) != PHOSIM_OK) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (n_surf > PHOSIM_MAX_SURFACES || n_mat > kMaxMaterials || n_coat > kMaxCoatings) return PHOSIM_ERR_LIMIT;
     for (int i = 0; i < n_surf; ++i) {
         const phosim_surface& s = surf[i];
@@ -617,6 +657,7 @@ phosim_status phosim_load_optics(phosim_scene* sc, const phosim_surface* surf, i
 
 phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, int n_layers) {
     if (!sc || n_layers < 0 || (n_layers > 0 && !layers)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (check_scene_device(sc) != PHOSIM_OK) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (n_layers > PHOSIM_MAX_LAYERS) return PHOSIM_ERR_LIMIT;
     for (int k = 0; k < n_layers; ++k) {
         const phosim_layer& L = layers[k];
@@ -669,6 +710,7 @@ phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, 
 
 phosim_status phosim_load_seds(phosim_scene* sc, const double* flux, int n_sed, int n_bins, double lam0, double dlam) {
     if (!sc || !flux || n_sed < 1 || n_bins < 2 || !(dlam > 0.0) || !is_finite(lam0)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (check_scene_device(sc) != PHOSIM_OK) return PHOSIM_ERR_INVALID_ARGUMENT;
     const size_t n = (size_t)n_sed * n_bins;
     double total = 0.0;
     for (int s = 0; s < n_sed; ++s) {
@@ -726,6 +768,7 @@ phosim_status phosim_load_seds(phosim_scene* sc, const double* flux, int n_sed, 
 
 phosim_status phosim_load_sersic(phosim_scene* sc, const double* table, int n_tables, int n_nodes) {
     if (!sc || !table || n_tables < 1 || n_nodes < 2) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (check_scene_device(sc) != PHOSIM_OK) return PHOSIM_ERR_INVALID_ARGUMENT;
     const size_t n = (size_t)n_tables * n_nodes;
     for (size_t i = 0; i < n; ++i) if (!(table[i] >= 0.0) || !is_finite(table[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
     std::vector<float> f(table, table + n);
@@ -746,6 +789,7 @@ phosim_status phosim_load_sersic(phosim_scene* sc, const double* table, int n_ta
 
 phosim_status phosim_load_hf_kick(phosim_scene* sc, const double* q, int n) {
     if (!sc || n < 0 || (n > 0 && (!q || n < 2))) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (check_scene_device(sc) != PHOSIM_OK) return PHOSIM_ERR_INVALID_ARGUMENT;
     for (int i = 0; i < n; ++i) if (!(q[i] >= 0.0) || !is_finite(q[i]) || (i && q[i] < q[i - 1])) return PHOSIM_ERR_INVALID_ARGUMENT;
     std::vector<void*> mem;
     double* d = nullptr;
@@ -777,9 +821,23 @@ phosim_status phosim_set_schedule(phosim_scene* sc, int threads, int tile) {
     return PHOSIM_OK;
 }
 
+phosim_status phosim_get_schedule(const phosim_scene* sc, int* threads, int* tile) {
+    if (!sc || !threads || !tile) return PHOSIM_ERR_INVALID_ARGUMENT;
+    *threads = sc->threads;
+    *tile = sc->tile_photons;
+    return PHOSIM_OK;
+}
+
+phosim_status phosim_moments_derive(const double* sums, int n_src, double* out) {
+    if (n_src < 0 || (n_src > 0 && (!sums || !out))) return PHOSIM_ERR_INVALID_ARGUMENT;
+    derive_moments(sums, n_src, out);
+    return PHOSIM_OK;
+}
+
 phosim_status phosim_autotune(phosim_scene* sc, const phosim_source* src, int n_src, const uint64_t* n_photons,
                               uint64_t sample, void* stream, int* out_threads, int* out_tile) {
     if (!sc || n_src < 1 || !src || !n_photons || sample < 1) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (check_scene_device(sc) != PHOSIM_OK) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
     uint64_t total = 0;
     for (int s = 0; s < n_src; ++s) total += n_photons[s];
@@ -866,6 +924,12 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
                            void* stream) {
     if (!sc || n_src < 0 || (n_src > 0 && (!src || !n_photons)) || !image) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
+    {   // the scene's device must be current; records and moments must be device memory on it
+        phosim_status vs = check_scene_device(sc);
+        if (vs == PHOSIM_OK) vs = check_device_buffer(records, sc->device);
+        if (vs == PHOSIM_OK) vs = check_device_buffer(moments, sc->device);
+        if (vs != PHOSIM_OK) return vs;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const int mode = sc->precision;
     const bool staged = mode == PHOSIM_MIXED_DS;        // the two-kernel double-single path
@@ -938,6 +1002,7 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         host_image = true;
     } else {
         host_image = attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
+        if (attr.type == cudaMemoryTypeDevice && attr.device != sc->device) return PHOSIM_ERR_INVALID_ARGUMENT;
     }
     const size_t img_bytes = (size_t)sc->base.nx * sc->base.ny * sizeof(uint32_t);
     uint32_t* d_image = image;
@@ -1093,6 +1158,10 @@ phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src,
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
     if (n_params > kMaxGradParams) return PHOSIM_ERR_LIMIT;
     if (sc->base.flags & kGhostFlag) return PHOSIM_ERR_UNSUPPORTED;   // the adjoint follows forward paths only
+    {
+        phosim_status vs = check_scene_device(sc);
+        if (vs != PHOSIM_OK) return vs;
+    }
     const TraceParams& B = sc->base;
     GradParams G;
     std::memset(&G, 0, sizeof(G));
@@ -1153,22 +1222,21 @@ phosim_status phosim_grad(phosim_scene* sc, const phosim_source* src, int n_src,
     CU(cudaStreamSynchronize(st));
     // cotangent seeds of the final positions: dL/dx_i = Ax + Bxx (x_i - mean x) + Bxy (y_i - mean y), ...
     std::vector<double> seeds((size_t)n_src * 8, 0.0);
+    std::vector<double> derived((size_t)n_src * 6);
+    derive_moments(mom.data(), n_src, derived.data());
     for (int s = 0; s < n_src; ++s) {
-        const double* M = &mom[(size_t)s * PHOSIM_MOMENT_WORDS];
-        const double n = M[0];
-        double mx = 0, my = 0, ixx = 0, ixy = 0, iyy = 0;
+        const double* D = &derived[(size_t)s * 6];
+        const double n = D[0];
         if (n > 0) {
-            const double ux = M[1] / n, uy = M[2] / n;
-            ixx = M[3] / n - ux * ux; ixy = M[4] / n - ux * uy; iyy = M[5] / n - uy * uy;
-            mx = M[6] + ux; my = M[7] + uy;
             const double* g = dL + (size_t)s * 5;
             double* q = &seeds[(size_t)s * 8];
             q[0] = g[0] / n; q[1] = g[1] / n; q[2] = 2.0 * g[2] / n; q[3] = g[3] / n; q[4] = 2.0 * g[4] / n;
-            q[5] = mx; q[6] = my;
+            q[5] = D[1]; q[6] = D[2];
         }
         if (moments_out) {
             double* o = moments_out + (size_t)s * 6;
-            o[0] = n; o[1] = mx; o[2] = my; o[3] = ixx; o[4] = ixy; o[5] = iyy;
+            o[0] = n;
+            for (int k = 1; k < 6; ++k) o[k] = n > 0 ? D[k] : 0.0;
         }
     }
     const size_t gbytes = ((size_t)n_src * 8 + (size_t)n_src * n_params) * sizeof(double);

@@ -21,6 +21,7 @@ struct TraceGraph {
 struct phosim_scene {
     phosim::TraceParams base;       // scalars and device table pointers; per-call fields filled by a trace
     int precision = PHOSIM_PLAIN_FP64;
+    int device = 0;                 // the CUDA device current at creation; every call must run with it current
     bool optics_loaded = false, seds_loaded = false;
     int sm_count = 0;
     int threads = 256;
@@ -87,4 +88,11 @@ const void* moment_stripes_kernel_ptr();
 cudaError_t launch_moment_stripes(const TraceParams& P, cudaStream_t st);
 int ds_optics_threads(int threads);      // the optics stage's block size for a schedule's block size
 void free_all(std::vector<void*>& v);
+// PHOSIM_OK when the current device is the scene's, INVALID_ARGUMENT otherwise (CUDA on a failed query)
+phosim_status check_scene_device(const phosim_scene* sc);
+// PHOSIM_OK when p is null or device / managed memory usable on `device`; INVALID_ARGUMENT for host memory,
+// unregistered pointers and another device's memory
+phosim_status check_device_buffer(const void* p, int device);
+// count, centroid and central second moments of n_src sources from their PHOSIM_MOMENT_WORDS additive sums
+void derive_moments(const double* sums, int n_src, double* out6);
 }  // namespace phosim

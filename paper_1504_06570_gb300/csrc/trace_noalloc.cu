@@ -57,13 +57,23 @@ extern "C" phosim_status phosim_trace_noalloc(phosim_scene* sc, const phosim_sou
     if (!sc || n_src < 0 || (n_src > 0 && (!src || !n_photons)) || !image) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (n_src > PHOSIM_NOALLOC_MAX_SOURCES) return PHOSIM_ERR_LIMIT;
     if (!sc->optics_loaded || !sc->seds_loaded) return PHOSIM_ERR_NOT_READY;
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, image) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_INVALID_ARGUMENT; }
-    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return PHOSIM_ERR_INVALID_ARGUMENT;
-    void* base = nullptr;
-    phosim_status st = scratch_address(&base);
-    if (st != PHOSIM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // The source list and tile prefix below are copied from host vectors that this call frees on return, so a
+    // stream being captured would record copies from freed memory: refuse before anything is enqueued.
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &capture) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+    if (capture != cudaStreamCaptureStatusNone) return PHOSIM_ERR_INVALID_ARGUMENT;
+    sc->timing_used = 0;      // per-kernel timing does not cover this call
+    // the scene's device must be current (the scratch address is looked up per device), and every output
+    // must be device memory on it
+    phosim_status st = check_scene_device(sc);
+    if (st == PHOSIM_OK) st = check_device_buffer(image, sc->device);
+    if (st == PHOSIM_OK) st = check_device_buffer(records, sc->device);
+    if (st == PHOSIM_OK) st = check_device_buffer(moments, sc->device);
+    if (st != PHOSIM_OK) return st;
+    void* base = nullptr;
+    st = scratch_address(&base);
+    if (st != PHOSIM_OK) return st;
     const int mode = sc->precision;
     int per_sm = 0;
     if (trace_occupancy(mode, sc->threads, &per_sm) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }

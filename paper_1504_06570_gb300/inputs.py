@@ -561,6 +561,52 @@ def grad_grid_scene(n_side=8, photons=1_000_000, seed=5, zernike_nm_max=50.0):
     return sc, params, camera
 
 
+def rigid_group_pert(surfaces, group, pivot_z, dx=0.0, dy=0.0, tx=0.0, ty=0.0):
+    """Per-surface misalignments (dx, dy, dz, tx, ty, tz) that move the surfaces of `group` as one rigid body
+    (Sec. 2.4.1 misalignments of a whole assembly, such as the camera): the body is turned by Ry(ty) Rx(tx)
+    about the point (0, 0, pivot_z), then shifted by (dx, dy).  A surface whose vertex sits h = z - pivot_z above
+    the pivot keeps the body's orientation and has its vertex moved to the turned point,
+    (sin ty cos tx h, -sin tx h, (cos ty cos tx - 1) h) + (dx, dy, 0).  Returns {surface: pert}."""
+    out = {}
+    for k in group:
+        h = surfaces[k].z - pivot_z
+        out[k] = (dx + math.sin(ty) * math.cos(tx) * h, dy - math.sin(tx) * h,
+                  (math.cos(ty) * math.cos(tx) - 1.0) * h, tx, ty, 0.0)
+    return out
+
+
+def grad_grid_parameters(surfaces, params, camera, pivot_z=None):
+    """The differentiation workload's enumerated parameters: M2 dx, dy, tx, ty; the camera as one rigid body
+    dx, dy, tx, ty (turned about its detector vertex unless pivot_z is given); Z4-Z22 of M1, M2 and M3 (65 in
+    all).  Returns (names, J) with J[i, p] the derivative of per-surface parameter params[p] (the (surface, field)
+    pairs phosim_grad takes) with respect to enumerated parameter i at zero misalignment, from
+    rigid_group_pert: per-surface gradients g (n_src x len(params)) give the enumerated ones as g @ J.T."""
+    if pivot_z is None:
+        pivot_z = surfaces[camera[-1]].z
+    index = {p: k for k, p in enumerate(params)}
+    names, rows = [], []
+
+    def row(entries):
+        r = np.zeros(len(params))
+        for p, v in entries:
+            r[index[p]] += v
+        return r
+    for f, nm in ((0, "dx"), (1, "dy"), (3, "tx"), (4, "ty")):
+        names.append(f"M2 {nm}")
+        rows.append(row([((1, f), 1.0)]))
+    h = {c: surfaces[c].z - pivot_z for c in camera}
+    names += ["camera dx", "camera dy", "camera tx", "camera ty"]
+    rows.append(row([((c, 0), 1.0) for c in camera]))
+    rows.append(row([((c, 1), 1.0) for c in camera]))
+    rows.append(row([((c, 3), 1.0) for c in camera] + [((c, 1), -h[c]) for c in camera]))
+    rows.append(row([((c, 4), 1.0) for c in camera] + [((c, 0), h[c]) for c in camera]))
+    for m in range(3):
+        for j in range(3, 22):
+            names.append(f"M{m + 1} Z{j + 1}")
+            rows.append(row([((m, 100 + j), 1.0)]))
+    return names, np.array(rows)
+
+
 # ----------------------------------------------------------------------------------------------------------
 # high-frequency atmospheric kick (Sec. 2.3.2): the long-exposure PSF of the kappa > kappa_crit screens
 # ----------------------------------------------------------------------------------------------------------

@@ -110,6 +110,8 @@ def lib():
         L.phosim_autotune.argtypes = [vp, C.POINTER(Source), C.c_int, C.POINTER(C.c_uint64), C.c_uint64, vp,
                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.phosim_get_counters.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int]
+        L.phosim_get_schedule.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.phosim_moments_derive.argtypes = [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double)]
         L.phosim_destroy_scene.argtypes = [vp]
         L.phosim_destroy_scene.restype = None
         L.phosim_status_string.argtypes = [C.c_int]
@@ -306,6 +308,12 @@ class Scene:
                                                          C.byref(t), C.byref(k)))
         return t.value, k.value
 
+    def schedule(self):
+        """phosim_get_schedule: (threads per block, photons per warp tile) of the scene's trace launch."""
+        t, k = C.c_int(), C.c_int()
+        _check("phosim_get_schedule", self.L.phosim_get_schedule(self.h, C.byref(t), C.byref(k)))
+        return t.value, k.value
+
     def counters(self):
         out = (C.c_uint64 * 10)()
         _check("phosim_get_counters", self.L.phosim_get_counters(self.h, out, 10))
@@ -341,15 +349,15 @@ def records_to_numpy(rec_tensor):
 
 
 def derived_moments(m):
-    """(count, mean x, mean y, Ixx, Ixy, Iyy) from the additive sums of phosim_trace."""
-    m = np.asarray(m, np.float64).reshape(-1, MOMENT_WORDS)
-    n = m[:, 0]
-    with np.errstate(invalid="ignore", divide="ignore"):
-        mx, my = m[:, 1] / n, m[:, 2] / n
-        ixx = m[:, 3] / n - mx * mx
-        ixy = m[:, 4] / n - mx * my
-        iyy = m[:, 5] / n - my * my
-    return np.stack([n, mx + m[:, 6], my + m[:, 7], ixx, ixy, iyy], 1)
+    """(count, mean x, mean y, Ixx, Ixy, Iyy) per source from the additive sums of phosim_trace, by
+    phosim_moments_derive (NaN for a source with no detected photon)."""
+    if hasattr(m, "detach"):
+        m = m.detach().cpu().numpy()
+    m = np.ascontiguousarray(np.asarray(m, np.float64).reshape(-1, MOMENT_WORDS))
+    out = np.zeros((m.shape[0], 6))
+    dp = C.POINTER(C.c_double)
+    _check("phosim_moments_derive", lib().phosim_moments_derive(m.ctypes.data_as(dp), m.shape[0], out.ctypes.data_as(dp)))
+    return out
 
 
 def _autograd_function():
@@ -362,11 +370,19 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, theta, scene, params):
+            # one FP64 trace with per-source moment sums (the adjoint runs only in backward)
             scene.set_parameters(params, theta.detach().cpu().numpy())
             n = len(scene.sources)
-            _, m = scene.grad(np.zeros((n, 5)), params)
+            dev = torch.device("cuda", torch.cuda.current_device())
+            d = scene.scene.detector
+            img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
+            sums = torch.zeros((n, MOMENT_WORDS), dtype=torch.float64, device=dev)
+            if scene.precision != PLAIN_FP64:
+                raise ValueError("PSFMoments needs a PLAIN_FP64 scene (the adjoint differentiates the FP64 path)")
+            scene.trace(img, None, sums)
+            m = derived_moments(sums)
             ctx.scene, ctx.params = scene, params
-            return torch.as_tensor(m[:, 1:], dtype=theta.dtype, device=theta.device)
+            return torch.as_tensor(np.nan_to_num(m[:, 1:]), dtype=theta.dtype, device=theta.device)
 
         @staticmethod
         def backward(ctx, g):

@@ -165,3 +165,82 @@ def test_bundle_and_reflection_limits():
     torch.cuda.synchronize()
     assert np.array_equal(img.cpu().numpy().view(np.uint32), ref["image"])
     s.close()
+
+
+def test_host_records_or_moments_are_refused_before_launch():
+    """phosim_trace writes records and moment sums from its kernels, so they must be device memory of the
+    scene's device: host tensors return INVALID_ARGUMENT and nothing is launched (the image is untouched)."""
+    sc = G.test_system_scene(sources=G.mixed_sources([300, 200]))
+    for prec in (P.PLAIN_FP64, P.MIXED_DS):
+        s = P.Scene(sc, prec)
+        d = sc.detector
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        rec_dev = torch.zeros(500 * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        mom_dev = torch.zeros((2, P.MOMENT_WORDS), dtype=torch.float64, device="cuda")
+        for rec, mom in ((torch.zeros(500 * P.RECORD_DTYPE.itemsize, dtype=torch.uint8), mom_dev),
+                         (rec_dev, torch.zeros((2, P.MOMENT_WORDS), dtype=torch.float64)),
+                         (torch.zeros(500 * P.RECORD_DTYPE.itemsize, dtype=torch.uint8).pin_memory(), None)):
+            with pytest.raises(P.PhosimError) as e:
+                s.trace(img, rec, mom)
+            assert e.value.code == -1
+        torch.cuda.synchronize()
+        assert int(img.sum()) == 0
+        s.trace(img, rec_dev, mom_dev)
+        torch.cuda.synchronize()
+        assert int(img.sum()) > 0
+        s.close()
+
+
+def test_autotune_keeps_a_listed_candidate_and_results_do_not_change():
+    """phosim_autotune times each candidate launch shape on a sample of the workload and keeps the fastest:
+    the scene then reports one of the listed candidates (phosim_get_schedule), and traces give bit-identical
+    records and image before and after (the random numbers are counter-based), and the same moment sums up to
+    their summation order."""
+    counts = [5000, 20000, 1, 0, 7000]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=23))
+    for prec in (P.PLAIN_FP64, P.MIXED_DS):
+        before = G.run_gpu(sc, prec, early_reject=True)
+        s = P.Scene(sc, prec, early_reject=True)
+        assert s.schedule() == (256, 0)
+        t, k = s.autotune(sample_photons=20000)
+        assert t in (64, 128, 256) and k in (64, 256, 1024, 4096)
+        assert s.schedule() == (t, k)
+        n = int(np.sum(counts))
+        d = sc.detector
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        rec = torch.zeros(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        mom = torch.zeros((len(counts), P.MOMENT_WORDS), dtype=torch.float64, device="cuda")
+        s.trace(img, rec, mom)
+        torch.cuda.synchronize()
+        assert np.array_equal(P.records_to_numpy(rec), before["rec"])
+        assert np.array_equal(img.cpu().numpy().view(np.uint32), before["image"])
+        # sums are reduced per tile before atomics, so their rounding order follows the schedule
+        np.testing.assert_allclose(mom.cpu().numpy(), before["moments"], rtol=1e-10, atol=1e-10)
+        # every other listed schedule gives the same records too
+        for tt, kk in ((64, 64), (128, 4096)):
+            s.set_schedule(tt, kk)
+            assert s.schedule() == (tt, kk)
+            rec.zero_()
+            img.zero_()
+            s.trace(img, rec, None)
+            torch.cuda.synchronize()
+            assert np.array_equal(P.records_to_numpy(rec), before["rec"])
+        s.close()
+
+
+def test_moments_derive_matches_two_pass_moments_of_the_records():
+    """phosim_moments_derive turns the additive sums into the count, centroid and central second moments;
+    they equal the two-pass moments of the detected records' positions (FP64 path)."""
+    counts = [3000, 500, 0]
+    sc = G.test_system_scene(sources=G.mixed_sources(counts, seed=29))
+    out = G.run_gpu(sc, P.PLAIN_FP64)
+    m = P.derived_moments(out["moments"])
+    r = out["rec"]
+    src = np.repeat(np.arange(len(counts)), counts)
+    for s_ in range(2):
+        k = (src == s_) & ((r["flags"] & 1) == 1)
+        x, y = r["x"][k], r["y"][k]
+        exp = [k.sum(), x.mean(), y.mean(), ((x - x.mean()) ** 2).mean(), ((x - x.mean()) * (y - y.mean())).mean(),
+               ((y - y.mean()) ** 2).mean()]
+        np.testing.assert_allclose(m[s_], exp, rtol=1e-9, atol=1e-12)
+    assert m[2, 0] == 0 and np.all(np.isnan(m[2, 1:]))

@@ -61,6 +61,65 @@ def test_full_size_sampled_parity(oracle_mod, scene, precision):
         assert np.array_equal(sample["pix"][okpix], ora["pix"][okpix])
     else:
         assert np.mean(err < 1e-2) > 0.999, np.percentile(err, [50, 99, 100])
+    # per-star moments of the same sampled photons (those both detect), GPU records against oracle records:
+    # the 0.1 % moment gate for every precision
+    src = np.repeat(np.arange(len(counts)), 64)
+    worst = 0.0
+    for s_ in range(len(counts)):
+        k = both & (src == s_)
+        if k.sum() < 5:
+            continue
+        xg, yg, xo, yo = sample["x"][k], sample["y"][k], ora["x"][k], ora["y"][k]
+        To = xo.var() + yo.var()
+        for a, b in ((xg.mean(), xo.mean()), (yg.mean(), yo.mean())):
+            worst = max(worst, abs(a - b) / np.sqrt(To))
+        for a, b in ((xg.var(), xo.var()), (yg.var(), yo.var()),
+                     (((xg - xg.mean()) * (yg - yg.mean())).mean(), ((xo - xo.mean()) * (yo - yo.mean())).mean())):
+            worst = max(worst, abs(a - b) / To)
+    assert worst < 1e-3, worst
+
+
+def test_precision_split_full_workload():
+    """Each mixed path against the all-FP64 GPU path on every one of the 1e8 photons of the large workload: the
+    photons keep the all-FP64 fate (at most 1e-7 of them differ, at accept boundaries), the positions of photons
+    both detect agree to 1e-4 pixel at the 99.999th percentile, and every star's centroid, size and ellipticity
+    agree within the 0.1 % moment gate."""
+    sc = I.three_mirror_scene()
+    counts = sc.sources.n_photons
+    n = int(counts.sum())
+    d = sc.detector
+    recs, sums = {}, {}
+    for prec in (P.PLAIN_FP64, P.MIXED, P.MIXED_DS):
+        s = P.Scene(sc, prec, early_reject=True)
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        rec = torch.empty(n * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        mom = torch.zeros((len(counts), P.MOMENT_WORDS), dtype=torch.float64, device="cuda")
+        s.trace(img, rec, mom)
+        torch.cuda.synchronize()
+        s.close()
+        del img
+        r = rec.view(torch.float64).view(-1, 6)
+        recs[prec] = (r[:, 0].clone(), r[:, 1].clone(), rec.view(torch.int32).view(-1, 12)[:, 10].clone())
+        sums[prec] = mom.cpu().numpy()
+        del rec, r
+        torch.cuda.empty_cache()
+    xp, yp, fp = recs[P.PLAIN_FP64]
+    gp = P.derived_moments(sums[P.PLAIN_FP64])
+    ok = gp[:, 0] > 100
+    Tp = gp[:, 3] + gp[:, 5]
+    for prec in (P.MIXED, P.MIXED_DS):
+        x, y, f = recs[prec]
+        assert int((f != fp).sum().item()) <= n // 10_000_000
+        both = ((f & 1) == 1) & ((fp & 1) == 1)
+        err = torch.maximum((x - xp).abs(), (y - yp).abs())[both] / d.pixel
+        q = torch.quantile(err[torch.randperm(len(err), device=err.device)[:10_000_000]].double(), 0.99999).item()
+        assert q <= 1e-4, q
+        g = P.derived_moments(sums[prec])
+        T = g[:, 3] + g[:, 5]
+        assert np.all(np.abs(np.hypot(g[:, 1] - gp[:, 1], g[:, 2] - gp[:, 2]) / np.sqrt(Tp))[ok] < 1e-3)
+        assert np.all(np.abs(T / Tp - 1)[ok] < 1e-3)
+        assert np.all(np.abs((g[:, 3] - g[:, 5]) / T - (gp[:, 3] - gp[:, 5]) / Tp)[ok] < 1e-3)
+        assert np.all(np.abs(2 * g[:, 4] / T - 2 * gp[:, 4] / Tp)[ok] < 1e-3)
 
 
 def test_double_single_chunks_compose():
@@ -90,3 +149,99 @@ def test_double_single_chunks_compose():
     assert np.array_equal(c_full, c1 + c2)
     assert np.array_equal(full, part1 + part2)
     assert int(full.sum()) == int(c_full[1])
+
+
+@pytest.fixture(scope="module")
+def batched():
+    return I.batched_scene()
+
+
+def _batched_sample(sc, seed=31):
+    """A fixed sample of the batched workload's sources: one Sersic galaxy of every index level (64), 96 stars
+    and 48 sky nodes (rays of 8 photons), with a block of 64 photons of each at a random offset."""
+    rng = np.random.default_rng(seed)
+    src = sc.sources
+    ser = np.nonzero(src.kind == I.SERSIC)[0]
+    pick = [int(rng.choice(ser[src.table[ser] == t])) for t in np.unique(src.table[ser])]
+    pick += list(rng.choice(np.nonzero(src.kind == I.POINT)[0], 96, replace=False))
+    pick += list(rng.choice(np.nonzero(src.kind == I.GAUSS)[0], 48, replace=False))
+    pick = np.array(sorted(pick))
+    cnt = np.zeros(len(src), np.uint64)
+    first = np.zeros(len(src), np.uint64)
+    cnt[pick] = 64
+    first[pick] = (rng.random(len(pick)) * (src.n_photons[pick] - 64).astype(np.float64)).astype(np.uint64)
+    return pick, cnt, first
+
+
+def test_batched_workload_full_launch_and_sampled_parity(oracle_mod, batched):
+    """The batched workload (10^4 stars and Sersic galaxies with counts log-uniform 1e2-1e7, plus 1e9 sky photons
+    in rays of 8) in the launch configuration the benchmark times (double-single, early rejection, CUDA graph,
+    autotuned schedule): every photon of the full launch is accounted for and the image holds the detected
+    ones; then a fixed sample of sources (every Sersic index level, stars, sky nodes) is traced photon by photon
+    in every precision and compared with the oracle: fates identical away from flagged accept boundaries,
+    positions within 1e-4 pixel (FP64) or 1e-2 pixel for 99.9 % of photons (mixed paths)."""
+    sc = batched
+    counts = sc.sources.n_photons
+    n = int(counts.sum())
+    d = sc.detector
+    s = P.Scene(sc, P.MIXED_DS, early_reject=True, graph=True)
+    s.autotune(sample_photons=20_000_000)
+    img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+    s.trace(img)
+    torch.cuda.synchronize()
+    c = s.counters()
+    assert int(c[0]) == n and int(c[1]) + int(c[2:].sum()) == n
+    assert int(img.sum().item()) == int(c[1])
+    pick, cnt, first = _batched_sample(sc)
+    ora = G.oracle_trace(oracle_mod, sc, n_photons=cnt, first=first)
+    bnd = G.boundary_mask(ora)
+    det_o = (ora["flags"] & 1) == 1
+    assert det_o.sum() > 1000
+    for prec in (P.MIXED_DS, P.MIXED, P.PLAIN_FP64):
+        scn = s if prec == P.MIXED_DS else P.Scene(sc, prec, early_reject=True)
+        m = int(cnt.sum())
+        rec = torch.zeros(m * P.RECORD_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        i2 = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        scn.trace(i2, rec, None, n_photons=cnt, first=first)
+        torch.cuda.synchronize()
+        r = P.records_to_numpy(rec)
+        if prec != P.MIXED_DS:
+            scn.close()
+        det_g = (r["flags"] & 1) == 1
+        assert np.all((r["flags"] == ora["flags"]) | bnd), prec
+        both = det_g & det_o
+        err = np.maximum(np.abs(r["x"][both] - ora["x"][both]), np.abs(r["y"][both] - ora["y"][both])) / d.pixel
+        if prec == P.PLAIN_FP64:
+            assert np.mean(err <= 1e-4) >= 0.99999 and err.max() < 1e-4, err.max()
+        else:
+            assert np.mean(err < 1e-2) > 0.999, np.percentile(err, [50, 99, 100])
+        kinds = sc.sources.kind[ora["source"][both]]
+        assert set(np.unique(kinds)) == {I.POINT, I.SERSIC, I.GAUSS}
+    s.close()
+
+
+def test_batched_workload_moments_double_single_vs_fp64(batched):
+    """Equal moment accuracy on the batched workload: every source's moments from the double-single path (the
+    benchmark's headline) and from the all-FP64 path over all ~9.8e9 photons agree within the 0.1 % gate
+    (centroid within 1e-3 of the size, size and ellipticities within 1e-3), for sources with > 100 detected
+    photons, and the detected counts agree to 1e-6."""
+    sc = batched
+    d = sc.detector
+    out = {}
+    for prec in (P.MIXED_DS, P.PLAIN_FP64):
+        s = P.Scene(sc, prec, early_reject=True)
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        mom = torch.zeros((len(sc.sources), P.MOMENT_WORDS), dtype=torch.float64, device="cuda")
+        s.trace(img, None, mom)
+        torch.cuda.synchronize()
+        s.close()
+        out[prec] = P.derived_moments(mom)
+    g, gp = out[P.MIXED_DS], out[P.PLAIN_FP64]
+    ok = gp[:, 0] > 100
+    assert ok.sum() > 5000
+    assert np.all(np.abs(g[:, 0] - gp[:, 0]) <= 1e-6 * gp[:, 0] + 1)
+    T, Tp = g[:, 3] + g[:, 5], gp[:, 3] + gp[:, 5]
+    assert np.all((np.hypot(g[:, 1] - gp[:, 1], g[:, 2] - gp[:, 2]) / np.sqrt(Tp))[ok] < 1e-3)
+    assert np.all(np.abs(T / Tp - 1)[ok] < 1e-3)
+    assert np.all(np.abs((g[:, 3] - g[:, 5]) / T - (gp[:, 3] - gp[:, 5]) / Tp)[ok] < 1e-3)
+    assert np.all(np.abs(2 * g[:, 4] / T - 2 * gp[:, 4] / Tp)[ok] < 1e-3)

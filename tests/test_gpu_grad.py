@@ -93,3 +93,20 @@ def test_autograd_function_backward_is_the_adjoint():
     g, _ = s.grad(w.numpy(), params)
     np.testing.assert_allclose(theta.grad.numpy(), g.sum(0), rtol=1e-12)
     s.close()
+
+
+def test_autograd_forward_is_one_trace_with_the_adjoints_moments():
+    """The forward pass of PSFMoments is a single FP64 trace with moment sums; its moments are those of the
+    adjoint's own forward pass (same photons, same FP64 kernel), derived by phosim_moments_derive."""
+    counts = [2000, 1000, 0]
+    sc = scene_for_grad(counts, seed=6)
+    s = P.Scene(sc, P.PLAIN_FP64)
+    params = [(0, 3), (1, 0)]
+    theta = torch.tensor([1e-6, 0.02], dtype=torch.float64)
+    M = P.psf_moments(theta, s, params).numpy()
+    _, m = s.grad(np.zeros((len(counts), 5)), params)
+    np.testing.assert_allclose(M[:2], m[:2, 1:], rtol=1e-12, atol=1e-15)
+    assert np.all(M[2] == 0)          # a source with no photons has no moments (NaN mapped to 0)
+    with pytest.raises(ValueError):
+        P.psf_moments(theta, P.Scene(sc, P.MIXED_DS), params)
+    s.close()

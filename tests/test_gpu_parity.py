@@ -93,7 +93,7 @@ def test_catadioptric_system_all_surface_features(oracle_mod, precision):
         assert r["max_err_px"] < 1e-6, r
         G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
     else:
-        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-3)
     assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
 
 
@@ -112,7 +112,7 @@ def test_second_atmospheric_kick(oracle_mod, precision):
         assert err.max() / sc.detector.pixel < 1e-6
         G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
     else:
-        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-3)
 
 
 @pytest.mark.parametrize("schedule", [(32, 32), (64, 96), (256, 1024), (128, 0)])
@@ -281,7 +281,7 @@ def test_sensor_extensions(oracle_mod, precision):
         both = det_g & det_o
         err = np.maximum(np.abs(gpu["rec"]["x"][both] - ora["x"][both]), np.abs(gpu["rec"]["y"][both] - ora["y"][both]))
         assert err.max() / sc.detector.pixel < 1e-6
-    G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6 if precision == P.PLAIN_FP64 else 3e-3)
+    G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6 if precision == P.PLAIN_FP64 else 1e-3)
 
 
 def test_bleeding_matches_oracle(oracle_mod):
@@ -332,7 +332,7 @@ def test_background_bundles(oracle_mod, precision):
         assert r["max_err_px"] < 1e-6, r
         G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
     else:
-        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-3)
     assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
     # one photon per ray: exactly the unbundled trace
     sc.sources.bundle = np.array([1, 1, 1], np.int32)
@@ -379,5 +379,5 @@ def test_ghosts_in_the_catadioptric_system(oracle_mod, precision):
         assert err.max() / sc.detector.pixel < 1e-6
         G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-6)
     else:
-        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=3e-3)
+        G.compare_moments(gpu["moments"], G.oracle_moments(ora, len(counts)), rel=1e-3)
     assert np.array_equal(gpu["image"], G.image_from_pix(gpu["rec"], sc.detector))
