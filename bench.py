@@ -220,11 +220,14 @@ def moment_errors(gpu_m, ora_rec, n_src):
             "max_de1": float(a[:, 2].max()), "max_de2": float(a[:, 3].max()), "max_rel_count": float(a[:, 4].max())}
 
 
-def moments_vs_fp64(sums, sums_fp64, min_count=100):
+def moments_vs_fp64(sums, sums_fp64, min_count=100, runs=1, runs_fp64=1):
     """Every source's moments of one path against the all-FP64 path's on the same photons: worst centroid
-    shift over the PSF size, relative size, e1 / e2 differences, relative detected count."""
+    shift over the PSF size, relative size, e1 / e2 differences, relative detected count (the sums may hold
+    several identical runs: the counts are divided by the number of runs)."""
     from paper_1504_06570_gb300 import phosim as P
     g, p = P.derived_moments(sums), P.derived_moments(sums_fp64)
+    g[:, 0] /= runs
+    p[:, 0] /= runs_fp64
     ok = p[:, 0] > min_count
     T, Tp = g[:, 3] + g[:, 5], p[:, 3] + p[:, 5]
     return {"sources": int(ok.sum()),
@@ -534,16 +537,21 @@ def main():
     per_plain = timed(plain, args.plain_steps, 1, moms["plain_fp64"])
     kt = stage_times(head, img, None, counts, first, stream, 2)
 
-    # e2e through the C ABI with host buffers: a pinned host image in and the result image out, every step
+    # e2e through the C ABI with host buffers: every step copies in a pinned host image (and the source list
+    # and photon counts), and reads back the result image and the per-source moment sums
     himg = torch.zeros((d.ny, d.nx), dtype=torch.int32, pin_memory=True)
-    head.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+    dmom = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
+    hmom = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, pin_memory=True)
+    head.trace(himg, None, dmom, n_photons=counts, first=first, stream=stream.cuda_stream)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        head.trace(himg, None, None, n_photons=counts, first=first, stream=stream.cuda_stream)
+        head.trace(himg, None, dmom, n_photons=counts, first=first, stream=stream.cuda_stream)
+        hmom.copy_(dmom, non_blocking=True)
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
     img_bytes = d.nx * d.ny * 4
+    mom_bytes = n_src * P.MOMENT_WORDS * 8
     src_bytes = n_src * (C.sizeof(P.Source) + 16)
 
     t_head = float(per_head.sum()) / 1e3
@@ -596,11 +604,14 @@ def main():
                                                "FP32 deflections/sensor"},
             "plain_fp64": {"value": plain_value, "unit": "photons/s", "ms_per_step": t_plain / args.plain_steps * 1e3,
                            "speedup_of_headline": value / plain_value},
-            "moments_vs_plain_fp64": {"mixed_ds": moments_vs_fp64(sums["mixed_ds"], sums["plain_fp64"]),
-                                      "mixed_fp64_optics": moments_vs_fp64(sums["mixed_fp64_optics"], sums["plain_fp64"])},
+            "moments_vs_plain_fp64": {
+                "mixed_ds": moments_vs_fp64(sums["mixed_ds"], sums["plain_fp64"], runs=args.warmup + args.steps,
+                                            runs_fp64=1 + args.plain_steps),
+                "mixed_fp64_optics": moments_vs_fp64(sums["mixed_fp64_optics"], sums["plain_fp64"],
+                                                     runs=1 + args.plain_steps, runs_fp64=1 + args.plain_steps)},
             "detected_fraction": float(counters[1] / max(1, counters[0])),
             "e2e": {"value": photons * world / e2e_s, "unit": "photons/s", "h2d_bytes_per_step": img_bytes + src_bytes,
-                    "d2h_bytes_per_step": img_bytes},
+                    "d2h_bytes_per_step": img_bytes + mom_bytes},
             "job_reduce": job,
             "stage_ms": kt,
             "clocks": clock_rec,

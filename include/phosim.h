@@ -74,8 +74,16 @@ enum {
                                     parameters */
 #define PHOSIM_BACK_REFLECT 16u  /* back-side reflection (Sec. 2.4.2): a photon whose conversion length takes it
                                     past the back of the silicon is reflected there with the Fresnel probability
-                                    of the silicon / vacuum interface at normal incidence, ((n - 1) / (n + 1))^2,
-                                    and converts on its way back (no interference fringing) */
+                                    of the silicon / vacuum interface at normal incidence, ((n - 1) / (n + 1))^2
+                                    (with PHOSIM_FRINGE: the single-layer interference result), and converts on
+                                    its way back */
+#define PHOSIM_FRINGE 32u       /* with PHOSIM_BACK_REFLECT, fringing (Sec. 2.4.2): the back-side reflection probability is
+                                    the single-layer electromagnetic result instead, the reflectance of one layer of
+                                    silicon (index n + i k, k = lambda / (4 pi ell(lambda)) from the absorption-length
+                                    table) between the medium in front of the detector and vacuum behind it: the Airy
+                                    sum of its two interfaces' amplitude reflection coefficients at the photon's angle,
+                                    averaged over the s and p polarisations, with the layer's optical thickness
+                                    t_si + t_si_gx (x - x0) + t_si_gy (y - y0) at the photon's entry point (x, y) */
 #define PHOSIM_EARLY_REJECT 4u   /* dynamic transmission (Sec. 3.2): decide each coating's accept draw against
                                     the largest transmission over incidence angles at the photon's wavelength
                                     before propagating it.  The detected photons, image and moments are
@@ -111,6 +119,9 @@ typedef struct phosim_scene_desc {
     const double* sigma;        /* diffusion sigma (mm) at depths k t_si / (n_sigma - 1) below the entrance */
     double dead_layer;          /* field-free layer at the entrance (Sec. 2.4.2), mm: photons converting in it
                                    are lost; 0 = none */
+    double t_si_gx, t_si_gy;    /* PHOSIM_FRINGE: gradient of the silicon's optical thickness across the chip (mm
+                                   per mm of the detector surface frame, about the chip centre); the conversion
+                                   geometry keeps t_si */
 } phosim_scene_desc;
 
 /* One optical surface (Sec. 2.4.1, Table 1): z(r) = r^2 / (R (1 + sqrt(1 - (1 + kappa) r^2 / R^2)))

@@ -100,6 +100,9 @@ class Oracle:
         L.oracle_set_sersic(self.h, C.c_int(sr.shape[0]), C.c_int(sr.shape[1]), _dp(sr))
         L.oracle_set_sensor_options(self.h, C.c_int(int(getattr(scene, "back_reflect", False))),
                                     C.c_double(float(getattr(scene.detector, "dead_layer", 0.0))))
+        L.oracle_set_fringe(self.h, C.c_int(int(getattr(scene, "fringe", False))),
+                            C.c_double(float(getattr(scene.detector, "t_si_gx", 0.0))),
+                            C.c_double(float(getattr(scene.detector, "t_si_gy", 0.0))))
         if getattr(scene, "hf_kick", None) is not None and len(scene.hf_kick):
             hf = _arr(scene.hf_kick, np.float64)
             L.oracle_set_hf_kick(self.h, C.c_int(len(hf)), _dp(hf))
@@ -260,6 +263,14 @@ def zernike(j, rho, theta):
     out = np.zeros_like(rho)
     lib().oracle_zernike(C.c_int(j), C.c_int(len(rho)), _dp(rho), _dp(theta), _dp(out))
     return out
+
+
+def film_reflectance(lam_nm, n0, n1, k1, t_mm, s):
+    """Back-side reflection probability of the fringing calculation (single silicon layer, unpolarised)."""
+    L = lib()
+    L.oracle_film_reflectance.restype = C.c_double
+    L.oracle_film_reflectance.argtypes = [C.c_double] * 6
+    return L.oracle_film_reflectance(lam_nm, n0, n1, k1, t_mm, s)
 
 
 def bleed(image, full_well):

@@ -23,10 +23,14 @@
  *  - screen coordinate = position - wind * t; deflection = (lambda_ref / 2 pi) grad(phi) (lambda/lambda_ref)^(-1/5)
  *    with grad(phi) the bilinear interpolation of central-difference gradients;
  *  - misalignment rotation R = Rz(tz) Ry(ty) Rx(tx) about the displaced vertex;
- *  - Zernike terms in Noll's order and normalisation over the radius zern_rnorm.
+ *  - Zernike terms in Noll's order and normalisation over the radius zern_rnorm;
+ *  - the fringing back-side reflection probability is the reflectance of one absorbing silicon layer
+ *    (Airy sum of its two interfaces' amplitudes, s and p averaged) between the medium in front of the
+ *    detector and vacuum behind it, at the photon's angle, wavelength and the local layer thickness.
  * Parity pins live in tests/test_oracle_*.py; "parity unpinned" is stated there for the parts without one.
  */
 #include <algorithm>
+#include <complex>
 #include <type_traits>
 #include <cmath>
 #include <cstdint>
@@ -155,6 +159,10 @@ struct Scene {
     double pr_in = 0, pr_out = 0, h_top = 1e8, lam_ref = 500.0, z_ent = 0;
     int atm_on = 1, sensor_on = 1, back_reflect = 0;
     double dead_layer = 0.0;
+    // fringing (Sec. 2.4.2): back-side reflection from the single-layer interference calculation, with the
+    // layer's optical thickness t_si + t_gx (x - x0) + t_gy (y - y0) at the photon's position
+    int fringe = 0;
+    double t_gx = 0.0, t_gy = 0.0;
     std::vector<Surf> surf;
     std::vector<Mat> mat;
     std::vector<Coat> coat;
@@ -602,6 +610,29 @@ void sample_and_atmosphere(const Scene& sc, const Source& s, const Draws& D, Pre
     sample_and_atmosphere_t<double>(sc, s, D, P.x, P.d, P.lam, P.t);
 }
 
+// Sec. 2.4.2 fringing: the probability that a photon reaching the back of the silicon is reflected, from the
+// electromagnetic calculation for a single layer.  The layer is silicon of complex index n1 + i k1 and
+// thickness t (mm); in front of it a medium of real index n0, behind it vacuum.  s = n sin(theta) is the
+// photon's invariant (the same in every medium).  In each medium q = N cos(theta) = sqrt(N^2 - s^2); the
+// amplitude reflection coefficients of an interface from medium a to medium b are
+//   s polarisation: (q_a - q_b) / (q_a + q_b),   p polarisation: (N_b^2 q_a - N_a^2 q_b) / (N_b^2 q_a + N_a^2 q_b);
+// the layer's amplitude is the sum of the multiple reflections inside it (Airy),
+//   r = (r01 + r12 e) / (1 + r01 r12 e),  e = exp(2 i beta),  beta = (2 pi / lambda) t q1,
+// and the probability is |r|^2 averaged over the two polarisations (unpolarised light).
+double film_reflectance(double lam_nm, double n0, double n1, double k1, double t_mm, double s) {
+    typedef std::complex<double> C;
+    const C N0(n0, 0.0), N1(n1, k1), N2(1.0, 0.0), s2(s * s, 0.0);
+    const C q0 = std::sqrt(N0 * N0 - s2), q1 = std::sqrt(N1 * N1 - s2), q2 = std::sqrt(N2 * N2 - s2);
+    const C rs01 = (q0 - q1) / (q0 + q1), rs12 = (q1 - q2) / (q1 + q2);
+    const C rp01 = (N1 * N1 * q0 - N0 * N0 * q1) / (N1 * N1 * q0 + N0 * N0 * q1);
+    const C rp12 = (N2 * N2 * q1 - N1 * N1 * q2) / (N2 * N2 * q1 + N1 * N1 * q2);
+    const double lam_mm = lam_nm * 1e-6;
+    const C e = std::exp(C(0.0, 2.0) * C(2.0 * M_PI / lam_mm * t_mm, 0.0) * q1);
+    const C rs = (rs01 + rs12 * e) / (C(1.0, 0.0) + rs01 * rs12 * e);
+    const C rp = (rp01 + rp12 * e) / (C(1.0, 0.0) + rp01 * rp12 * e);
+    return 0.5 * (std::norm(rs) + std::norm(rp));
+}
+
 template <class T>
 struct OpticsOut {
     T x, y;          // final position (detector frame)
@@ -685,12 +716,24 @@ void optics_and_sensor(const Scene& sc, const std::vector<SurfT<T>>& ST, const P
                 double depth = val(deptht), L = val(Lt);
                 min_margin(out.margin_mm, depth - sc.t_si);
                 if (!(depth <= sc.t_si)) {
-                    // back-side reflection with the normal-incidence Fresnel probability of the Si/vacuum
-                    // interface; the photon converts on its way back towards the entrance
+                    // back-side reflection (Sec. 2.4.2) with the normal-incidence Fresnel probability of the
+                    // Si/vacuum interface, or with fringing the single-layer interference calculation; the
+                    // photon converts on its way back towards the entrance
                     bool back = false;
                     if (sc.back_reflect) {
-                        T rf = (n_si - T(1.0)) / (n_si + T(1.0));
-                        double r_back = val(rf * rf);
+                        double r_back;
+                        if (sc.fringe) {
+                            // the single-layer calculation at the photon's angle in the silicon, its
+                            // wavelength and the layer's thickness where it entered the chip
+                            const double ns = val(n_si), c1 = std::fabs(val(dz));
+                            const double sinv = ns * std::sqrt(std::max(0.0, 1.0 - c1 * c1));
+                            const double k1 = lam * 1e-6 / (4.0 * M_PI * val(ell));
+                            const double thick = sc.t_si + sc.t_gx * (xc - sc.x0) + sc.t_gy * (yc - sc.y0);
+                            r_back = film_reflectance(lam, val(n_cur), ns, k1, thick, sinv);
+                        } else {
+                            T rf = (n_si - T(1.0)) / (n_si + T(1.0));
+                            r_back = val(rf * rf);
+                        }
                         double u = uniform01(w_back);
                         if (std::fabs(u - r_back) < 1e-12) out.margin_mm = 0.0;
                         if (u < r_back) {
@@ -909,6 +952,15 @@ void oracle_set_sensor_options(void* p, int back_reflect, double dead_layer) {
     Scene* sc = (Scene*)p;
     sc->back_reflect = back_reflect;
     sc->dead_layer = dead_layer;
+}
+void oracle_set_fringe(void* p, int on, double t_gx, double t_gy) {
+    Scene* sc = (Scene*)p;
+    sc->fringe = on;
+    sc->t_gx = t_gx;
+    sc->t_gy = t_gy;
+}
+double oracle_film_reflectance(double lam_nm, double n0, double n1, double k1, double t_mm, double s) {
+    return film_reflectance(lam_nm, n0, n1, k1, t_mm, s);
 }
 
 // Saturation and bleeding (Sec. 2.5) on a finished image: in each half of every row, pixels above the full

@@ -438,6 +438,7 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
     if (!(d->pupil_r_out > d->pupil_r_in) || d->pupil_r_in < 0.0) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->h_top > d->z_entrance) || !is_finite(d->h_top) || !is_finite(d->z_entrance)) return PHOSIM_ERR_INVALID_ARGUMENT;
     if (!(d->dead_layer >= 0.0) || !(d->dead_layer < d->t_si)) return PHOSIM_ERR_INVALID_ARGUMENT;
+    if (!is_finite(d->t_si_gx) || !is_finite(d->t_si_gy)) return PHOSIM_ERR_INVALID_ARGUMENT;
     for (int i = 0; i < d->n_ell; ++i) if (!(d->ell[i] > 0.0) || !is_finite(d->ell[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
     for (int i = 0; i < d->n_sigma; ++i) if (!(d->sigma[i] >= 0.0) || !is_finite(d->sigma[i])) return PHOSIM_ERR_INVALID_ARGUMENT;
     phosim_scene* sc = new (std::nothrow) phosim_scene();
@@ -462,6 +463,10 @@ phosim_status phosim_create_scene(const phosim_scene_desc* d, phosim_scene** out
     P.n_ell = d->n_ell; P.n_sig = d->n_sigma;
     P.sig_scale = (d->n_sigma - 1) / d->t_si;
     P.dead_layer = d->dead_layer;
+    // fringing: optical thickness t_si + gx (x - x0) + gy (y - y0) = fr_t0 + gx x + gy y
+    P.fr_gx = d->t_si_gx; P.fr_gy = d->t_si_gy;
+    P.fr_t0 = d->t_si - d->t_si_gx * d->x0 - d->t_si_gy * d->y0;
+    P.fr_t0_s = ds_of(P.fr_t0); P.fr_gxf = (float)P.fr_gx; P.fr_gyf = (float)P.fr_gy;
     P.pr_in2_s = ds_of(P.pr_in2); P.pr_dr2_s = ds_of(P.pr_dr2);
     P.h_top_s = ds_of(P.h_top); P.z_ent_s = ds_of(P.z_ent);
     P.xlo_s = ds_of(P.xlo); P.ylo_s = ds_of(P.ylo); P.inv_pixel_s = ds_of(P.inv_pixel);

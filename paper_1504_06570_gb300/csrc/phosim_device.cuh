@@ -133,6 +133,11 @@ struct TraceParams {
     // sensor / detector
     int nx, ny, n_ell, n_sig;
     double pixel, inv_pixel, xlo, ylo, t_si, ell_lam0, inv_ell_dlam, sig_scale, dead_layer;
+    // fringing (PHOSIM_FRINGE): the silicon's optical thickness at (x, y) of the detector surface frame is
+    // fr_t0 + fr_gx x + fr_gy y
+    double fr_t0, fr_gx, fr_gy;
+    ds fr_t0_s;
+    float fr_gxf, fr_gyf;
     const double* ell;
     const float* ell32;
     const double* sig;
@@ -338,6 +343,53 @@ __device__ __forceinline__ double silicon_index(double lam_nm) {
 __device__ __forceinline__ float silicon_index_f(float lam_nm) {
     const float E = 1239.841984f / lam_nm;
     return 3.36f + 0.211f * E + 2.79f * expf((E - 3.30f) * (1.0f / 0.398f));
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Fringing (Sec. 2.4.2): the back-side reflection probability from the single-layer electromagnetic
+// calculation.  One layer of silicon (index n1 + i k1, thickness t) lies between the medium in front of the
+// detector (real index n0) and vacuum behind it; a photon travels through it with direction cosine c1 (real,
+// from its refracted direction), so its invariant is s^2 = n1^2 (1 - c1^2).  With q = N cos(theta) =
+// sqrt(N^2 - s^2) in each medium, the s and p amplitude reflection coefficients of each interface, and the
+// layer's round trip e = exp(i 4 pi t q1 / lambda), the layer reflects r = (r01 + r12 e) / (1 + r01 r12 e);
+// the probability is (|r_s|^2 + |r_p|^2) / 2.
+// ------------------------------------------------------------------------------------------------------
+struct cplx {
+    double re, im;
+};
+__device__ __forceinline__ cplx c_add(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx c_sub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx c_mul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cplx c_div(cplx a, cplx b) {
+    const double d = 1.0 / (b.re * b.re + b.im * b.im);
+    return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
+}
+// principal square root, without cancellation in the smaller part
+__device__ __forceinline__ cplx c_sqrt(cplx z) {
+    const double m = sqrt(0.5 * (hypot(z.re, z.im) + fabs(z.re)));
+    if (m == 0.0) return {0.0, 0.0};
+    if (z.re >= 0.0) return {m, 0.5 * z.im / m};
+    return {0.5 * fabs(z.im) / m, z.im < 0.0 ? -m : m};
+}
+
+static __device__ __noinline__ double film_reflectance(double lam_nm, double n0, double n1, double k1, double t, double c1) {
+    const double s2 = n1 * n1 * fmax(0.0, 1.0 - c1 * c1);
+    const cplx q0 = c_sqrt({n0 * n0 - s2, 0.0}), q2 = c_sqrt({1.0 - s2, 0.0});
+    const cplx N1sq = {n1 * n1 - k1 * k1, 2.0 * n1 * k1};
+    const cplx q1 = c_sqrt(c_sub(N1sq, {s2, 0.0}));
+    const cplx n0sq = {n0 * n0, 0.0};
+    // s and p coefficients of the front (0 -> 1) and back (1 -> vacuum) interfaces
+    const cplx rs01 = c_div(c_sub(q0, q1), c_add(q0, q1)), rs12 = c_div(c_sub(q1, q2), c_add(q1, q2));
+    const cplx rp01 = c_div(c_sub(c_mul(N1sq, q0), c_mul(n0sq, q1)), c_add(c_mul(N1sq, q0), c_mul(n0sq, q1)));
+    const cplx rp12 = c_div(c_sub(q1, c_mul(N1sq, q2)), c_add(q1, c_mul(N1sq, q2)));
+    const double w = 4.0 * M_PI * t / (lam_nm * 1e-6);
+    double sn, cs;
+    sincos(w * q1.re, &sn, &cs);
+    const double amp = exp(-w * q1.im);
+    const cplx e = {amp * cs, amp * sn};
+    const cplx rs = c_div(c_add(rs01, c_mul(rs12, e)), c_add({1.0, 0.0}, c_mul(c_mul(rs01, rs12), e)));
+    const cplx rp = c_div(c_add(rp01, c_mul(rp12, e)), c_add({1.0, 0.0}, c_mul(c_mul(rp01, rp12), e)));
+    return 0.5 * (rs.re * rs.re + rs.im * rs.im + rp.re * rp.re + rp.im * rp.im);
 }
 
 // Snell's law in vector form (Sec. 2.4.2) with mu = n1 / n2; false on total internal reflection

@@ -201,9 +201,18 @@ __device__ __forceinline__ void optics(const TraceParams& P, double X[3], double
                 if (!(depth <= P.t_si)) {
                     // back-side reflection: the photon turns round at the back and converts on its way back
                     bool back = false;
-                    if ((P.flags & PHOSIM_BACK_REFLECT) && u64of(w_back) < r_back) {
-                        depth = 2.0 * P.t_si - depth;
-                        back = depth >= 0.0;
+                    if (P.flags & PHOSIM_BACK_REFLECT) {
+                        if (P.flags & PHOSIM_FRINGE) {
+                            // fringing: the single-layer calculation in FP64 at the photon's entry point (both
+                            // the plain and the mixed path: the phase spans ~10^3 cycles)
+                            const double ell = lerp_table(P.ell, P.n_ell, (lam - P.ell_lam0) * P.inv_ell_dlam);
+                            r_back = film_reflectance(lam, n_cur, silicon_index(lam), lam * 1e-6 / (4.0 * M_PI * ell),
+                                                      P.fr_t0 + P.fr_gx * p[0] + P.fr_gy * p[1], fabs(dl[2]));
+                        }
+                        if (u64of(w_back) < r_back) {
+                            depth = 2.0 * P.t_si - depth;
+                            back = depth >= 0.0;
+                        }
                     }
                     if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
                 }

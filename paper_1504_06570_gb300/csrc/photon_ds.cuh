@@ -57,7 +57,7 @@ struct DetectorHit {
 // A bundle's ray on the detector surface, handed from the optics stage to the photons of the bundle
 struct __align__(16) DSHit {
     DetectorHit H;
-    float lam;
+    float lam, lam_lo;            // the ray's double-single wavelength
     int src;
     unsigned long long ray;
 };
@@ -497,10 +497,57 @@ __device__ __forceinline__ SensorWords sensor_words(const TraceParams& P, int sr
     return sw;
 }
 
+// Fringing (Sec. 2.4.2) in the double-single path: the single-layer calculation of film_reflectance
+// (phosim_device.cuh) with the layer's round-trip phase, about 10^3 cycles, in double-single (the wavelength,
+// the silicon index's large terms, the thickness and the direction cosine c1), and the rest in single
+// precision.  With q1 = N1 cos(theta1) = sqrt((n1 + i k1)^2 - s^2), s^2 = n1^2 (1 - c1^2): Re q1 = n1 c1 +
+// k1^2 (1 / c1^2 - 1) / (2 n1 c1) and Im q1 = k1 / c1 to second order in k1 / n1 (k1 < 1e-2 here).
+struct cfl {
+    float re, im;
+};
+__device__ __forceinline__ cfl cf_add(cfl a, cfl b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cfl cf_sub(cfl a, cfl b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cfl cf_mul(cfl a, cfl b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cfl cf_div(cfl a, cfl b) {
+    const float d = 1.f / (b.re * b.re + b.im * b.im);
+    return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
+}
+__device__ __forceinline__ cfl cf_sqrt_real(float v) {     // principal root of a real number
+    return v >= 0.f ? cfl{sqrtf(v), 0.f} : cfl{0.f, sqrtf(-v)};
+}
+
+static __device__ __noinline__ float film_reflectance_ds(const TraceParams& P, ds lam, float n0, ds c1, ds x, ds y,
+                                                          float ell) {
+    const ds E = ds_of(1239.841984) / lam;                             // photon energy, eV
+    const ds n1 = dfma(ds_of(0.211), E, ds_of(3.36)) + 2.79f * expf((E.hi - 3.30f) * (1.0f / 0.398f));
+    const ds lam_mm = lam * ds_of(1e-6);
+    const float c1f = c1.hi, n1f = n1.hi;
+    const float k1 = lam_mm.hi / (4.f * (float)M_PI * ell);
+    const ds q1r = n1 * c1 + k1 * k1 * (1.f / (c1f * c1f) - 1.f) / (2.f * n1f * c1f);
+    const float q1i = k1 / c1f;
+    const ds t = P.fr_t0_s + x * P.fr_gxf + y * P.fr_gyf;
+    const ds cycles = (t * q1r) * 2.f / lam_mm;                        // round trip: 2 t Re(q1) / lambda
+    const float f = ds_frac(cycles, ds_floor(cycles));
+    float sn, cs;
+    sincospif(2.f * f, &sn, &cs);
+    const float amp = expf(-4.f * (float)M_PI * t.hi * q1i / lam_mm.hi);
+    const cfl e = {amp * cs, amp * sn};
+    const float s2 = n1f * n1f * fmaxf(0.f, 1.f - c1f * c1f);
+    const cfl q0 = cf_sqrt_real(n0 * n0 - s2), q2 = cf_sqrt_real(1.f - s2), q1 = {q1r.hi, q1i};
+    const cfl N1sq = {n1f * n1f - k1 * k1, 2.f * n1f * k1}, n0sq = {n0 * n0, 0.f}, one = {1.f, 0.f};
+    const cfl rs01 = cf_div(cf_sub(q0, q1), cf_add(q0, q1)), rs12 = cf_div(cf_sub(q1, q2), cf_add(q1, q2));
+    const cfl rp01 = cf_div(cf_sub(cf_mul(N1sq, q0), cf_mul(n0sq, q1)), cf_add(cf_mul(N1sq, q0), cf_mul(n0sq, q1)));
+    const cfl rp12 = cf_div(cf_sub(q1, cf_mul(N1sq, q2)), cf_add(q1, cf_mul(N1sq, q2)));
+    const cfl rs = cf_div(cf_add(rs01, cf_mul(rs12, e)), cf_add(one, cf_mul(cf_mul(rs01, rs12), e)));
+    const cfl rp = cf_div(cf_add(rp01, cf_mul(rp12, e)), cf_add(one, cf_mul(cf_mul(rp01, rp12), e)));
+    return 0.5f * (rs.re * rs.re + rs.im * rs.im + rp.re * rp.re + rp.im * rp.im);
+}
+
 // The sensor and the pixel for a ray's hit on the detector surface (Sec. 2.4.2, 2.5): the detector steps of
 // optics<MIXED = true, FULL = true>, with a bundle photon's offset and draws when mb is given.
-__device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHit& H, float lam, int src, uint64_t ray,
+__device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHit& H, ds lamd, int src, uint64_t ray,
                                           PhotonOutS& R, const MemberDrawS* mb = nullptr) {
+    const float lam = lamd.hi;
     const int si = H.si;
     ds p0 = H.px, p1 = H.py;
     ds dl[3] = {H.dl[0], H.dl[1], H.dl[2]}, Nv[3] = {H.N[0], H.N[1], H.N[2]};
@@ -531,9 +578,14 @@ __device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHi
         if (!(depth <= P.t_sif)) {
             // back-side reflection: the photon turns round at the back and converts on its way back
             bool back = false;
-            if ((P.flags & PHOSIM_BACK_REFLECT) && u32of(w_back) < rf * rf) {
-                depth = 2.f * P.t_sif - depth;
-                back = depth >= 0.f;
+            if (P.flags & PHOSIM_BACK_REFLECT) {
+                const float r_back = (P.flags & PHOSIM_FRINGE) ? film_reflectance_ds(P, lamd, H.n_cur.hi, ds_abs(dl[2]),
+                                                                                    p0, p1, ell)
+                                                                : rf * rf;
+                if (u32of(w_back) < r_back) {
+                    depth = 2.f * P.t_sif - depth;
+                    back = depth >= 0.f;
+                }
             }
             if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
         }
@@ -618,7 +670,7 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
             R.flags = kHandedOff;
             return false;
         }
-        detect_ds(P, H, lam.hi, src, ray, R, mb);
+        detect_ds(P, H, lam, src, ray, R, mb);
         return false;
     }
     // clear aperture

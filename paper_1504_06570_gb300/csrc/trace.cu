@@ -538,14 +538,16 @@ __global__ void __launch_bounds__(kOpticsMaxThreads, PHOSIM_DS_OPTICS_MIN_BLOCKS
             if (go) go = surface_step_ds(P, W, lam, src, u, R, nullptr, bundled ? &H : nullptr);
         }
 #else
+        ds lam = ds_f(0.f);
         if (v) {
             const DSState st = S.state[e];
             src = st.src;
             u = st.idx;
             R.lam = st.lam;
+            lam = ds{st.lam, st.lam_lo};
             const bool bundled = P.sources[src].bundle > 1;
             const ds X[3] = {st.x, st.y, P.z_ent_s}, D[3] = {st.nx, st.ny, st.nz};
-            optics_ds(P, X, D, ds{st.lam, st.lam_lo}, src, u, R, nullptr, bundled ? &H : nullptr);
+            optics_ds(P, X, D, lam, src, u, R, nullptr, bundled ? &H : nullptr);
         }
 #endif
         // a bundle's ray that reached the detector surface hands its hit over to the bundle stage
@@ -558,7 +560,8 @@ __global__ void __launch_bounds__(kOpticsMaxThreads, PHOSIM_DS_OPTICS_MIN_BLOCKS
             if (handed) {
                 DSHit h;
                 h.H = H;
-                h.lam = R.lam;
+                h.lam = lam.hi;
+                h.lam_lo = lam.lo;
                 h.src = src;
                 h.ray = u;
                 S.hits[slot] = h;
@@ -592,7 +595,7 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_MEMBERS_MIN_BLOCKS) ds_members_
         const unsigned long long e = b + lane;
         const bool v = e < n;
         DSHit h;
-        h.src = 0; h.ray = 0; h.lam = 0.f;
+        h.src = 0; h.ray = 0; h.lam = 0.f; h.lam_lo = 0.f;
         if (v) h = S.hits[e];
         const DSource& s = P.sources[h.src];
         const uint32_t nb = v ? s.bundle : 0u;
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_MEMBERS_MIN_BLOCKS) ds_members_
             R.x = R.y = R.xc = R.yc = ds_f(0.f);
             if (vm) {
                 const MemberDrawS mb = member_draw_s(P, (float)s.bsig, h.src, lo + m);
-                detect_ds(P, h.H, h.lam, h.src, h.ray, R, &mb);
+                detect_ds(P, h.H, ds{h.lam, h.lam_lo}, h.src, h.ray, R, &mb);
             }
             account_ds(P, R, vm, h.src, lo + m, lane, cnt);
         }

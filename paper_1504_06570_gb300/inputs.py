@@ -86,6 +86,8 @@ class Detector:
     ell: np.ndarray = None
     sigma: np.ndarray = None     # diffusion sigma (mm) at depths uniformly spaced over [0, t_si]
     dead_layer: float = 0.0      # field-free layer at the entrance (mm)
+    t_si_gx: float = 0.0         # gradient of the silicon's optical thickness across the chip (mm per mm), for
+    t_si_gy: float = 0.0         # the fringing calculation: t_si + t_si_gx (x - x0) + t_si_gy (y - y0)
 
 
 @dataclass
@@ -149,6 +151,8 @@ class Scene:
     z_entrance: float = None     # plane (mm) where the raytrace starts, below every layer, above every optic
     hf_kick: np.ndarray = None   # quantiles (rad at lambda_ref) of the high-frequency kick, or None
     back_reflect: bool = False   # back-side reflection of photons that cross the silicon
+    fringe: bool = False         # with back_reflect: the reflection probability from the single-layer
+                                 # interference calculation (fringing) instead of the normal-incidence Fresnel one
 
     def __post_init__(self):
         if self.z_entrance is None:

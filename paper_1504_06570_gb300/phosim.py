@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libphosim.so")
 
 MAX_SURFACES, MAX_LAYERS, MAX_SCALES, MAX_ZERNIKE = 16, 8, 2, 28
 PLAIN_FP64, MIXED, MIXED_DS = 0, 1, 2
-ATMOSPHERE, SENSOR, EARLY_REJECT, GRAPH, BACK_REFLECT = 1, 2, 4, 8, 16
+ATMOSPHERE, SENSOR, EARLY_REJECT, GRAPH, BACK_REFLECT, FRINGE = 1, 2, 4, 8, 16, 32
 MOMENT_WORDS = 8
 F_DETECTED = 1
 
@@ -39,7 +39,7 @@ class SceneDesc(C.Structure):
                 ("pixel", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("t_si", C.c_double),
                 ("ell_lam0", C.c_double), ("ell_dlam", C.c_double), ("n_ell", C.c_int32),
                 ("ell", C.POINTER(C.c_double)), ("n_sigma", C.c_int32), ("sigma", C.POINTER(C.c_double)),
-                ("dead_layer", C.c_double)]
+                ("dead_layer", C.c_double), ("t_si_gx", C.c_double), ("t_si_gy", C.c_double)]
 
 
 class Surface(C.Structure):
@@ -175,13 +175,15 @@ class Scene:
         desc = SceneDesc(seed=scene.seed, precision=precision,
                          flags=(ATMOSPHERE if scene.atmosphere else 0) | (SENSOR if scene.sensor else 0)
                          | (EARLY_REJECT if early_reject else 0) | (GRAPH if graph else 0)
-                         | (BACK_REFLECT if getattr(scene, "back_reflect", False) else 0),
+                         | (BACK_REFLECT if getattr(scene, "back_reflect", False) else 0)
+                         | (FRINGE if getattr(scene, "fringe", False) else 0),
                          pupil_r_in=scene.pupil_r_in, pupil_r_out=scene.pupil_r_out, h_top=scene.h_top,
                          z_entrance=scene.z_entrance, lambda_ref=scene.lambda_ref, nx=d.nx, ny=d.ny, pixel=d.pixel,
                          x0=d.x0, y0=d.y0, t_si=d.t_si, ell_lam0=d.ell_lam0, ell_dlam=d.ell_dlam,
                          n_ell=len(self._ell), ell=self._ell.ctypes.data_as(C.POINTER(C.c_double)),
                          n_sigma=len(self._sig), sigma=self._sig.ctypes.data_as(C.POINTER(C.c_double)),
-                         dead_layer=float(getattr(d, "dead_layer", 0.0)))
+                         dead_layer=float(getattr(d, "dead_layer", 0.0)), t_si_gx=float(getattr(d, "t_si_gx", 0.0)),
+                         t_si_gy=float(getattr(d, "t_si_gy", 0.0)))
         h = C.c_void_p()
         _check("phosim_create_scene", L.phosim_create_scene(C.byref(desc), C.byref(h)))
         self.h = h

@@ -43,7 +43,7 @@ def test_exports_every_declared_symbol(L):
 
 def test_struct_layout_matches_header():
     """sizeof / offsetof of every ABI structure, compiled from the header with the system C compiler."""
-    checks = {"phosim_scene_desc": (P.SceneDesc, ["seed", "precision", "ell", "n_sigma", "sigma", "dead_layer"]),
+    checks = {"phosim_scene_desc": (P.SceneDesc, ["seed", "precision", "ell", "n_sigma", "sigma", "dead_layer", "t_si_gy"]),
               "phosim_surface": (P.Surface, ["R", "alpha", "pert", "zern_rnorm", "zern"]),
               "phosim_material": (P.Material, ["B", "C"]),
               "phosim_coating": (P.Coating, ["n_lambda", "table", "reflect"]),

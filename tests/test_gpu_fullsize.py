@@ -208,7 +208,12 @@ def test_batched_workload_full_launch_and_sampled_parity(oracle_mod, batched):
         if prec != P.MIXED_DS:
             scn.close()
         det_g = (r["flags"] & 1) == 1
-        assert np.all((r["flags"] == ora["flags"]) | bnd), prec
+        assert np.all((det_g == det_o) | bnd), prec
+        # losses agree too, except that the dynamic transmission test reports a photon it rejects as a
+        # coating loss even where the oracle (no early test) finds an earlier surface vignetting it
+        reason_g, reason_o = (r["flags"] >> 8) & 0xFF, (ora["flags"] >> 8) & 0xFF
+        early = (reason_g == 5) & (reason_o != 5) & ~det_o
+        assert np.all((r["flags"] == ora["flags"]) | bnd | early), prec
         both = det_g & det_o
         err = np.maximum(np.abs(r["x"][both] - ora["x"][both]), np.abs(r["y"][both] - ora["y"][both])) / d.pixel
         if prec == P.PLAIN_FP64:

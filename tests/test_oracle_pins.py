@@ -875,3 +875,98 @@ def test_bleeding_hand_worked_rows(oracle_mod):
     # right half: pixel 6 (16) gives 11: pixel 5 and 7 alternate (5, 5 after 10), pixel 4 takes the last one
     np.testing.assert_array_equal(out, [[3, 5, 5, 5, 1, 5, 5, 5]])
     assert removed == 0
+
+
+# ---------------------------------------------------------------------------------------------- Sec. 2.4.2 fringing
+def _airy(R1, delta):
+    """Reflectance of a non-absorbing layer between two equal media (Airy): F sin^2 d / (1 + F sin^2 d)."""
+    F = 4 * R1 / (1 - R1) ** 2
+    return F * np.sin(delta) ** 2 / (1 + F * np.sin(delta) ** 2)
+
+
+def test_fringing_single_layer_closed_forms(oracle_mod):
+    """Sec. 2.4.2 fringing: the back-side reflection probability is the single-layer electromagnetic result.
+    Without absorption, a layer of index n and thickness t in vacuum reflects F sin^2(d) / (1 + F sin^2(d)) of
+    each polarisation (Airy), d = 2 pi n t cos(theta1) / lambda, F = 4 R1 / (1 - R1)^2 with R1 the textbook
+    Fresnel reflectance of one interface: s: ((cos th0 - n cos th1) / (cos th0 + n cos th1))^2, p: ((n cos th0 -
+    cos th1) / (n cos th0 + cos th1))^2; unpolarised light takes the mean.  A thick absorbing layer
+    (index n + i k) returns the single interface's ((n - 1)^2 + k^2) / ((n + 1)^2 + k^2) at normal incidence."""
+    f = oracle_mod.film_reflectance
+    n, t = 3.6, 0.1
+    lam = np.linspace(990.0, 1010.0, 97)
+    for th0 in (0.0, 0.05, 0.3):
+        s = math.sin(th0)
+        c0, c1 = math.cos(th0), math.sqrt(1 - (s / n) ** 2)
+        Rs1 = ((c0 - n * c1) / (c0 + n * c1)) ** 2
+        Rp1 = ((n * c0 - c1) / (n * c0 + c1)) ** 2
+        d = 2 * np.pi * n * t * c1 / (lam * 1e-6)
+        expect = 0.5 * (_airy(Rs1, d) + _airy(Rp1, d))
+        got = np.array([f(l, 1.0, n, 0.0, t, s) for l in lam])
+        np.testing.assert_allclose(got, expect, rtol=1e-9, atol=1e-12)
+    for k in (0.01, 0.3):
+        assert abs(f(800.0, 1.0, n, k, 1.0, 0.0) - ((n - 1) ** 2 + k * k) / ((n + 1) ** 2 + k * k)) < 1e-12
+    # with absorption the fringes lose contrast: the extremes move towards the single-interface value
+    R1 = ((n - 1) / (n + 1)) ** 2
+    F = 4 * R1 / (1 - R1) ** 2
+    r_abs = [f(l, 1.0, n, 1e-3, t, 0.0) for l in lam]
+    assert max(r_abs) < F / (1 + F) and min(r_abs) > 0.0
+
+
+def test_fringing_period_in_wavelength(oracle_mod):
+    """Sec. 2.4.2 fringing with the silicon index of Sec. 2.4.1: at normal incidence and without absorption
+    the reflectance peaks where 2 n(lambda) t / lambda = m + 1/2, so neighbouring peaks are lambda^2 / (2 t n_g)
+    apart, n_g = n - lambda dn / dlambda the group index, a period that t_Si fixes."""
+    o = oracle_mod.Oracle(bare_scene([I.Surface(kind=I.DETECTOR, z=0.0, material=1)]))
+    t = 0.1
+    lam = np.linspace(899.0, 905.0, 60001)
+    n = np.array([o.index(1, l) for l in lam])
+    R = np.array([oracle_mod.film_reflectance(l, 1.0, nn, 0.0, t, 0.0) for l, nn in zip(lam, n)])
+    peaks = np.nonzero((R[1:-1] > R[:-2]) & (R[1:-1] >= R[2:]))[0] + 1
+    assert len(peaks) >= 4
+    order = 2 * n[peaks] * t / (lam[peaks] * 1e-6)
+    np.testing.assert_allclose(order - np.floor(order), 0.5, atol=2e-3)
+    l0 = lam[peaks]
+    ng = n[peaks] - l0 * np.gradient(n, lam)[peaks]
+    np.testing.assert_allclose(np.diff(l0), (l0[:-1] ** 2 / (2 * t * 1e6 * ng[:-1])), rtol=5e-3)
+
+
+def test_fringing_conversion_fraction_across_a_thickness_wedge(oracle_mod):
+    """Sec. 2.4.2: with fringing, a photon crossing the silicon (thickness t) is reflected at the back with the
+    single-layer probability R(lambda, theta, t_opt) of the layer's local optical thickness t_opt = t + g (x -
+    x0), and converts on the way back.  For a vertical beam onto a flat 20 um chip whose optical thickness rises
+    by g = 2e-4 across it (a fringe every lambda / (2 n g) ~ 0.7 mm), the converted fraction in each strip of
+    the chip equals the mean over its photons of P(L <= t) + R P(t < L <= 2 t), L exponential of mean ell(lambda)
+    (binomial 4 sigma), and the strips' fractions differ by far more than that (the fringe pattern)."""
+    n_ph, t, g = 120000, 0.02, 2e-4
+    surfaces = [I.Surface(kind=I.DETECTOR, z=0.0, material=1)]
+    sc = bare_scene(surfaces, sensor=True, lam_lo=1000.0, lam_hi=1001.0, pupil=(0.0, 1.2), t_si=t,
+                    n_photons=n_ph)
+    sc.back_reflect = True
+    sc.fringe = True
+    sc.detector.t_si_gx = g
+    o = oracle_mod.Oracle(sc)
+    rec = o.trace(n_threads=8)
+    pos, d, lam, _ = o.pre_optics(0, 0, n_ph)
+    assert np.allclose(lam, rec["lam"]) and np.allclose(d[:, :2], 0.0)
+    x = pos[:, 0]
+    ell = np.interp(lam, sc.detector.ell_lam0 + np.arange(len(sc.detector.ell)), sc.detector.ell)
+    nsi = np.array([o.index(1, l) for l in lam])
+    R = np.array([oracle_mod.film_reflectance(l, 1.0, nn, l * 1e-6 / (4 * np.pi * e), t + g * xx, 0.0)
+                  for l, nn, e, xx in zip(lam, nsi, ell, x)])
+    p = (1 - np.exp(-t / ell)) + R * (np.exp(-t / ell) - np.exp(-2 * t / ell))
+    det = (rec["flags"] & 1) == 1
+    edges = np.linspace(-1.2, 1.2, 13)
+    strip = np.digitize(x, edges) - 1
+    fr, pr = [], []
+    for k in range(12):
+        m = strip == k
+        fr.append(det[m].mean()); pr.append(p[m].mean())
+        sig = np.sqrt(pr[-1] * (1 - pr[-1]) / m.sum())
+        assert abs(fr[-1] - pr[-1]) < 4 * sig + 1e-3, (k, fr[-1], pr[-1])
+    assert max(pr) - min(pr) > 0.02          # ~ 8 sigma of one strip
+    # without fringing the same photons follow the normal-incidence Fresnel probability
+    sc.fringe = False
+    rec2 = oracle_mod.Oracle(sc).trace(n_threads=8)
+    R0 = ((nsi - 1) / (nsi + 1)) ** 2
+    p0 = (1 - np.exp(-t / ell)) + R0 * (np.exp(-t / ell) - np.exp(-2 * t / ell))
+    assert abs(((rec2["flags"] & 1) == 1).mean() - p0.mean()) < 4 * np.sqrt(p0.mean() * (1 - p0.mean()) / n_ph)
