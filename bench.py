@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the 1e8-star, background and adjoint legs")
     ap.add_argument("--stars-photons", type=float, default=1e8, help="photons of the 1000-star extra leg")
+    ap.add_argument("--no-fp64-arms", action="store_true", help="time the headline path only (profiling runs)")
+    ap.add_argument("--schedule", default=None, help="threads,tile for every path instead of the autotuner")
     ap.add_argument("--fine-n", type=int, default=4096, help="fine screen size (smaller: profiling case)")
     ap.add_argument("--coarse-n", type=int, default=1024, help="coarse screen size (smaller: profiling case)")
     return ap.parse_args()
@@ -124,8 +126,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "launches_three_mirror_1e8.md")
-INST_PROFILE = os.path.join(ROOT, "profiles", "ds_stages_three_mirror_2e7.md")
+TRAFFIC_PROFILE = INST_PROFILE = None       # every committed summary under profiles/
 KERNEL_SOURCES = ("paper_1504_06570_gb300/csrc/photon.cuh", "paper_1504_06570_gb300/csrc/trace.cu",
                   "paper_1504_06570_gb300/csrc/phosim_device.cuh", "paper_1504_06570_gb300/csrc/photon_ds.cuh",
                   "paper_1504_06570_gb300/csrc/ds.cuh")
@@ -141,13 +142,16 @@ def kernel_source_hash():
 
 
 def _profile_records(path, tag):
-    """(kernel, workload, value, photons, sources hash) of the `tag` lines of a committed ncu summary; lines
-    without a workload field belong to the 1000-star workload."""
+    """(kernel, workload, value, photons, sources hash) of the `tag` lines of the committed ncu summaries
+    (every profiles/*.md when path is None); lines without a workload field belong to the 1000-star workload."""
+    import glob
     import re
-    try:
-        text = open(os.path.join(ROOT, "profiles", path) if not os.path.isabs(path) else path).read()
-    except OSError:
-        return []
+    text = ""
+    for f in ([path] if path else sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))):
+        try:
+            text += open(f).read() + "\n"
+        except OSError:
+            pass
     pat = tag + r": kernel=(\S+)(?: workload=(\S+))? \w+=(\d+) photons=(\d+) kernel_sources=([0-9a-f]+)"
     return [(m.group(1), m.group(2) or "stars", int(m.group(3)), int(m.group(4)), m.group(5))
             for m in re.finditer(pat, text)]
@@ -489,11 +493,18 @@ def main():
     # every path with the paper's dynamic transmission (early coating rejection), which leaves the detected
     # photons unchanged, and its launch shape picked by the autotuner on a sample of this workload
     head = P.Scene(sc, P.MIXED_DS, early_reject=True, graph=True)
-    other = P.Scene(sc, P.MIXED, early_reject=True, graph=True)
-    plain = P.Scene(sc, P.PLAIN_FP64, early_reject=True)
+    arms = {"mixed_ds": head}
+    if not args.no_fp64_arms:
+        arms["mixed_fp64_optics"] = P.Scene(sc, P.MIXED, early_reject=True, graph=True)
+        arms["plain_fp64"] = P.Scene(sc, P.PLAIN_FP64, early_reject=True)
     tuned = {}
-    for name, scn in (("mixed_ds", head), ("mixed_fp64_optics", other), ("plain_fp64", plain)):
-        tuned[name] = scn.autotune(sample_photons=20_000_000, n_photons=counts, stream=stream.cuda_stream)
+    for name, scn in arms.items():
+        if args.schedule:
+            scn.set_schedule(*[int(v) for v in args.schedule.split(",")])
+            tuned[name] = scn.schedule()
+        else:
+            tuned[name] = scn.autotune(sample_photons=20_000_000, n_photons=counts, stream=stream.cuda_stream)
+    other, plain = arms.get("mixed_fp64_optics"), arms.get("plain_fp64")
     setup_s = time.perf_counter() - t_setup
     d = sc.detector
     img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
@@ -533,8 +544,8 @@ def main():
     clocks.start()
     per_head = timed(head, args.steps, args.warmup, moms["mixed_ds"], on_start=clocks.mark)
     clock_rec = clocks.stop()
-    per_other = timed(other, args.plain_steps, 1, moms["mixed_fp64_optics"])
-    per_plain = timed(plain, args.plain_steps, 1, moms["plain_fp64"])
+    per_other = timed(other, args.plain_steps, 1, moms["mixed_fp64_optics"]) if other else np.array([np.nan])
+    per_plain = timed(plain, args.plain_steps, 1, moms["plain_fp64"]) if plain else np.array([np.nan])
     kt = stage_times(head, img, None, counts, first, stream, 2)
 
     # e2e through the C ABI with host buffers: every step copies in a pinned host image (and the source list
@@ -581,7 +592,8 @@ def main():
     job["consistent"] = job["image_sum"] == job["detected"] and job["moment_count_sum"] == float(job["detected"])
 
     if rank != 0:
-        head.close(); other.close(); plain.close()
+        for scn in arms.values():
+            scn.close()
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
@@ -598,13 +610,14 @@ def main():
                        "schedule": {"autotuned": tuned}, "parallelism": f"photon ranges x{world}",
                        "l2": "inputs larger than L2 (gradient screens 3.8 GB single precision, swept by the wind)",
                        "setup_s": round(setup_s, 1)},
-            "mixed_fp64_optics": {"value": other_value, "unit": "photons/s",
+            "mixed_fp64_optics": None if other is None else {"value": other_value, "unit": "photons/s",
                                   "ms_per_step": t_other / args.plain_steps * 1e3,
                                   "precision": "mixed, FP64 positions/directions/transforms/intersections/wavelength, "
                                                "FP32 deflections/sensor"},
-            "plain_fp64": {"value": plain_value, "unit": "photons/s", "ms_per_step": t_plain / args.plain_steps * 1e3,
-                           "speedup_of_headline": value / plain_value},
-            "moments_vs_plain_fp64": {
+            "plain_fp64": None if plain is None else {"value": plain_value, "unit": "photons/s",
+                                                      "ms_per_step": t_plain / args.plain_steps * 1e3,
+                                                      "speedup_of_headline": value / plain_value},
+            "moments_vs_plain_fp64": None if plain is None else {
                 "mixed_ds": moments_vs_fp64(sums["mixed_ds"], sums["plain_fp64"], runs=args.warmup + args.steps,
                                             runs_fp64=1 + args.plain_steps),
                 "mixed_fp64_optics": moments_vs_fp64(sums["mixed_fp64_optics"], sums["plain_fp64"],
@@ -655,30 +668,31 @@ def main():
             "entry_gather_gbs": work["gather_bytes"] / (kt["entry"] / 1e3) / 1e9 if kt["entry"] else None,
             "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}
         # native-FP64 mixed kernel: the same operations against the FP64 FMA rate
-        kt_other = stage_times(other, img, None, counts, first, stream, 1)
         peak64 = fp64_rate or FP64_NOMINAL_TFLOPS
-        line["roofline_mixed_fp64_optics"] = {
-            "bound": "alu", "kernel": "trace_kernel<1>", "kernel_ms": kt_other["one_kernel"],
-            "achieved": fl_opt / (kt_other["one_kernel"] / 1e3) / 1e12, "peak": peak64, "unit": "TFLOP/s",
-            "note": "the oracle's optics operations per launch over the kernel's time; peak = " +
-                    ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)")}
-        line["roofline_mixed_fp64_optics"]["frac"] = line["roofline_mixed_fp64_optics"]["achieved"] / peak64
-        line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) / (t_plain / args.plain_steps) / 1e12,
-                                       "peak": peak64, "unit": "TFLOP/s"}
-        line["roofline_plain_fp64"]["frac"] = line["roofline_plain_fp64"]["achieved"] / peak64
+        if other is not None:
+            kt_other = stage_times(other, img, None, counts, first, stream, 1)
+            line["roofline_mixed_fp64_optics"] = {
+                "bound": "alu", "kernel": "trace_kernel<1>", "kernel_ms": kt_other["one_kernel"],
+                "achieved": fl_opt / (kt_other["one_kernel"] / 1e3) / 1e12, "peak": peak64, "unit": "TFLOP/s",
+                "note": "the oracle's optics operations per launch over the kernel's time; peak = " +
+                        ("measured FP64 FMA rate" if fp64_rate else "nominal FP64 (fallback)")}
+            line["roofline_mixed_fp64_optics"]["frac"] = line["roofline_mixed_fp64_optics"]["achieved"] / peak64
+        if plain is not None:
+            line["roofline_plain_fp64"] = {"achieved": (fl_opt + fl_pre) / (t_plain / args.plain_steps) / 1e12,
+                                           "peak": peak64, "unit": "TFLOP/s"}
+            line["roofline_plain_fp64"]["frac"] = line["roofline_plain_fp64"]["achieved"] / peak64
         cpu, rec, cnt = cpu_leg(sc, args.sample)
         line["cpu_baseline"] = cpu
         errs = {}
-        for name, scn in (("mixed_ds", head), ("mixed_fp64_optics", other), ("plain_fp64", plain)):
+        for name, scn in arms.items():
             m2 = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
             i2 = torch.zeros((d.ny, d.nx), dtype=torch.int32, device=dev)
             scn.trace(i2, None, m2, n_photons=cnt)
             torch.cuda.synchronize(dev)
             errs[name] = moment_errors(m2.cpu().numpy(), rec, n_src)
         line["moment_error_vs_oracle"] = errs
-    head.close()
-    other.close()
-    plain.close()
+    for scn in arms.values():
+        scn.close()
     if not args.no_extras:
         line["stars_1e8"], sc_stars = stars_leg(args, dev, stream)
         line["background_bundles"] = background_leg(sc_stars.layers, dev, stream, P.MIXED_DS)
