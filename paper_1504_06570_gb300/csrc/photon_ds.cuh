@@ -267,12 +267,29 @@ __device__ __forceinline__ bool sag_f(const DSurfaceS& E, int flags, float x, fl
     return true;
 }
 
+// The unit normal of a conic at a point (x, y, z) on it: (-c x, -c y, 1 - kc z) normalised.  For a sphere
+// (kappa = 0, kc = c) that vector's squared length is 1 + c Q with Q = c (x^2 + y^2) + c z^2 - 2 z the quadric,
+// which vanishes at the intersection: it is already a unit vector (to the root's 1e-14) and needs no root.
+__device__ __forceinline__ void conic_normal_ds(const DSurfaceS& E, ds x, ds y, ds z, ds N[3]) {
+    const ds vx = -(E.c * x), vy = -(E.c * y), vz = ds_f(1.f) - E.kc * z;
+    if (E.kmc.hi == 0.f) {
+        N[0] = vx; N[1] = vy; N[2] = vz;
+        return;
+    }
+    const ds inv = ds_rsqrt(dfma(vx, vx, dfma(vy, vy, vz * vz)));
+    N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
+}
+
 // Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
 // vertex branch, then Newton's method for the aspheric and Zernike terms until the step is below 1e-8 mm.
-// Newton converges to the same root from any start close enough to it, so for the aspheric and Zernike
-// surfaces the start (the conic's root, then Newton steps while they exceed 10 um: the asphere moves the root
-// by up to millimetres) is computed in single precision, and the double-single steps only take it from
-// there to the final 1e-8 mm.
+// Newton converges to the same root from any start close enough to it, so the start is computed in single
+// precision: the conic's root, then for the aspheric and Zernike surfaces Newton steps while they exceed 10 um
+// (the asphere moves the root by up to millimetres).  For those, the double-single Newton steps take it from
+// there to the final 1e-8 mm; for a plain conic one double-single Newton step on the quadric Q = c (x^2 + y^2) +
+// kc z^2 - 2 z along the ray does: from a single-precision root (error below 1e-3 mm for the paths here) it
+// leaves an error of about (Q'' / 2 Q') e^2 ~ c e^2, below 1e-10 mm (Q', which only scales the step, in single
+// precision).  A ray whose single-precision discriminant is not clearly positive (grazing or missing the
+// conic) takes the double-single root.
 static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
                                                  ds N[3]) {
     if (flags & SF_FLAT_ONLY) {
@@ -283,8 +300,6 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
     }
     const bool newton = (flags & (SF_EVEN | SF_ODD | SF_ZERN)) != 0;
     if (newton) {
-        // the conic's root in single precision; a ray whose discriminant is not clearly positive (grazing or
-        // missing the conic) takes the double-single root below
         const float c = E.c.hi, kc = E.kc.hi;
         const float Af = fmaf(E.kmc.hi * d[2].hi, d[2].hi, c);
         const float bf = fmaf(kc * p[2].hi, d[2].hi, c * fmaf(p[0].hi, d[0].hi, p[1].hi * d[1].hi)) - d[2].hi;
@@ -311,6 +326,29 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
                 return newton_ds(E, flags, p, d, l, N);
             }
         }
+    } else {
+        const float c = E.c.hi, kc = E.kc.hi;
+        const float Af = fmaf(E.kmc.hi * d[2].hi, d[2].hi, c);
+        const float bf = fmaf(kc * p[2].hi, d[2].hi, c * fmaf(p[0].hi, d[0].hi, p[1].hi * d[1].hi)) - d[2].hi;
+        const float Cf = fmaf(kc * p[2].hi, p[2].hi, c * fmaf(p[0].hi, p[0].hi, p[1].hi * p[1].hi)) - 2.f * p[2].hi;
+        const float disc = fmaf(bf, bf, -(Af * Cf));
+        if (disc > 1e-6f * bf * bf) {
+            const float sq = sqrtf(disc);
+            const float qf = bf >= 0.f ? -(bf + sq) : sq - bf;
+            float lf = Cf / qf;
+            if (Af != 0.f && fmaf(-kc, fmaf(lf, d[2].hi, p[2].hi), 1.f) < 0.f) lf = qf / Af;
+            if (fabsf(lf) < 1e30f) {
+                l = ds_f(lf);
+                const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]), z = dfma(l, d[2], p[2]);
+                const ds Q = dfma(E.c, dfma(x, x, y * y), dfma(E.kc * z, z, z * -2.f));
+                const float dQ = 2.f * (fmaf(c, fmaf(x.hi, d[0].hi, y.hi * d[1].hi), kc * z.hi * d[2].hi) - d[2].hi);
+                if (dQ != 0.f) {
+                    l = l - Q.hi / dQ;
+                    conic_normal_ds(E, dfma(l, d[0], p[0]), dfma(l, d[1], p[1]), dfma(l, d[2], p[2]), N);
+                    return 0;
+                }
+            }
+        }
     }
     // the quadric's l^2 coefficient c (d_x^2 + d_y^2) + kc d_z^2, which for the unit direction is c + (kc - c) d_z^2
     const ds A = dfma(E.kmc * d[2], d[2], E.c);
@@ -324,10 +362,7 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
     l = C / q;
     if (A.hi != 0.f && (ds_f(1.f) - E.kc * dfma(l, d[2], p[2])).hi < 0.f) l = q / A;
     if (newton) return newton_ds(E, flags, p, d, l, N);
-    const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]), z = dfma(l, d[2], p[2]);
-    const ds vx = -(E.c * x), vy = -(E.c * y), vz = ds_f(1.f) - E.kc * z;
-    const ds inv = ds_rsqrt(dfma(vx, vx, dfma(vy, vy, vz * vz)));
-    N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
+    conic_normal_ds(E, dfma(l, d[0], p[0]), dfma(l, d[1], p[1]), dfma(l, d[2], p[2]), N);
     return 0;
 }
 
