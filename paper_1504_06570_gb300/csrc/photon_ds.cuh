@@ -709,8 +709,16 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
         return false;
     }
     // clear aperture
-    const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
-    if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return false; }
+    {   // decided in single precision unless the radius is within 1e-5 (relative) of a bound
+        const float r2f = fmaf(p[0].hi, p[0].hi, p[1].hi * p[1].hi);
+        const float ro = E.r_out2.hi, ri = E.r_in2.hi;
+        if (fabsf(r2f - ro) > 1e-5f * ro && fabsf(r2f - ri) > 1e-5f * ri) {
+            if (!(r2f <= ro && r2f >= ri)) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return false; }
+        } else {
+            const ds r2 = dfma(p[0], p[0], p[1] * p[1]);
+            if (!(ds_le(r2, E.r_out2) && ds_le(E.r_in2, r2))) { R.flags = lost(PHOSIM_LOST_VIGNETTED, si); return false; }
+        }
+    }
     // coating accept-reject at the incidence angle and wavelength
     if (S.coat_slot >= 0) {
         const DCoating& C = P.coat[S.coating];
