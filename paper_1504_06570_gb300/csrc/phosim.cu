@@ -5,6 +5,7 @@
 // photon-number cumulative SED tables (Sec. 2.2), surface frames and Zernike figures as monomials
 // (Sec. 2.4.1).  phosim_trace uploads the source list and launches one persistent trace kernel.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -311,60 +312,68 @@ phosim_status timing_pair(phosim_scene* sc, int kind, cudaEvent_t* a, cudaEvent_
     return PHOSIM_OK;
 }
 
-// one kernel launch of a captured sequence
-struct KernelLaunch {
+// one step of a trace call's launch sequence: a kernel launch (func set) or a memset to zero (func null)
+struct LaunchOp {
     const void* func;
     dim3 grid, block;
     void** args;
+    void* dst;
+    size_t bytes;
 };
 
-// Launch a fixed sequence of kernels as one CUDA graph: captured once per slot on a private stream, then
+// Launch a trace call's sequence as one CUDA graph: built node by node (each depending on the one before) when
+// the sequence's shape (its kernels and memsets) differs from the scene's cached graph for this slot, then
 // replayed on the caller's stream with this call's kernel parameters and launch shapes.
-phosim_status launch_graph(phosim_scene* sc, int slot, const KernelLaunch* L, int n, cudaStream_t st) {
+phosim_status launch_graph(phosim_scene* sc, int slot, const std::vector<LaunchOp>& ops, cudaStream_t st) {
     TraceGraph& g = sc->graphs[slot];
-    if (n > kMaxGraphNodes) return PHOSIM_ERR_LIMIT;
-    bool same = g.exec && g.n == n;
-    for (int i = 0; same && i < n; ++i) same = g.func[i] == L[i].func;
+    const size_t n = ops.size();
+    bool same = g.exec && g.func.size() == n;
+    for (size_t i = 0; same && i < n; ++i)
+        same = g.func[i] == ops[i].func && g.memset_dst[i] == (ops[i].func ? nullptr : ops[i].dst) &&
+               g.memset_bytes[i] == (ops[i].func ? 0 : ops[i].bytes);
     if (g.exec && !same) destroy_graph(g);
     if (!g.exec) {
-        if (!sc->capture_stream) CU(cudaStreamCreateWithFlags(&sc->capture_stream, cudaStreamNonBlocking));
-        CU(cudaStreamBeginCapture(sc->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (int i = 0; i < n && e == cudaSuccess; ++i)
-            e = cudaLaunchKernel(L[i].func, L[i].grid, L[i].block, L[i].args, 0, sc->capture_stream);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(sc->capture_stream, &graph);
-        if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
-            if (graph) cudaGraphDestroy(graph);
-            (void)cudaGetLastError();
-            return PHOSIM_ERR_CUDA;
+        if (cudaGraphCreate(&g.graph, 0) != cudaSuccess) { (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+        cudaGraphNode_t prev = nullptr;
+        for (size_t i = 0; i < n; ++i) {
+            const LaunchOp& o = ops[i];
+            cudaGraphNode_t node = nullptr;
+            cudaError_t e;
+            if (o.func) {
+                cudaKernelNodeParams kp = {};
+                kp.func = (void*)o.func;
+                kp.gridDim = o.grid;
+                kp.blockDim = o.block;
+                kp.kernelParams = o.args;
+                e = cudaGraphAddKernelNode(&node, g.graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            } else {
+                cudaMemsetParams mp = {};
+                mp.dst = o.dst;
+                mp.value = 0;
+                mp.elementSize = 4;
+                mp.width = o.bytes / 4;
+                mp.height = 1;
+                mp.pitch = 0;
+                e = cudaGraphAddMemsetNode(&node, g.graph, prev ? &prev : nullptr, prev ? 1 : 0, &mp);
+            }
+            if (e != cudaSuccess) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
+            g.func.push_back(o.func);
+            g.memset_dst.push_back(o.func ? nullptr : o.dst);
+            g.memset_bytes.push_back(o.func ? 0 : o.bytes);
+            g.node.push_back(node);
+            prev = node;
         }
-        g.graph = graph;
-        g.n = n;
-        for (int i = 0; i < n; ++i) g.func[i] = L[i].func;
         if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
-        size_t cnt = 0;
-        cudaGraphGetNodes(g.graph, nullptr, &cnt);
-        std::vector<cudaGraphNode_t> nodes(cnt);
-        cudaGraphGetNodes(g.graph, nodes.data(), &cnt);
-        for (cudaGraphNode_t node : nodes) {
-            cudaGraphNodeType t;
-            if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
-            cudaKernelNodeParams kp;
-            if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) continue;
-            for (int i = 0; i < n; ++i)
-                if (kp.func == L[i].func) g.node[i] = node;
+    } else {
+        for (size_t i = 0; i < n; ++i) {
+            if (!ops[i].func) continue;
+            cudaKernelNodeParams kp = {};
+            kp.func = (void*)ops[i].func;
+            kp.gridDim = ops[i].grid;
+            kp.blockDim = ops[i].block;
+            kp.kernelParams = ops[i].args;
+            CU(cudaGraphExecKernelNodeSetParams(g.exec, g.node[i], &kp));
         }
-        for (int i = 0; i < n; ++i)
-            if (!g.node[i]) { destroy_graph(g); (void)cudaGetLastError(); return PHOSIM_ERR_CUDA; }
-    }
-    for (int i = 0; i < n; ++i) {
-        cudaKernelNodeParams kp = {};
-        kp.func = (void*)L[i].func;
-        kp.gridDim = L[i].grid;
-        kp.blockDim = L[i].block;
-        kp.kernelParams = L[i].args;
-        CU(cudaGraphExecKernelNodeSetParams(g.exec, g.node[i], &kp));
     }
     CU(cudaGraphLaunch(g.exec, st));
     return PHOSIM_OK;
@@ -1090,9 +1099,10 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     if (!staged) {
         void* trace_args[1] = {&P};
         if (use_graph) {
-            const KernelLaunch L[2] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
-                                       {trace_kernel_ptr(mode), dim3((unsigned)blocks), dim3((unsigned)sc->threads), trace_args}};
-            phosim_status gs = launch_graph(sc, mode, L, 2, st);
+            const std::vector<LaunchOp> ops = {
+                {chief_kernel_ptr(), chief_grid, chief_block, chief_args, nullptr, 0},
+                {trace_kernel_ptr(mode), dim3((unsigned)blocks), dim3((unsigned)sc->threads), trace_args, nullptr, 0}};
+            phosim_status gs = launch_graph(sc, mode, ops, st);
             if (gs != PHOSIM_OK) return gs;
         } else {
             phosim_status ls = timed(0, [&] { return launch_chief_rays(P, sc->d_src, n_src, moments, st); });
@@ -1112,18 +1122,35 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
         const dim3 block((unsigned)sc->threads);
         const bool bundles = bundled_units > 0;
         void* reduce_args[1] = {&P};
-        const KernelLaunch reduce = {moment_stripes_kernel_ptr(), dim3((unsigned)((n_src * 6 + 255) / 256)), dim3(256),
-                                     reduce_args};
-        if (use_graph && chunk_tiles >= n_tiles) {
-            KernelLaunch L[5] = {{chief_kernel_ptr(), chief_grid, chief_block, chief_args},
-                                 {ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, stage_args},
-                                 {ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics),
-                                  dim3((unsigned)ds_optics_threads(sc->threads)), stage_args},
-                                 {ds_members_kernel_ptr(), dim3((unsigned)blocks_members), block, stage_args},
-                                 reduce};
-            int n_nodes = bundles ? 4 : 3;
-            if (striped) L[n_nodes++] = reduce;
-            phosim_status gs = launch_graph(sc, mode, L, n_nodes, st);
+        const LaunchOp reduce = {moment_stripes_kernel_ptr(), dim3((unsigned)((n_src * 6 + 255) / 256)), dim3(256),
+                                 reduce_args, nullptr, 0};
+        if (use_graph) {
+            // the whole call as one graph: chief rays; per chunk the counter resets (after the first), the entry,
+            // optics and bundle stages; the moment-stripe sum
+            const uint64_t n_chunks = (n_tiles + chunk_tiles - 1) / chunk_tiles;
+            std::vector<DSStage> stages((size_t)n_chunks, S);
+            std::vector<std::array<void*, 2>> chunk_args((size_t)n_chunks);
+            std::vector<LaunchOp> ops;
+            ops.reserve((size_t)n_chunks * 5 + 2);
+            ops.push_back({chief_kernel_ptr(), chief_grid, chief_block, chief_args, nullptr, 0});
+            for (uint64_t c = 0; c < n_chunks; ++c) {
+                DSStage& Sc = stages[(size_t)c];
+                Sc.tile_begin = c * chunk_tiles;
+                Sc.tile_end = std::min(n_tiles, Sc.tile_begin + chunk_tiles);
+                chunk_args[(size_t)c] = {&P, &Sc};
+                void** a = chunk_args[(size_t)c].data();
+                if (c > 0) {
+                    ops.push_back({nullptr, dim3(), dim3(), nullptr, sc->d_counters, sizeof(unsigned long long)});
+                    ops.push_back({nullptr, dim3(), dim3(), nullptr, sc->d_counters + kStateCountWord,
+                                   3 * sizeof(unsigned long long)});
+                }
+                ops.push_back({ds_entry_kernel_ptr(), dim3((unsigned)blocks), block, a, nullptr, 0});
+                ops.push_back({ds_optics_kernel_ptr(), dim3((unsigned)blocks_optics),
+                               dim3((unsigned)ds_optics_threads(sc->threads)), a, nullptr, 0});
+                if (bundles) ops.push_back({ds_members_kernel_ptr(), dim3((unsigned)blocks_members), block, a, nullptr, 0});
+            }
+            if (striped) ops.push_back(reduce);
+            phosim_status gs = launch_graph(sc, mode, ops, st);
             if (gs != PHOSIM_OK) return gs;
         } else {
             phosim_status ls = timed(0, [&] { return launch_chief_rays(P, sc->d_src, n_src, moments, st); });

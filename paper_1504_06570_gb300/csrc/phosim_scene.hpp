@@ -6,16 +6,17 @@
 #include "phosim_device.cuh"
 #include "photon_ds.cuh"
 
-// One captured [chief rays, trace] launch pair, replayed with updated kernel parameters.
-// One captured sequence of kernel launches ([chief rays, trace] or [chief rays, entry, optics(, bundles)]), replayed
-// with each call's kernel parameters and launch shapes.
-constexpr int kMaxGraphNodes = 6;
+// One trace call's launch sequence as a CUDA graph: kernels ([chief rays, trace], or chief rays, then per chunk of
+// the two-kernel path the entry, optics and bundle stages, then the moment-stripe sum) and the counter resets
+// between chunks, one node each in launch order.  Built once for a sequence's shape and replayed with each
+// call's kernel parameters and launch shapes.
 struct TraceGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int n = 0;
-    const void* func[kMaxGraphNodes] = {};      // the kernels the graph was captured with, in order
-    cudaGraphNode_t node[kMaxGraphNodes] = {};
+    std::vector<const void*> func;              // per node: the kernel, or null for a memset
+    std::vector<void*> memset_dst;              // per node: the memset's destination (null for a kernel)
+    std::vector<size_t> memset_bytes;
+    std::vector<cudaGraphNode_t> node;
 };
 
 struct phosim_scene {

@@ -250,3 +250,37 @@ def test_batched_workload_moments_double_single_vs_fp64(batched):
     assert np.all(np.abs(T / Tp - 1)[ok] < 1e-3)
     assert np.all(np.abs((g[:, 3] - g[:, 5]) / T - (gp[:, 3] - gp[:, 5]) / Tp)[ok] < 1e-3)
     assert np.all(np.abs(2 * g[:, 4] / T - 2 * gp[:, 4] / Tp)[ok] < 1e-3)
+
+
+def test_multi_chunk_launch_as_one_graph():
+    """PHOSIM_GRAPH with a launch of several chunks of the state buffer (2^27 work units each): the whole call
+    (chief rays; per chunk the counter resets, the entry, optics and bundle stages; the moment-stripe sum) is one
+    CUDA graph, rebuilt when the number of chunks or the kernel list changes and otherwise replayed with the
+    call's parameters.  Every call gives the image, counters and moment sums of the same call launched kernel by
+    kernel: two calls in a row on the batched workload (1.95e8 photons, sky in rays of 8, two chunks), a
+    one-chunk call, and the two-chunk call again."""
+    sc = I.batched_scene(fine_n=256, coarse_n=64, photon_scale=0.02)
+    counts = sc.sources.n_photons.astype(np.uint64)
+    d = sc.detector
+    ref = P.Scene(sc, P.MIXED_DS, early_reject=True)
+    gr = P.Scene(sc, P.MIXED_DS, early_reject=True, graph=True)
+
+    def run(s, cnt):
+        img = torch.zeros((d.ny, d.nx), dtype=torch.int32, device="cuda")
+        mom = torch.zeros((len(cnt), P.MOMENT_WORDS), dtype=torch.float64, device="cuda")
+        s.trace(img, None, mom, n_photons=cnt)
+        torch.cuda.synchronize()
+        return img.cpu().numpy(), s.counters(), mom.cpu().numpy()
+
+    small = np.minimum(counts, np.uint64(2000))
+    bundle = np.maximum(1, sc.sources.bundle).astype(np.uint64)
+    units = int(((counts + bundle - np.uint64(1)) // bundle).sum())
+    assert units > (1 << 27) and int(small.sum()) < (1 << 27)
+    for cnt in (counts, counts, small, counts):
+        a, b = run(ref, cnt), run(gr, cnt)
+        assert np.array_equal(a[0], b[0])
+        assert np.array_equal(a[1], b[1])
+        assert int(b[1][0]) == int(cnt.sum()) and int(b[1][1]) == int(b[0].sum())
+        np.testing.assert_allclose(b[2], a[2], rtol=1e-12, atol=1e-12)
+    ref.close()
+    gr.close()
