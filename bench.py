@@ -582,14 +582,7 @@ def main():
     job_mom = torch.zeros((n_src, P.MOMENT_WORDS), dtype=torch.float64, device=dev)
     head.trace(img, None, job_mom, n_photons=counts, first=first, stream=stream.cuda_stream)
     torch.cuda.synchronize(dev)
-    det = torch.tensor([float(head.counters()[1])], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(img, op=dist.ReduceOp.SUM)
-        dist.all_reduce(job_mom, op=dist.ReduceOp.SUM)
-        dist.all_reduce(det, op=dist.ReduceOp.SUM)
-    job = {"ranks": world, "detected": int(det.item()), "image_sum": int(img.to(torch.int64).sum().item()),
-           "moment_count_sum": float(job_mom[:, 0].sum().item())}
-    job["consistent"] = job["image_sum"] == job["detected"] and job["moment_count_sum"] == float(job["detected"])
+    job = sharding.reduce_job(img, job_mom, int(head.counters()[1]))
 
     if rank != 0:
         for scn in arms.values():
