@@ -69,9 +69,11 @@ enum {
 /* scene flags */
 #define PHOSIM_ATMOSPHERE 1u     /* apply the phase-screen layers */
 #define PHOSIM_SENSOR 2u         /* silicon conversion and diffusion; otherwise the detector-surface hit */
-#define PHOSIM_GRAPH 8u          /* launch the chief-ray and trace kernels of phosim_trace as one CUDA graph,
-                                    captured on the first call (per precision) and replayed with each call's
-                                    parameters */
+#define PHOSIM_GRAPH 8u          /* launch each phosim_trace call's kernels as one CUDA graph: the chief rays and the
+                                    trace kernel, or in the two-kernel double-single path the chief rays, then per
+                                    chunk of the state buffer the counter resets and the entry, optics and bundle
+                                    stages, then the moment-stripe sum.  Built on the first call of a given shape
+                                    (number of chunks, kernel list) and replayed with each call's parameters */
 #define PHOSIM_BACK_REFLECT 16u  /* back-side reflection (Sec. 2.4.2): a photon whose conversion length takes it
                                     past the back of the silicon is reflected there with the Fresnel probability
                                     of the silicon / vacuum interface at normal incidence, ((n - 1) / (n + 1))^2
