@@ -99,6 +99,79 @@ __device__ __forceinline__ ds dfma(ds a, float b, ds c) {
     return fast_two_sum(s.hi, e);
 }
 
+// Two double-single numbers, the x and y components of a vector, carried as packed pairs for Blackwell's FP32x2
+// instructions (one issue for both halves).  Every primitive below performs, in each half, exactly the
+// operations of its scalar counterpart in the same order (a subtraction as the exact fused form b (-1) + a), so
+// the results are bit for bit those of two scalar calls.
+struct ds2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ ds2 ds2_of(ds x, ds y) { return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+__device__ __forceinline__ ds ds2_x(ds2 v) { return {v.hi.x, v.lo.x}; }
+__device__ __forceinline__ ds ds2_y(ds2 v) { return {v.hi.y, v.lo.y}; }
+__device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ ds2 two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = f2_sub(s, a);
+    return {s, __fadd2_rn(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb))};
+}
+__device__ __forceinline__ ds2 fast_two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    return {s, f2_sub(b, f2_sub(s, a))};
+}
+// dfma(a, b, c) in each half, a shared
+__device__ __forceinline__ ds2 dfma2(ds a, ds2 b, ds2 c) {
+    const float2 ah = make_float2(a.hi, a.hi), al = make_float2(a.lo, a.lo);
+    const float2 p = __fmul2_rn(ah, b.hi);
+    float2 e = __ffma2_rn(ah, b.hi, f2_neg(p));
+    const ds2 s = two_sum2(p, c.hi);
+    e = __ffma2_rn(ah, b.lo, e);
+    e = __ffma2_rn(al, b.hi, e);
+    e = __fadd2_rn(e, __fadd2_rn(s.lo, c.lo));
+    return fast_two_sum2(s.hi, e);
+}
+// a * b in each half with a shared (the scalar operator*(a, b))
+__device__ __forceinline__ ds2 mul2(ds a, ds2 b) {
+    const float2 ah = make_float2(a.hi, a.hi), al = make_float2(a.lo, a.lo);
+    const float2 p = __fmul2_rn(ah, b.hi);
+    float2 e = __ffma2_rn(ah, b.hi, f2_neg(p));
+    e = __ffma2_rn(ah, b.lo, e);
+    e = __ffma2_rn(al, b.hi, e);
+    return fast_two_sum2(p, e);
+}
+// a * b in each half with b shared (the scalar operator*(a, b))
+__device__ __forceinline__ ds2 mul2(ds2 a, ds b) {
+    const float2 bh = make_float2(b.hi, b.hi), bl = make_float2(b.lo, b.lo);
+    const float2 p = __fmul2_rn(a.hi, bh);
+    float2 e = __ffma2_rn(a.hi, bh, f2_neg(p));
+    e = __ffma2_rn(a.hi, bl, e);
+    e = __ffma2_rn(a.lo, bh, e);
+    return fast_two_sum2(p, e);
+}
+
+// a + b in each half (the scalar operator+(a, b))
+__device__ __forceinline__ ds2 add2(ds2 a, ds2 b) {
+    const ds2 s = two_sum2(a.hi, b.hi);
+    return fast_two_sum2(s.hi, __fadd2_rn(s.lo, __fadd2_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ds2 neg2(ds2 a) { return {f2_neg(a.hi), f2_neg(a.lo)}; }
+// a + b in each half for a single-precision b (the scalar operator+(a, float))
+__device__ __forceinline__ ds2 add2(ds2 a, float2 b) {
+    const ds2 s = two_sum2(a.hi, b);
+    return fast_two_sum2(s.hi, __fadd2_rn(s.lo, a.lo));
+}
+// dfma(a, b, c) in each half for a shared single-precision b
+__device__ __forceinline__ ds2 dfma2(ds2 a, float b, ds2 c) {
+    const float2 bb = make_float2(b, b);
+    const float2 p = __fmul2_rn(a.hi, bb);
+    float2 e = __ffma2_rn(a.hi, bb, f2_neg(p));
+    const ds2 s = two_sum2(p, c.hi);
+    e = __ffma2_rn(a.lo, bb, e);
+    e = __fadd2_rn(e, __fadd2_rn(s.lo, c.lo));
+    return fast_two_sum2(s.hi, e);
+}
+
 // Quotient: a single-precision reciprocal estimate r, q1 = a r, then one correction from the remainder
 // a - q1 b evaluated in double-single; relative error about 2^-45.
 static __device__ PHOSIM_DS_HEAVY ds operator/(ds a, ds b) {

@@ -191,8 +191,11 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
         const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
         g = dfma(rho * E.inv_rn2, pd, g);
     }
-    zx = x * g;
-    zy = y * g;
+    {
+        const ds2 q = mul2(ds2_of(x, y), g);
+        zx = ds2_x(q);
+        zy = ds2_y(q);
+    }
     if (flags & SF_ZERN) {
         float zz, zu, zv;
         zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
@@ -211,7 +214,8 @@ __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, con
     ds zx = ds_f(0.f), zy = ds_f(0.f);
 #pragma unroll 1
     for (int it = 0; it < 20; ++it) {
-        const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]);
+        const ds2 xy = dfma2(l, ds2_of(d[0], d[1]), ds2_of(p[0], p[1]));
+        const ds x = ds2_x(xy), y = ds2_y(xy);
         ds zs;
         if (!sag_ds(E, flags, x, y, zs, zx, zy)) return PHOSIM_LOST_MISSED;
         const ds F = dfma(l, d[2], p[2]) - zs;
@@ -221,7 +225,8 @@ __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, con
         l = l - step;
         if (fabsf(step) < 1e-8f) {
             const ds inv = ds_rsqrt(dfma(zx, zx, dfma(zy, zy, ds_f(1.f))));
-            N[0] = -(zx * inv); N[1] = -(zy * inv); N[2] = inv;
+            const ds2 nxy = mul2(ds2_of(zx, zy), inv);
+            N[0] = -ds2_x(nxy); N[1] = -ds2_y(nxy); N[2] = inv;
             return 0;
         }
     }
@@ -271,13 +276,16 @@ __device__ __forceinline__ bool sag_f(const DSurfaceS& E, int flags, float x, fl
 // (kappa = 0, kc = c) that vector's squared length is 1 + c Q with Q = c (x^2 + y^2) + c z^2 - 2 z the quadric,
 // which vanishes at the intersection: it is already a unit vector (to the root's 1e-14) and needs no root.
 __device__ __forceinline__ void conic_normal_ds(const DSurfaceS& E, ds x, ds y, ds z, ds N[3]) {
-    const ds vx = -(E.c * x), vy = -(E.c * y), vz = ds_f(1.f) - E.kc * z;
+    const ds2 cxy = mul2(E.c, ds2_of(x, y));
+    const ds vx = -ds2_x(cxy), vy = -ds2_y(cxy), vz = ds_f(1.f) - E.kc * z;
     if (E.kmc.hi == 0.f) {
         N[0] = vx; N[1] = vy; N[2] = vz;
         return;
     }
     const ds inv = ds_rsqrt(dfma(vx, vx, dfma(vy, vy, vz * vz)));
-    N[0] = vx * inv; N[1] = vy * inv; N[2] = vz * inv;
+    const ds2 nxy = mul2(ds2_of(vx, vy), inv);
+    N[0] = ds2_x(nxy); N[1] = ds2_y(nxy);
+    N[2] = vz * inv;
 }
 
 // Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
@@ -376,8 +384,11 @@ static __device__ PHOSIM_DS_STEP bool refract_ds(ds d[3], ds N[3], ds mu) {
     const ds k = ds_f(1.f) - mu * mu * (ds_f(1.f) - cosi * cosi);
     if (k.hi < 0.f) return false;
     const ds a = mu * cosi - ds_sqrt(k);
-    d[0] = dfma(mu, d[0], a * n0);
-    d[1] = dfma(mu, d[1], a * n1);
+    {
+        const ds2 q = dfma2(mu, ds2_of(d[0], d[1]), mul2(a, ds2_of(n0, n1)));
+        d[0] = ds2_x(q);
+        d[1] = ds2_y(q);
+    }
     d[2] = dfma(mu, d[2], a * n2);
     return true;
 }
@@ -625,19 +636,19 @@ __device__ __forceinline__ void detect_ds(const TraceParams& P, const DetectorHi
             if (!back) { R.flags = lost(PHOSIM_LOST_NOT_CONVERTED, si); return; }
         }
         if (depth < P.dead_layerf) { R.flags = lost(PHOSIM_LOST_DEAD_LAYER, si); return; }
-        fx = dfma(dl[0], L, fx);
-        fy = dfma(dl[1], L, fy);
-        R.xc = fx; R.yc = fy;
+        ds2 f = dfma2(ds2_of(dl[0], dl[1]), L, ds2_of(fx, fy));
+        R.xc = ds2_x(f); R.yc = ds2_y(f);
         // lateral Gaussian diffusion (Sec. 2.5)
         const float sg = lerp_table_f(P.sig32, P.n_sig, depth * P.sig_scalef);
         const float g = sqrtf(-2.f * logf(u32of(w_diff_a)));
         float sn, cs;
         sincospif(2.f * u32of(w_diff_b), &sn, &cs);
-        fx = fx + sg * g * cs;
-        fy = fy + sg * g * sn;
+        f = add2(f, make_float2(sg * g * cs, sg * g * sn));
+        fx = ds2_x(f); fy = ds2_y(f);
     }
     R.x = fx; R.y = fy;
-    const float px = ds_floor((fx - P.xlo_s) * P.inv_pixel_s), py = ds_floor((fy - P.ylo_s) * P.inv_pixel_s);
+    const ds2 u = mul2(add2(ds2_of(fx, fy), neg2(ds2_of(P.xlo_s, P.ylo_s))), P.inv_pixel_s);
+    const float px = ds_floor(ds2_x(u)), py = ds_floor(ds2_y(u));
     if (!(px >= 0.f && py >= 0.f && px < (float)P.nx && py < (float)P.ny)) {
         R.flags = lost(PHOSIM_LOST_OFF_CHIP, si);
         return;
@@ -689,8 +700,11 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
     const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
     if (why) { R.flags = lost(why, si); return false; }
     if (W.bounces > 0 && !(l.hi > 0.f)) { R.flags = lost(PHOSIM_LOST_MISSED, si); return false; }
-    p[0] = dfma(l, dl[0], p[0]);
-    p[1] = dfma(l, dl[1], p[1]);
+    {
+        const ds2 q = dfma2(l, ds2_of(dl[0], dl[1]), ds2_of(p[0], p[1]));
+        p[0] = ds2_x(q);
+        p[1] = ds2_y(q);
+    }
     p[2] = dfma(l, dl[2], p[2]);
     if (S.kind == PHOSIM_DETECTOR) {
         // the hit on the detector surface, its direction and the medium in front of it
@@ -736,8 +750,11 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
             if ((P.flags & kGhostFlag) && S.kind != PHOSIM_MIRROR && C.TR_thr &&
                 (unsigned long long)w < __ldg(C.TR_thr + ix)) {
                 const ds dn2 = dot3(dl, Nv) * -2.f;
-                dl[0] = dfma(dn2, Nv[0], dl[0]);
-                dl[1] = dfma(dn2, Nv[1], dl[1]);
+                {
+                    const ds2 q = dfma2(dn2, ds2_of(Nv[0], Nv[1]), ds2_of(dl[0], dl[1]));
+                    dl[0] = ds2_x(q);
+                    dl[1] = ds2_y(q);
+                }
                 dl[2] = dfma(dn2, Nv[2], dl[2]);
                 W.dir = -W.dir;
                 if (++W.bounces > kMaxGhostBounces) { R.flags = lost(PHOSIM_LOST_MISSED, si); return false; }
@@ -751,8 +768,11 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
     }
     if (S.kind == PHOSIM_MIRROR) {
         const ds dn2 = dot3(dl, Nv) * -2.f;
-        dl[0] = dfma(dn2, Nv[0], dl[0]);
-        dl[1] = dfma(dn2, Nv[1], dl[1]);
+        {
+            const ds2 q = dfma2(dn2, ds2_of(Nv[0], Nv[1]), ds2_of(dl[0], dl[1]));
+            dl[0] = ds2_x(q);
+            dl[1] = ds2_y(q);
+        }
         dl[2] = dfma(dn2, Nv[2], dl[2]);
     } else {
         // the medium beyond the surface in the direction of travel (-1: vacuum)

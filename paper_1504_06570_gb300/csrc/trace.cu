@@ -459,14 +459,22 @@ __device__ __forceinline__ void account_ds(const TraceParams& P, const PhotonOut
         const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != src);
         const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;
         const int first = 31 - __clz(heads & upto);
+        // the sums in pairs (x, y), (xx, xy) and yy, the pairs added by the packed primitive (bit for bit the same)
+        ds2 m01 = ds2_of(mm[0], mm[1]), m23 = ds2_of(mm[2], mm[3]);
+        ds m4 = mm[4];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const ds t = {__shfl_up_sync(0xffffffffu, mm[q].hi, d), __shfl_up_sync(0xffffffffu, mm[q].lo, d)};
-                if (lane - d >= first) mm[q] = mm[q] + t;
+            const auto up = [&](float v) { return __shfl_up_sync(0xffffffffu, v, d); };
+            const ds2 t01 = {make_float2(up(m01.hi.x), up(m01.hi.y)), make_float2(up(m01.lo.x), up(m01.lo.y))};
+            const ds2 t23 = {make_float2(up(m23.hi.x), up(m23.hi.y)), make_float2(up(m23.lo.x), up(m23.lo.y))};
+            const ds t4 = {up(m4.hi), up(m4.lo)};
+            if (lane - d >= first) {
+                m01 = add2(m01, t01);
+                m23 = add2(m23, t23);
+                m4 = m4 + t4;
             }
         }
+        mm[0] = ds2_x(m01); mm[1] = ds2_y(m01); mm[2] = ds2_x(m23); mm[3] = ds2_y(m23); mm[4] = m4;
         const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
         // the segment's detected photons, counted from the ballot
         const unsigned n_det = __popc(dmask & upto & ~((1u << first) - 1u));
