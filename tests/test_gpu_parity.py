@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, photon by photon, on seeded inputs.
 
 Tolerances (written from the arithmetic): the FP64 path and the oracle evaluate the same formulas with
-different operation order and contraction, so final positions agree to ~1e-12 mm; the gate is the
-spec one, 1e-4 pixel for at least 99.999 % of the photons detected by both, with identical fates
+different operation order and contraction, so final positions agree to ~1e-12 mm; the per-photon gate is
+1e-4 pixel for at least 99.999 % of the photons detected by both, with identical fates
 except for photons within 1e-7 mm / 1e-6 nm of an accept boundary.  The mixed path keeps positions and
 intersections in FP64 and rounds the deflections, the wavelength blur and the sensor draws to FP32, so it
 is held to the moment gate (0.1 %) and to 1e-2 pixel per photon for 99.9 % of the photons.  The
