@@ -50,3 +50,40 @@ def test_dual_numbers_match_oracle_central_differences(oracle_mod):
         scale = max(np.abs(t["dx"][ok, k]).max(), np.abs(t["dy"][ok, k]).max(), 1e-12)
         assert np.abs(fdx - t["dx"][ok, k]).max() < 1e-5 * scale + 1e-9, (si, f)
         assert np.abs(fdy - t["dy"][ok, k]).max() < 1e-5 * scale + 1e-9, (si, f)
+
+
+def test_tilt_and_zernike_gradients_closed_forms(oracle_mod):
+    """Sec. 2.4.1 misalignments and figure, differentiated: a vertical beam on a flat mirror reaches the
+    detector plane z = L above it at y = y0 - tan(2 tx)(L - y0 tan tx) and x = x0 + tan(2 ty)(L + x0 tan ty)
+    (exact trigonometry), so at zero tilt dy/dtx = -2 L and dx/dty = +2 L for every photon.  A Noll Z2 term
+    of coefficient c over rho_n is the plane z = (2 c / rho_n) x, which turns the beam by twice its slope:
+    dx/dc = -4 L / rho_n at c = 0 (Z3 likewise in y).  With c != 0 and the mirror turned by tz the spot is
+    (x0, y0) + (L - z_h) s (cos tz, sin tz), s = -2 g / (1 - g^2), g = 2 c / rho_n, z_h = g (x0 cos tz + y0 sin
+    tz), so at tz = 0: dx/dtz = -g y0 s and dy/dtz = (L - g x0) s."""
+    from tests.test_oracle_pins import _flat_mirror_scene
+    L, rn = 500.0, 1000.0
+    src = I.point_sources([0.0], [0.0], [1500])
+    sc = _flat_mirror_scene(zern=(0.0, 0.0, 0.0), rnorm=rn, L=L, sources=src)
+    o = oracle_mod.Oracle(sc)
+    t = o.trace_tangents([(0, 3), (0, 4), (0, 101), (0, 102)])
+    det = (t["flags"] & 1) == 1
+    assert det.mean() > 0.99
+    np.testing.assert_allclose(t["dy"][det, 0], -2 * L, rtol=1e-12)
+    np.testing.assert_allclose(t["dx"][det, 0], 0.0, atol=1e-9)
+    np.testing.assert_allclose(t["dx"][det, 1], 2 * L, rtol=1e-12)
+    np.testing.assert_allclose(t["dy"][det, 1], 0.0, atol=1e-9)
+    np.testing.assert_allclose(t["dx"][det, 2], -4 * L / rn, rtol=1e-12)
+    np.testing.assert_allclose(t["dy"][det, 2], 0.0, atol=1e-12)
+    np.testing.assert_allclose(t["dy"][det, 3], -4 * L / rn, rtol=1e-12)
+    np.testing.assert_allclose(t["dx"][det, 3], 0.0, atol=1e-12)
+    c = 0.3
+    g = 2 * c / rn
+    s = -2 * g / (1 - g * g)
+    sc = _flat_mirror_scene(zern=(0.0, c), rnorm=rn, L=L, sources=src)
+    o = oracle_mod.Oracle(sc)
+    t = o.trace_tangents([(0, 5)])
+    det = (t["flags"] & 1) == 1
+    pos, _, _, _ = o.pre_optics(0, 0, 1500)
+    x0, y0 = pos[det, 0], pos[det, 1]
+    np.testing.assert_allclose(t["dx"][det, 0], -g * y0 * s, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(t["dy"][det, 0], (L - g * x0) * s, rtol=1e-9, atol=1e-12)
