@@ -154,8 +154,8 @@ phosim_status build_surface(const phosim_surface& s, DSurface& d) {
     for (int i = 0; i < 4; ++i) {
         d.ao[i] = s.alpha[2 * i];        // alpha_3, 5, 7, 9
         d.ae[i] = s.alpha[2 * i + 1];    // alpha_4, 6, 8, 10
-        if (d.ao[i] != 0.0) flags |= SF_ODD;
-        if (d.ae[i] != 0.0) flags |= SF_EVEN;
+        if (d.ao[i] != 0.0) { flags |= SF_ODD; d.no = i + 1; }
+        if (d.ae[i] != 0.0) { flags |= SF_EVEN; d.ne = i + 1; }
     }
     if (s.zern_rnorm > 0.0) d.zinv = 1.0 / s.zern_rnorm;
     if (s.n_zern > 0 && s.zern_rnorm > 0.0) {
@@ -209,6 +209,8 @@ void build_surface_s(const phosim_surface& s, const DSurface& d, DSurfaceS& e) {
         e.aed[k] = ds_clamped((2 * k + 4) * ae);
         e.ao[k] = ds_clamped(ao);
         e.aod[k] = ds_clamped((2 * k + 3) * ao);
+        if (d.ae[k] != 0.0) e.ne = (unsigned char)(k + 1);
+        if (d.ao[k] != 0.0) e.no = (unsigned char)(k + 1);
     }
     for (int i = 0; i < 9; ++i) e.M[i] = ds_of(d.M[i]);
     for (int i = 0; i < 3; ++i) e.o[i] = ds_of(d.o[i]);

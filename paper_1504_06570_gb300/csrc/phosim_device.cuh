@@ -28,7 +28,7 @@ struct DSurface {
     int kind, material, coating, coat_slot;   // coat_slot: index of this surface's accept draw, -1 none
     int flags;
     int mat_before;                           // medium in front of the surface (material index, -1 vacuum)
-    int pad1, pad2;
+    int ne, no;                               // terms of the even / odd polynomials up to the last nonzero one
     double c, k1c2, kc;                       // 1/R, (1 + kappa) / R^2, (1 + kappa) / R
     double ae[4];                             // alpha_4, alpha_6, alpha_8, alpha_10
     double ao[4];                             // alpha_3, alpha_5, alpha_7, alpha_9
@@ -51,7 +51,8 @@ struct DSurfaceS {
     ds M[9], o[3];
     ds r_in2, r_out2;
     ds inv_rn, inv_rn2;
-    float zinv, pad;
+    float zinv;
+    unsigned char ne, no, pad0, pad1;         // terms of the even / odd polynomials up to the last nonzero one
     float zp[kZPoly];
 };
 
@@ -248,17 +249,28 @@ __device__ __forceinline__ bool sag(const DSurface& S, double x, double y, doubl
         z = S.c * r2 / fma(arg, rs, 1.0);
         g = S.c * rs;
     }
+    // Horner from the last nonzero coefficient: the zero terms above it would add exact zeros
     if (S.flags & SF_EVEN) {
-        const double pe = fma(r2, fma(r2, fma(r2, S.ae[3], S.ae[2]), S.ae[1]), S.ae[0]);
+        int k = S.ne - 1;
+        double pe = S.ae[k], pd = (2 * k + 4) * S.ae[k];
+#pragma unroll 1
+        while (--k >= 0) {
+            pe = fma(r2, pe, S.ae[k]);
+            pd = fma(r2, pd, (2 * k + 4) * S.ae[k]);
+        }
         z = fma(r2 * r2, pe, z);
-        const double pd = fma(r2, fma(r2, fma(r2, 10.0 * S.ae[3], 8.0 * S.ae[2]), 6.0 * S.ae[1]), 4.0 * S.ae[0]);
         g = fma(r2, pd, g);
     }
     if (S.flags & SF_ODD) {
         const double r = sqrt(r2);
-        const double po = fma(r2, fma(r2, fma(r2, S.ao[3], S.ao[2]), S.ao[1]), S.ao[0]);
+        int k = S.no - 1;
+        double po = S.ao[k], pd = (2 * k + 3) * S.ao[k];
+#pragma unroll 1
+        while (--k >= 0) {
+            po = fma(r2, po, S.ao[k]);
+            pd = fma(r2, pd, (2 * k + 3) * S.ao[k]);
+        }
         z = fma(r2 * r, po, z);
-        const double pd = fma(r2, fma(r2, fma(r2, 9.0 * S.ao[3], 7.0 * S.ao[2]), 5.0 * S.ao[1]), 3.0 * S.ao[0]);
         g = fma(r, pd, g);
     }
     zx = x * g;

@@ -176,19 +176,30 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
         z = E.c * r2 / dfma(arg, rs, ds_f(1.f));
         g = E.c * rs;
     }
+    // Horner from the last nonzero coefficient: the zero terms above it would add exact zeros
     if (flags & SF_EVEN) {
         const ds u = r2 * E.inv_rn2;
-        const ds pe = dfma(dfma(dfma(E.ae[3], u, E.ae[2]), u, E.ae[1]), u, E.ae[0]);
+        int k = E.ne - 1;
+        ds pe = E.ae[k], pd = E.aed[k];
+#pragma unroll 1
+        while (--k >= 0) {
+            pe = dfma(pe, u, E.ae[k]);
+            pd = dfma(pd, u, E.aed[k]);
+        }
         z = dfma(u * u, pe, z);
-        const ds pd = dfma(dfma(dfma(E.aed[3], u, E.aed[2]), u, E.aed[1]), u, E.aed[0]);
         g = dfma(u * E.inv_rn2, pd, g);
     }
     if (flags & SF_ODD) {
         const ds rho = ds_sqrt(r2) * E.inv_rn;
         const ds u = rho * rho;
-        const ds po = dfma(dfma(dfma(E.ao[3], u, E.ao[2]), u, E.ao[1]), u, E.ao[0]);
+        int k = E.no - 1;
+        ds po = E.ao[k], pd = E.aod[k];
+#pragma unroll 1
+        while (--k >= 0) {
+            po = dfma(po, u, E.ao[k]);
+            pd = dfma(pd, u, E.aod[k]);
+        }
         z = dfma(u * rho, po, z);
-        const ds pd = dfma(dfma(dfma(E.aod[3], u, E.aod[2]), u, E.aod[1]), u, E.aod[0]);
         g = dfma(rho * E.inv_rn2, pd, g);
     }
     {
@@ -247,17 +258,27 @@ __device__ __forceinline__ bool sag_f(const DSurfaceS& E, int flags, float x, fl
     }
     if (flags & SF_EVEN) {
         const float u = r2 * E.inv_rn2.hi;
-        const float pe = fmaf(fmaf(fmaf(E.ae[3].hi, u, E.ae[2].hi), u, E.ae[1].hi), u, E.ae[0].hi);
+        int k = E.ne - 1;
+        float pe = E.ae[k].hi, pd = E.aed[k].hi;
+#pragma unroll 1
+        while (--k >= 0) {
+            pe = fmaf(pe, u, E.ae[k].hi);
+            pd = fmaf(pd, u, E.aed[k].hi);
+        }
         z = fmaf(u * u, pe, z);
-        const float pd = fmaf(fmaf(fmaf(E.aed[3].hi, u, E.aed[2].hi), u, E.aed[1].hi), u, E.aed[0].hi);
         g = fmaf(u * E.inv_rn2.hi, pd, g);
     }
     if (flags & SF_ODD) {
         const float rho = sqrtf(r2) * E.inv_rn.hi;
         const float u = rho * rho;
-        const float po = fmaf(fmaf(fmaf(E.ao[3].hi, u, E.ao[2].hi), u, E.ao[1].hi), u, E.ao[0].hi);
+        int k = E.no - 1;
+        float po = E.ao[k].hi, pd = E.aod[k].hi;
+#pragma unroll 1
+        while (--k >= 0) {
+            po = fmaf(po, u, E.ao[k].hi);
+            pd = fmaf(pd, u, E.aod[k].hi);
+        }
         z = fmaf(u * rho, po, z);
-        const float pd = fmaf(fmaf(fmaf(E.aod[3].hi, u, E.aod[2].hi), u, E.aod[1].hi), u, E.aod[0].hi);
         g = fmaf(rho * E.inv_rn2.hi, pd, g);
     }
     zx = x * g;
