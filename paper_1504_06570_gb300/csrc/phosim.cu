@@ -209,6 +209,7 @@ void build_surface_s(const phosim_surface& s, const DSurface& d, DSurfaceS& e) {
         e.aed[k] = ds_clamped((2 * k + 4) * ae);
         e.ao[k] = ds_clamped(ao);
         e.aod[k] = ds_clamped((2 * k + 3) * ao);
+        e.ae2[k] = (float)((k + 1) * (2 * k + 4) * ae / (rn * rn * rn * rn));
         if (d.ae[k] != 0.0) e.ne = (unsigned char)(k + 1);
         if (d.ao[k] != 0.0) e.no = (unsigned char)(k + 1);
     }

@@ -51,6 +51,7 @@ struct DSurfaceS {
     ds M[9], o[3];
     ds r_in2, r_out2;
     ds inv_rn, inv_rn2;
+    float ae2[4];                             // (k + 1) aed[k] / rn^4: d^2 S / (d r^2)^2 terms of the even part, single
     float zinv;
     unsigned char ne, no, pad0, pad1;         // terms of the even / odd polynomials up to the last nonzero one
     float zp[kZPoly];

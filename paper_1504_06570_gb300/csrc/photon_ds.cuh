@@ -164,17 +164,23 @@ __device__ __forceinline__ void zern_eval_f(const float* __restrict__ zp, float 
 }
 
 // Sag and slopes (Sec. 2.4.1).  The Zernike figure (tens of nanometres) is evaluated in single precision:
-// its absolute error is far below the 1e-8 mm the intersection resolves.
-static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy) {
+// its absolute error is far below the 1e-8 mm the intersection resolves.  With the slopes S_x = x g(r^2),
+// S_y = y g(r^2) it returns, in single precision, g and, for the conic and even terms, g1 = dg / d(r^2), which
+// give the second derivatives S_xx = g + 2 x^2 g1, S_xy = 2 x y g1, S_yy = g + 2 y^2 g1.
+static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x, ds y, ds& z, ds& zx, ds& zy,
+                                            float& gf, float& g1f) {
     const ds r2 = dfma(x, x, y * y);
     ds g = ds_f(0.f);
     z = ds_f(0.f);
+    g1f = 0.f;
     if (flags & SF_CONIC) {
         const ds arg = ds_f(1.f) - E.k1c2 * r2;
         if (arg.hi < 0.f) return false;
         const ds rs = ds_rsqrt(arg);
         z = E.c * r2 / dfma(arg, rs, ds_f(1.f));
         g = E.c * rs;
+        // g = c (1 - k1c2 r^2)^(-1/2): dg / d(r^2) = k1c2 c rs^3 / 2
+        g1f = 0.5f * E.k1c2.hi * g.hi * rs.hi * rs.hi;
     }
     // Horner from the last nonzero coefficient: the zero terms above it would add exact zeros
     if (flags & SF_EVEN) {
@@ -188,6 +194,12 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
         }
         z = dfma(u * u, pe, z);
         g = dfma(u * E.inv_rn2, pd, g);
+        // the even part of g is sum_k aed[k] u^(k+1) / rn^2, so its derivative in r^2 is sum_k ae2[k] u^k
+        k = E.ne - 1;
+        float q = E.ae2[k];
+#pragma unroll 1
+        while (--k >= 0) q = fmaf(q, u.hi, E.ae2[k]);
+        g1f += q;
     }
     if (flags & SF_ODD) {
         const ds rho = ds_sqrt(r2) * E.inv_rn;
@@ -207,6 +219,7 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
         zx = ds2_x(q);
         zy = ds2_y(q);
     }
+    gf = g.hi;
     if (flags & SF_ZERN) {
         float zz, zu, zv;
         zern_eval_f(E.zp, x.hi * E.zinv, y.hi * E.zinv, zz, zu, zv);
@@ -217,9 +230,21 @@ static __device__ PHOSIM_DS_SAG bool sag_ds(const DSurfaceS& E, int flags, ds x,
     return true;
 }
 
+// the unit normal (-S_x, -S_y, 1) / |.| from the slopes
+__device__ __forceinline__ void slope_normal_ds(ds zx, ds zy, ds N[3]) {
+    const ds inv = ds_rsqrt(dfma(zx, zx, dfma(zy, zy, ds_f(1.f))));
+    const ds2 nxy = mul2(ds2_of(zx, zy), inv);
+    N[0] = -ds2_x(nxy); N[1] = -ds2_y(nxy); N[2] = inv;
+}
+
 // Newton's method in double-single on F(l) = p_z + l d_z - S(p_x + l d_x, p_y + l d_y) from l until the step
 // is below 1e-8 mm (the Newton slope F'(l) only scales the step, so it is taken in single precision); the
-// normal from the slopes at the last point
+// normal from the slopes at the last point.  Newton's error after a step s is about F'' s^2 / (2 F'), with
+// F'' = -d^T H d (H the sag's second derivatives, d the direction's x, y part): where that bound is below
+// 1e-10 mm the root is taken after this step, with the slopes carried to the new point by H (their change
+// over the step, tens of nanoradians, in single precision), instead of a further evaluation of the sag.
+// The single-precision second derivatives cover the conic and even terms, so surfaces with odd or Zernike
+// terms iterate until the step itself is below 1e-8 mm.
 __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
                                               ds N[3]) {
     ds zx = ds_f(0.f), zy = ds_f(0.f);
@@ -228,17 +253,29 @@ __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, con
         const ds2 xy = dfma2(l, ds2_of(d[0], d[1]), ds2_of(p[0], p[1]));
         const ds x = ds2_x(xy), y = ds2_y(xy);
         ds zs;
-        if (!sag_ds(E, flags, x, y, zs, zx, zy)) return PHOSIM_LOST_MISSED;
+        float gf, g1f;
+        if (!sag_ds(E, flags, x, y, zs, zx, zy, gf, g1f)) return PHOSIM_LOST_MISSED;
         const ds F = dfma(l, d[2], p[2]) - zs;
         const float dF = d[2].hi - zx.hi * d[0].hi - zy.hi * d[1].hi;
         if (dF == 0.f) return PHOSIM_LOST_NEWTON;
         const float step = F.hi * __fdividef(1.f, dF);
         l = l - step;
         if (fabsf(step) < 1e-8f) {
-            const ds inv = ds_rsqrt(dfma(zx, zx, dfma(zy, zy, ds_f(1.f))));
-            const ds2 nxy = mul2(ds2_of(zx, zy), inv);
-            N[0] = -ds2_x(nxy); N[1] = -ds2_y(nxy); N[2] = inv;
+            slope_normal_ds(zx, zy, N);
             return 0;
+        }
+        if (!(flags & (SF_ODD | SF_ZERN))) {
+            const float xf = x.hi, yf = y.hi, dx = d[0].hi, dy = d[1].hi;
+            const float hxy = 2.f * xf * yf * g1f;
+            const float hdx = fmaf(fmaf(2.f * xf * xf, g1f, gf), dx, hxy * dy);
+            const float hdy = fmaf(hxy, dx, fmaf(2.f * yf * yf, g1f, gf) * dy);
+            const float fpp = fmaf(dx, hdx, dy * hdy);
+            if (fabsf(fpp) * (step * step) < 2e-10f * fabsf(dF)) {
+                // the point moved by -step (dx, dy): the slopes by -step H (dx, dy)
+                const ds2 zn = add2(ds2_of(zx, zy), make_float2(-step * hdx, -step * hdy));
+                slope_normal_ds(ds2_x(zn), ds2_y(zn), N);
+                return 0;
+            }
         }
     }
     return PHOSIM_LOST_NEWTON;
@@ -905,7 +942,8 @@ __device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const Sour
     ds_sincos_2pi(ds_uniform(w0.y), sp, cp);
     ds x = r * cp, y = r * sp;
     ds zs = ds_f(0.f), zx, zy;
-    sag_ds(P.pupil_s, P.pupil_surf.flags, x, y, zs, zx, zy);
+    float gf, g1f;
+    sag_ds(P.pupil_s, P.pupil_surf.flags, x, y, zs, zx, zy, gf, g1f);
     ds z = P.pupil_z_s + zs;
     {
         const ds l = (P.h_top_s - z) * rinv;
