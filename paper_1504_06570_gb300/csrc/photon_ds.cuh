@@ -245,8 +245,9 @@ __device__ __forceinline__ void slope_normal_ds(ds zx, ds zy, ds N[3]) {
 // over the step, tens of nanoradians, in single precision), instead of a further evaluation of the sag.
 // The single-precision second derivatives cover the conic and even terms, so surfaces with odd or Zernike
 // terms iterate until the step itself is below 1e-8 mm.
+// The hit point is the last point of the iteration moved by the last step along the ray.
 __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
-                                              ds N[3]) {
+                                              ds N[3], ds hit[3]) {
     ds zx = ds_f(0.f), zy = ds_f(0.f);
 #pragma unroll 1
     for (int it = 0; it < 20; ++it) {
@@ -255,13 +256,20 @@ __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, con
         ds zs;
         float gf, g1f;
         if (!sag_ds(E, flags, x, y, zs, zx, zy, gf, g1f)) return PHOSIM_LOST_MISSED;
-        const ds F = dfma(l, d[2], p[2]) - zs;
+        const ds zr = dfma(l, d[2], p[2]);
+        const ds F = zr - zs;
         const float dF = d[2].hi - zx.hi * d[0].hi - zy.hi * d[1].hi;
         if (dF == 0.f) return PHOSIM_LOST_NEWTON;
         const float step = F.hi * __fdividef(1.f, dF);
         l = l - step;
+        const auto moved = [&] {
+            const ds2 h = dfma2(ds2_of(d[0], d[1]), -step, xy);
+            hit[0] = ds2_x(h); hit[1] = ds2_y(h);
+            hit[2] = dfma(d[2], -step, zr);
+        };
         if (fabsf(step) < 1e-8f) {
             slope_normal_ds(zx, zy, N);
+            moved();
             return 0;
         }
         if (!(flags & (SF_ODD | SF_ZERN))) {
@@ -274,6 +282,7 @@ __device__ __forceinline__ uint32_t newton_ds(const DSurfaceS& E, int flags, con
                 // the point moved by -step (dx, dy): the slopes by -step H (dx, dy)
                 const ds2 zn = add2(ds2_of(zx, zy), make_float2(-step * hdx, -step * hdy));
                 slope_normal_ds(ds2_x(zn), ds2_y(zn), N);
+                moved();
                 return 0;
             }
         }
@@ -346,6 +355,14 @@ __device__ __forceinline__ void conic_normal_ds(const DSurfaceS& E, ds x, ds y, 
     N[2] = vz * inv;
 }
 
+// the point p + l d of a ray (x and y as a packed pair)
+__device__ __forceinline__ void ray_point_ds(ds l, const ds p[3], const ds d[3], ds out[3]) {
+    const ds2 q = dfma2(l, ds2_of(d[0], d[1]), ds2_of(p[0], p[1]));
+    out[0] = ds2_x(q);
+    out[1] = ds2_y(q);
+    out[2] = dfma(l, d[2], p[2]);
+}
+
 // Intersection (Sec. 2.4.2), the steps of intersect() in phosim_device.cuh: the conic's exact root on the
 // vertex branch, then Newton's method for the aspheric and Zernike terms until the step is below 1e-8 mm.
 // Newton converges to the same root from any start close enough to it, so the start is computed in single
@@ -357,11 +374,12 @@ __device__ __forceinline__ void conic_normal_ds(const DSurfaceS& E, ds x, ds y, 
 // precision).  A ray whose single-precision discriminant is not clearly positive (grazing or missing the
 // conic) takes the double-single root.
 static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int flags, const ds p[3], const ds d[3], ds& l,
-                                                 ds N[3]) {
+                                                 ds N[3], ds hit[3]) {
     if (flags & SF_FLAT_ONLY) {
         if (d[2].hi == 0.f) return PHOSIM_LOST_MISSED;
         l = -(p[2] / d[2]);
         N[0] = ds_f(0.f); N[1] = ds_f(0.f); N[2] = ds_f(1.f);
+        ray_point_ds(l, p, d, hit);
         return 0;
     }
     const bool newton = (flags & (SF_EVEN | SF_ODD | SF_ZERN)) != 0;
@@ -389,7 +407,7 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
             }
             if (fabsf(lf) < 1e30f) {
                 l = ds_f(lf);
-                return newton_ds(E, flags, p, d, l, N);
+                return newton_ds(E, flags, p, d, l, N, hit);
             }
         }
     } else {
@@ -405,12 +423,15 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
             if (Af != 0.f && fmaf(-kc, fmaf(lf, d[2].hi, p[2].hi), 1.f) < 0.f) lf = qf / Af;
             if (fabsf(lf) < 1e30f) {
                 l = ds_f(lf);
-                const ds x = dfma(l, d[0], p[0]), y = dfma(l, d[1], p[1]), z = dfma(l, d[2], p[2]);
+                ds q0[3];
+                ray_point_ds(l, p, d, q0);
+                const ds x = q0[0], y = q0[1], z = q0[2];
                 const ds Q = dfma(E.c, dfma(x, x, y * y), dfma(E.kc * z, z, z * -2.f));
                 const float dQ = 2.f * (fmaf(c, fmaf(x.hi, d[0].hi, y.hi * d[1].hi), kc * z.hi * d[2].hi) - d[2].hi);
                 if (dQ != 0.f) {
                     l = l - Q.hi / dQ;
-                    conic_normal_ds(E, dfma(l, d[0], p[0]), dfma(l, d[1], p[1]), dfma(l, d[2], p[2]), N);
+                    ray_point_ds(l, p, d, hit);
+                    conic_normal_ds(E, hit[0], hit[1], hit[2], N);
                     return 0;
                 }
             }
@@ -427,8 +448,9 @@ static __device__ PHOSIM_DS_STEP uint32_t intersect_ds(const DSurfaceS& E, int f
     if (q.hi == 0.f) return PHOSIM_LOST_MISSED;
     l = C / q;
     if (A.hi != 0.f && (ds_f(1.f) - E.kc * dfma(l, d[2], p[2])).hi < 0.f) l = q / A;
-    if (newton) return newton_ds(E, flags, p, d, l, N);
-    conic_normal_ds(E, dfma(l, d[0], p[0]), dfma(l, d[1], p[1]), dfma(l, d[2], p[2]), N);
+    if (newton) return newton_ds(E, flags, p, d, l, N, hit);
+    ray_point_ds(l, p, d, hit);
+    conic_normal_ds(E, hit[0], hit[1], hit[2], N);
     return 0;
 }
 
@@ -754,16 +776,11 @@ __device__ __forceinline__ bool surface_step_ds(const TraceParams& P, OpticsWalk
     const int flags = S.flags;
     ds p[3], dl[3];
     to_surface_ds(E, flags, W.X, W.D, p, dl);
-    ds l, Nv[3];
-    const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv);
+    ds l, Nv[3], hit[3];
+    const uint32_t why = intersect_ds(E, flags, p, dl, l, Nv, hit);
     if (why) { R.flags = lost(why, si); return false; }
     if (W.bounces > 0 && !(l.hi > 0.f)) { R.flags = lost(PHOSIM_LOST_MISSED, si); return false; }
-    {
-        const ds2 q = dfma2(l, ds2_of(dl[0], dl[1]), ds2_of(p[0], p[1]));
-        p[0] = ds2_x(q);
-        p[1] = ds2_y(q);
-    }
-    p[2] = dfma(l, dl[2], p[2]);
+    p[0] = hit[0]; p[1] = hit[1]; p[2] = hit[2];
     if (S.kind == PHOSIM_DETECTOR) {
         // the hit on the detector surface, its direction and the medium in front of it
         DetectorHit H;
