@@ -691,6 +691,7 @@ phosim_status phosim_load_screens(phosim_scene* sc, const phosim_layer* layers, 
         DLayer& D = P.layer[k];
         D.z = L.z; D.vx = L.vx; D.vy = L.vy; D.n_scales = L.n_scales;
         D.zs = ds_of(L.z); D.vxs = ds_of(L.vx); D.vys = ds_of(L.vy);
+        D.dzs = ds_of((k == 0 ? P.h_top : layers[k - 1].z) - L.z);
         for (int q = 0; q < L.n_scales; ++q) {
             const phosim_screen_scale& S = L.scales[q];
             const size_t nn = (size_t)S.n * S.n;

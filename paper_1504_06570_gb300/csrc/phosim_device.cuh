@@ -94,6 +94,7 @@ struct DScale {
 struct DLayer {
     double z, vx, vy;
     ds zs, vxs, vys;
+    ds dzs;                                   // height of the plane above (the previous layer or the top) over z
     int n_scales, pad;
     DScale s[PHOSIM_MAX_SCALES];
 };

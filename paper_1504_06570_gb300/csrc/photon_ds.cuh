@@ -976,7 +976,7 @@ __device__ __forceinline__ bool photon_entry_ds(const TraceParams& P, const Sour
 #pragma unroll 1
         for (int k = 0; k < P.n_layers; ++k) {
             const DLayer& L = P.layer[k];
-            const ds ll = (z - L.zs) * rinv;
+            const ds ll = L.dzs * rinv;           // the drop from the plane above, z_above - z_k
             x = dfma(nx, ll, x);
             y = dfma(ny, ll, y);
             z = L.zs;

@@ -242,8 +242,9 @@ __global__ void __launch_bounds__(256, min_blocks(MODE)) trace_kernel(const __gr
 #ifndef PHOSIM_DS_ENTRY_MIN_BLOCKS
 #define PHOSIM_DS_ENTRY_MIN_BLOCKS 6
 #endif
+// blocks per SM the optics stage is compiled for: 3 of 80 registers (fewer spills) measured faster than 4 of 64
 #ifndef PHOSIM_DS_OPTICS_MIN_BLOCKS
-#define PHOSIM_DS_OPTICS_MIN_BLOCKS 4
+#define PHOSIM_DS_OPTICS_MIN_BLOCKS 3
 #endif
 #ifndef PHOSIM_DS_LOCKSTEP
 #define PHOSIM_DS_LOCKSTEP 1
