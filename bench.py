@@ -535,6 +535,12 @@ def main():
         fp64_rate = r.value
     if L.phosim_fma_rate(0, 20000, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
         fp32_rate = r.value
+    # ceilings of the entry stage's screen lookups: random aligned 32-byte gathers from a buffer the size of
+    # the screens (HBM) and from one well inside the L2
+    gather_peaks = {}
+    for name, nbytes in (("hbm", 4 << 30), ("l2", 32 << 20)):
+        if L.phosim_gather_rate(C.c_size_t(nbytes), 2048, 4, C.c_void_p(stream.cuda_stream), C.byref(r)) == 0:
+            gather_peaks[name] = r.value
 
     # moment sums of each path over all its runs (warm-up and timed): the derived moments do not depend on
     # how many identical runs were added
@@ -660,6 +666,16 @@ def main():
             "algorithmic_gather_bytes": work["gather_bytes"],
             "entry_gather_gbs": work["gather_bytes"] / (kt["entry"] / 1e3) / 1e9 if kt["entry"] else None,
             "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}
+        # the entry stage against the measured random-gather ceilings (its lookups are dependent, one per layer
+        # and scale, so it sits below them: the latency of the chain, not the bandwidth, sets its time)
+        g_entry = line["roofline"]["entry_gather_gbs"]
+        line["roofline_entry"] = {
+            "bound": "gather latency", "kernel": "ds_entry_kernel", "kernel_ms": kt["entry"], "achieved": g_entry,
+            "unit": "GB/s", "peak_random_gather": gather_peaks or None,
+            "frac_of_hbm_random_gather": g_entry / gather_peaks["hbm"] if (g_entry and gather_peaks.get("hbm")) else None,
+            "note": "achieved = algorithmic bytes of the screen lookups (32 B per layer and scale of every surviving "
+                    "ray) over the entry stage's time; peaks = phosim_gather_rate: independent random aligned "
+                    "32-byte gathers from a 4 GiB buffer (HBM) and a 32 MiB one (L2) on this device"}
         # native-FP64 mixed kernel: the same operations against the FP64 FMA rate
         peak64 = fp64_rate or FP64_NOMINAL_TFLOPS
         if other is not None:

@@ -29,6 +29,17 @@ phosim_status phosim_fma_rate(int fp64, int iterations, int blocks_per_sm, void*
    synchronises it.  Errors: INVALID_ARGUMENT (unknown op, null output, iterations < 1), OUT_OF_MEMORY, CUDA. */
 phosim_status phosim_ds_rate(int op, int iterations, int blocks_per_sm, void* stream, double* tops);
 
+/* Sustained rate of random 32-byte gathers from a device buffer of `bytes` bytes (a multiple of 32, at least
+   32 KiB, below 128 GiB), in GB/s of gathered bytes (1e9 bytes per second): every thread of a grid of
+   blocks_per_sm x SM-count blocks of 256 threads reads `gathers` aligned 32-byte blocks at hashed positions,
+   four independent streams at a time, the gather shape of the atmosphere stage's screen lookups (one 2 x 2
+   block of FP32 gradient pairs per lookup).  A buffer far larger than the L2 gives the HBM's random-gather
+   ceiling (each 32-byte lookup fetches whole DRAM bursts); one far smaller gives the L2's.  The buffer is
+   allocated, zeroed and freed inside the call.  Blocks on `stream` and synchronises it.
+   Errors: INVALID_ARGUMENT (size out of range or not a multiple of 32, gathers < 1, null output),
+   OUT_OF_MEMORY, CUDA. */
+phosim_status phosim_gather_rate(size_t bytes, int gathers, int blocks_per_sm, void* stream, double* gbs);
+
 /* The device Philox4x32-10 the trace kernel draws from (Salmon et al., SC'11), applied to n counters with
    one key, for known-answer checks.  ctr: host, 4 n words; key: host, 2 words; out: host, 4 n words.
    Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */

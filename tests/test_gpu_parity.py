@@ -413,3 +413,28 @@ def test_fringing_back_side_reflection(oracle_mod, precision):
     sc.fringe = False
     ora0 = G.oracle_trace(oracle_mod, sc)
     assert np.sum(det_o != ((ora0["flags"] & 1) == 1)) > 50
+
+
+@pytest.mark.parametrize("precision", [P.PLAIN_FP64, P.MIXED_DS])
+def test_asphere_terms_of_every_order(oracle_mod, precision):
+    """Sec. 2.4.1 asphere polynomials of every order against the oracle, photon by photon, without the
+    atmosphere and the sensor: the paraboloid carries all four even terms alpha_4..alpha_10 (each about 10 um
+    of sag at the rim; the double-single path takes its Newton root after one step there, with the slopes
+    carried by the single-precision second derivatives of all four terms), and the lens's first face all four
+    odd terms alpha_3..alpha_9 (about 1 um each) beside alpha_4, which the double-single path iterates to a step
+    below 1e-8 mm.  Fates as the oracle's away from boundaries and positions at the FP64 per-photon gate."""
+    import dataclasses
+    sc = G.test_system_scene(n_photons=20000, sensor=False, atmosphere=False)
+    s0, s1 = sc.surfaces[0], sc.surfaces[1]
+    r0, r1 = s0.r_out, s1.r_out
+    even = (1e-2 / r0 ** 4, -1e-2 / r0 ** 6, 1e-2 / r0 ** 8, -1e-2 / r0 ** 10)
+    odd = (1e-3 / r1 ** 3, -1e-3 / r1 ** 5, 1e-3 / r1 ** 7, -1e-3 / r1 ** 9)
+    surfaces = list(sc.surfaces)
+    surfaces[0] = dataclasses.replace(s0, alpha=(0.0, even[0], 0.0, even[1], 0.0, even[2], 0.0, even[3]))
+    surfaces[1] = dataclasses.replace(s1, alpha=(odd[0], s1.alpha[1], odd[1], 0.0, odd[2], 0.0, odd[3], 0.0))
+    sc = dataclasses.replace(sc, surfaces=surfaces)
+    gpu = G.run_gpu(sc, precision)
+    ora = G.oracle_trace(oracle_mod, sc)
+    r = G.compare_records(sc, gpu, ora)
+    assert r["n_detected"] > 5000, r
+    assert r["max_err_px"] < (1e-6 if precision == P.PLAIN_FP64 else 1e-4), r
