@@ -530,6 +530,7 @@ void phosim_destroy_scene(phosim_scene* sc) {
     free_all(sc->sersic_mem);
     free_all(sc->hf_mem);
     cudaFree(sc->d_src);
+    cudaFree(sc->d_src_s);
     cudaFree(sc->d_prefix);
     cudaFree(sc->d_counters);
     cudaFree(sc->d_stage);
@@ -1006,9 +1007,11 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     if (n_src == 0 || total == 0) return PHOSIM_OK;
     if (sc->cap_src < (size_t)n_src) {
         cudaFree(sc->d_src);
+        cudaFree(sc->d_src_s);
         cudaFree(sc->d_prefix);
-        sc->d_src = nullptr; sc->d_prefix = nullptr; sc->cap_src = 0;
+        sc->d_src = nullptr; sc->d_src_s = nullptr; sc->d_prefix = nullptr; sc->cap_src = 0;
         CU(cudaMalloc(&sc->d_src, (size_t)n_src * sizeof(DSource)));
+        CU(cudaMalloc(&sc->d_src_s, (size_t)n_src * source_s_bytes()));
         CU(cudaMalloc(&sc->d_prefix, ((size_t)n_src + 1) * sizeof(unsigned long long)));
         sc->cap_src = n_src;
     }
@@ -1073,6 +1076,7 @@ phosim_status phosim_trace(phosim_scene* sc, const phosim_source* src, int n_src
     P.mom_stripes = striped ? sc->d_mom_stripes : nullptr;
     P.mom_stripe_stride = striped ? stripe_stride : 0;
     P.sources = sc->d_src;
+    P.sources_s = staged ? (SourceS*)sc->d_src_s : nullptr;
     P.tile_prefix = sc->d_prefix;
     P.n_src = n_src;
     P.tile_photons = (uint32_t)T;

@@ -99,6 +99,8 @@ struct DLayer {
     DScale s[PHOSIM_MAX_SCALES];
 };
 
+struct SourceS;                              // a source's constants as the double-single path reads them
+
 struct DSource {
     int kind, sed, table;
     uint32_t bundle;                          // photons per ray (Sec. 3.2 background optimisation), >= 1
@@ -159,6 +161,7 @@ struct TraceParams {
     // work and outputs: tile t of the launch is tile t - tile_prefix[s] of the source s with
     // tile_prefix[s] <= t < tile_prefix[s + 1]; a tile holds tile_photons consecutive photons
     const DSource* sources;
+    SourceS* sources_s;                       // the same sources converted once by the chief-ray kernel (two-kernel path)
     const unsigned long long* tile_prefix;
     int n_src;
     uint32_t tile_photons;

@@ -41,6 +41,7 @@ struct phosim_scene {
     // per-call scratch, grown on demand
     phosim::DSource* d_src = nullptr;
     size_t cap_src = 0;
+    void* d_src_s = nullptr;                    // the sources' double-single constants (phosim::SourceS, n_src)
     unsigned long long* d_prefix = nullptr;
     size_t cap_prefix = 0;
     unsigned long long* d_counters = nullptr;   // [0] tile counter, [1..9] counters
@@ -77,6 +78,7 @@ cudaError_t launch_chief_rays(const TraceParams& P, DSource* sources, int n_src,
 cudaError_t trace_occupancy(int mode, int threads, int* blocks_per_sm);
 const void* trace_kernel_ptr(int mode);
 const void* chief_kernel_ptr();
+size_t source_s_bytes();                       // sizeof(SourceS), which the host code does not see
 // the two-kernel double-single path (PHOSIM_MIXED_DS in phosim_trace)
 cudaError_t launch_ds_entry(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_ds_optics(const TraceParams& P, const DSStage& S, int blocks, int threads, cudaStream_t st);

@@ -322,7 +322,12 @@ __global__ void __launch_bounds__(256, PHOSIM_DS_ENTRY_MIN_BLOCKS) ds_entry_kern
         const uint64_t off = j * P.tile_photons;
         const uint32_t count = (uint32_t)min((uint64_t)P.tile_photons, s.ucount - off);
         const uint64_t ufirst = s.ufirst + off;
-        if (lane == 0) src_mem[warp] = source_s(s);
+        {   // the source's constants, converted by the chief-ray kernel: one word a lane
+            static_assert(sizeof(SourceS) % 4 == 0 && sizeof(SourceS) <= 128, "SourceS copy");
+            const uint32_t* from = reinterpret_cast<const uint32_t*>(P.sources_s + src);
+            uint32_t* to = reinterpret_cast<uint32_t*>(&src_mem[warp]);
+            for (int w = lane; w < (int)(sizeof(SourceS) / 4); w += 32) to[w] = __ldg(from + w);
+        }
         __syncwarp();
         const SourceS& ss = src_mem[warp];
         const uint32_t nb = ss.bundle;          // the same for the whole warp (one source per tile)
@@ -658,6 +663,9 @@ __global__ void chief_ray_kernel(const __grid_constant__ TraceParams P, DSource*
     S.ref_y = ok ? R.y : 0.0;
     const ds rx = ds_of(S.ref_x), ry = ds_of(S.ref_y);
     S.ref_s[0] = rx.hi; S.ref_s[1] = rx.lo; S.ref_s[2] = ry.hi; S.ref_s[3] = ry.lo;
+    // the double-single constants of the source, converted once here instead of once per tile (the conversions
+    // from double run on the FP64 pipe)
+    if (P.sources_s) P.sources_s[s] = source_s(S);
     if (moments) {
         moments[(size_t)s * PHOSIM_MOMENT_WORDS + 6] = S.ref_x;
         moments[(size_t)s * PHOSIM_MOMENT_WORDS + 7] = S.ref_y;
@@ -682,6 +690,7 @@ const void* trace_kernel_ptr(int mode) {
     return mode == kMixed ? (const void*)trace_kernel<kMixed> : (const void*)trace_kernel<kPlain>;
 }
 const void* chief_kernel_ptr() { return (const void*)chief_ray_kernel; }
+size_t source_s_bytes() { return sizeof(SourceS); }
 const void* ds_entry_kernel_ptr() { return (const void*)ds_entry_kernel; }
 const void* ds_optics_kernel_ptr() { return (const void*)ds_optics_kernel; }
 const void* moment_stripes_kernel_ptr() { return (const void*)moment_stripes_kernel; }
