@@ -128,6 +128,7 @@ class ClockSampler:
 
 TRAFFIC_PROFILE = INST_PROFILE = None       # every committed summary under profiles/
 KERNEL_SOURCES = ("paper_1504_06570_gb300/csrc/photon.cuh", "paper_1504_06570_gb300/csrc/trace.cu",
+                  "paper_1504_06570_gb300/csrc/trace_optics.cu",
                   "paper_1504_06570_gb300/csrc/phosim_device.cuh", "paper_1504_06570_gb300/csrc/photon_ds.cuh",
                   "paper_1504_06570_gb300/csrc/ds.cuh")
 

@@ -178,6 +178,8 @@ struct TraceParams {
     unsigned long long mom_stripe_stride;
 };
 constexpr int kMomStripes = 16;
+// warps of the entry and bundle stages' blocks (the shared-memory queues and counters are sized for it)
+constexpr int kWarpsPerBlock = 8;
 
 // ------------------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two 32x32 multiplications per round.

@@ -25,6 +25,15 @@
 
 namespace phosim {
 
+// A work unit of the two-kernel path is a photon, or for a bundle of n photons per ray (Sec. 3.2) a ray:
+// the ray is traced once and its photons (those in the call's range) only go through the sensor apart.
+__device__ __forceinline__ void unit_members(const DSource& s, uint32_t nb, uint64_t u, uint64_t& lo, uint32_t& nm) {
+    if (nb <= 1) { lo = u; nm = 1; return; }
+    const uint64_t a = max(s.first, u * nb), b = min(s.first + s.count, (u + 1) * nb);
+    lo = a;
+    nm = b > a ? (uint32_t)(b - a) : 0u;
+}
+
 // one out-of-line copy of the generator for the double-single path (the FP64 kernels inline it)
 static __device__ PHOSIM_DS_PHILOX uint4 philox_ds(uint4 c, uint32_t k0, uint32_t k1) { return philox(c, k0, k1); }
 
