@@ -504,7 +504,11 @@ def main():
             scn.set_schedule(*[int(v) for v in args.schedule.split(",")])
             tuned[name] = scn.schedule()
         else:
-            tuned[name] = scn.autotune(sample_photons=20_000_000, n_photons=counts, stream=stream.cuda_stream)
+            # the double-single path on 2e8 photons (~20 ms a trial): on 2e7 its trials had about three tiles
+            # of 1024 photons per warp and favoured small tiles that the full workload runs slower (entry stage
+            # 402 against 370 ms); the FP64 paths, 8 times slower, on 2e7
+            sample = 200_000_000 if name == "mixed_ds" else 20_000_000
+            tuned[name] = scn.autotune(sample_photons=sample, n_photons=counts, stream=stream.cuda_stream)
     other, plain = arms.get("mixed_fp64_optics"), arms.get("plain_fp64")
     setup_s = time.perf_counter() - t_setup
     d = sc.detector
