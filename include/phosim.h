@@ -297,7 +297,10 @@ phosim_status phosim_moments_derive(const double* sums, int n_src, double* out);
    over the sources in proportion to their counts) with each candidate (threads per block in {64, 128, 256},
    photons per warp tile in {64, 256, 1024, 4096}), times each on the stream with CUDA events (best of
    two), and keeps the fastest through phosim_set_schedule.  Results never depend on the schedule (the
-   random numbers are counter-based), only the speed does.  out_threads / out_tile may be NULL.
+   random numbers are counter-based), only the speed does.  A sample should give every resident warp several
+   tiles of the largest candidate (on a GB300 with the double-single path, 2e8 photons: with 2e7 the large
+   tiles' trials end on a ragged last round and small tiles win that the whole workload runs slower).
+   out_threads / out_tile may be NULL.
    Errors: as phosim_trace. */
 phosim_status phosim_autotune(phosim_scene* scene, const phosim_source* sources, int n_src,
                               const uint64_t* n_photons, uint64_t sample_photons, void* stream,
