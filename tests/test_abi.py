@@ -83,3 +83,20 @@ def test_argument_validation_before_device_work(L):
     assert L.phosim_set_schedule(None, 64, 0) == -1
     assert L.phosim_status_string(-6) == b"size exceeds a library maximum"
     L.phosim_destroy_scene(None)
+
+
+def test_probe_arguments_checked_before_device_work(L):
+    """The measurement probes of phosim_bench.h reject their malformed arguments before any CUDA call, so these
+    answers need no device."""
+    r = C.c_double()
+    assert L.phosim_fma_rate(0, 0, 4, None, C.byref(r)) == -1               # iterations < 1
+    assert L.phosim_fma_rate(0, 10, 4, None, None) == -1                    # no output
+    assert L.phosim_ds_rate(5, 10, 4, None, C.byref(r)) == -1               # unknown primitive
+    assert L.phosim_ds_rate(-1, 10, 4, None, C.byref(r)) == -1
+    assert L.phosim_ds_rate(0, 10, 0, None, C.byref(r)) == -1               # blocks per SM < 1
+    for nbytes in (0, 32 * 1023, (1 << 20) + 16, 128 << 30):               # too small, not a multiple of 32, too large
+        assert L.phosim_gather_rate(C.c_size_t(nbytes), 16, 4, None, C.byref(r)) == -1, nbytes
+    assert L.phosim_gather_rate(C.c_size_t(1 << 20), 0, 4, None, C.byref(r)) == -1
+    assert L.phosim_gather_rate(C.c_size_t(1 << 20), 16, 4, None, None) == -1
+    assert L.phosim_moments_derive(None, 1, None) == -1
+    assert L.phosim_ds_eval(10, None, None, None, 1) == -1
