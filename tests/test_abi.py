@@ -100,3 +100,28 @@ def test_probe_arguments_checked_before_device_work(L):
     assert L.phosim_gather_rate(C.c_size_t(1 << 20), 16, 4, None, None) == -1
     assert L.phosim_moments_derive(None, 1, None) == -1
     assert L.phosim_ds_eval(10, None, None, None, 1) == -1
+
+
+def test_moments_derive_on_the_host(L):
+    """phosim_moments_derive is host arithmetic (Sec. 3.1 counts and centroids, the second moments of the
+    image-quality comparisons): from sums about a reference point it gives the count, the centroid and the
+    central second moments of a point set, computed here two-pass from the points themselves; NaN for a
+    source with no photon."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    pts = [rng.normal([3.0, -2.0], [0.02, 0.05], size=(n, 2)) for n in (1, 7, 1000)]
+    sums = np.zeros((4, P.MOMENT_WORDS))
+    for s, p in enumerate(pts):
+        ref = np.array([2.99, -2.01])
+        d = p - ref
+        sums[s, :6] = [len(p), d[:, 0].sum(), d[:, 1].sum(), (d[:, 0] ** 2).sum(), (d[:, 0] * d[:, 1]).sum(),
+                       (d[:, 1] ** 2).sum()]
+        sums[s, 6:8] = ref
+    out = P.derived_moments(sums)
+    for s, p in enumerate(pts):
+        c = p.mean(axis=0)
+        q = p - c
+        want = [len(p), c[0], c[1], (q[:, 0] ** 2).mean(), (q[:, 0] * q[:, 1]).mean(), (q[:, 1] ** 2).mean()]
+        np.testing.assert_allclose(out[s], want, rtol=1e-9, atol=1e-13)
+    assert np.all(np.isnan(out[3, 1:]))
+    assert out[3, 0] == 0
