@@ -970,3 +970,27 @@ def test_fringing_conversion_fraction_across_a_thickness_wedge(oracle_mod):
     R0 = ((nsi - 1) / (nsi + 1)) ** 2
     p0 = (1 - np.exp(-t / ell)) + R0 * (np.exp(-t / ell) - np.exp(-2 * t / ell))
     assert abs(((rec2["flags"] & 1) == 1).mean() - p0.mean()) < 4 * np.sqrt(p0.mean() * (1 - p0.mean()) / n_ph)
+
+
+def test_sag_every_asphere_order(oracle_mod):
+    """Sec. 2.4.1 asphere polynomial of every order the interface carries, alpha_3 r^3 through alpha_10 r^10 (odd
+    terms included), on a conic: the sag is the closed form term by term, and its slopes are the central
+    differences of that sag (odd powers of r have their r-derivative singular only in the third derivative, so
+    the slopes are smooth through the vertex)."""
+    alpha = [2e-10, 3e-12, -4e-15, -2e-18, 5e-21, 1e-24, -3e-27, 2e-30]
+    surfaces = [I.Surface(kind=I.MIRROR, R=7000.0, kappa=-0.7, alpha=alpha), I.Surface(kind=I.DETECTOR, z=1.0, material=1)]
+    o = oracle_mod.Oracle(bare_scene(surfaces))
+    rng = np.random.default_rng(21)
+    x, y = rng.uniform(-900, 900, 400), rng.uniform(-900, 900, 400)
+    r = np.hypot(x, y)
+    c = 1 / 7000.0
+    want = c * r * r / (1 + np.sqrt(1 - 0.3 * c * c * r * r)) + sum(a * r ** (i + 3) for i, a in enumerate(alpha))
+    z, zx, zy = o.sag(0, x, y)
+    np.testing.assert_allclose(z, want, rtol=1e-12, atol=1e-12)
+    # dz/dr of the closed form, projected on x and y
+    dr = c * r / np.sqrt(1 - 0.3 * c * c * r * r) + sum((i + 3) * a * r ** (i + 2) for i, a in enumerate(alpha))
+    np.testing.assert_allclose(zx, dr * x / r, rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(zy, dr * y / r, rtol=1e-10, atol=1e-13)
+    h = 1e-3
+    zp, _, _ = o.sag(0, x + h, y); zm, _, _ = o.sag(0, x - h, y)
+    np.testing.assert_allclose(zx, (zp - zm) / (2 * h), rtol=1e-7, atol=1e-10)
